@@ -1,0 +1,343 @@
+"""Benchmark of one DC-DFT SCF step (the whole batched fragment Kohn-Sham solve) on one B300.
+
+A step is one pass of every stage of the path over the Si512 workload (80^3 grid, 8^3 fragments of
+10^3 core + 6-point buffers = 22^3 points, 48 orbitals each, 512 atoms): potential (Poisson +
+exchange), gather, Chebyshev filter (degree 10) with the fused stencil H-apply, Gram and
+Rayleigh-Ritz, FP64 subspace solves, rotation, core weights, Fermi level, density, energies and
+mixing.  The orbital block (1.05 GB in FP32) is larger than L2, so no L2 flush is needed between
+steps.
+
+Output: one JSON line (rank 0).  ``value`` is SCF steps per second summed over ranks (each rank runs
+its own replica: weak scaling, no collective on the data path).  ``--impl reference`` times the FP64
+CPU oracle on a bounded sample of the same workload (fragments sampled, global stages whole).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = None
+WORKLOAD_TEXT = {
+    "si512": "Si512 a-Si-like (4^3 diamond supercell, a=41.04 bohr, N(0,0.3) displacements), 80^3 grid, "
+             "8^3 fragments of 10^3 core + 6-point buffer (22^3), 48 orbitals each",
+    "si64": "Si64 (2^3 supercell), 40^3 grid, 4^3 fragments of 10^3 core + 5 (20^3), 32 orbitals",
+    "si8": "Si8 diamond cell, 20^3 grid, 2^3 fragments of 10^3 core + 4 (18^3), 24 orbitals",
+}
+
+
+def _metric():
+    global METRIC
+    if METRIC is None:
+        with open(os.path.join(ROOT, "BASELINE.json")) as fh:
+            METRIC = json.load(fh)["metric"]
+    return METRIC
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="si512", choices=sorted(WORKLOAD_TEXT))
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    p.add_argument("--sample-frags", type=int, default=8, help="fragments in the oracle's timed sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm), reasons=sorted(reasons))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return dict(hbm_gbs=6400.0, bf16_tflops=1800.0, bf16_tflops_sustained=1400.0), "fallback"
+
+
+def kernel_traffic(kernel_file):
+    """DRAM traffic per launch of the dominant kernel from a committed ncu summary, if it is current."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        src = open(os.path.join(ROOT, "paper_2606_21125_b300", "csrc", kernel_file), "rb").read()
+        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None, "kernel changed since the ncu capture"
+        return rec["bytes_per_launch"], rec.get("note", "")
+    except (OSError, KeyError, ValueError):
+        return None, "no ncu capture"
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# ------------------------------------------------------------------------------------------------
+class OracleSample:
+    """The FP64 oracle timed on `k` stride-chosen fragments plus every global stage.
+
+    One sampled step = V_eff (FFT Poisson + exchange) + one CheFSI pass on the k fragments + their
+    core weights and densities + Fermi level + energy + mixing; the fragment part is scaled by F/k.
+    """
+
+    def __init__(self, cfg, k):
+        from oracle import scf
+        self.cfg = cfg
+        nf = int(cfg["num_fragment"][0] * cfg["num_fragment"][1] * cfg["num_fragment"][2])
+        k = max(1, min(k, nf))
+        self.sample = sorted(set(int(round(i * nf / k)) % nf for i in range(k)))
+        self.nf = nf
+        self.st = scf.DCState(cfg, fragments_subset=self.sample)
+        V = self.st.veff(self.st.rho_in)
+        self.st.initial_rr(V)
+
+    def step(self):
+        from oracle import energy, fermi
+        st = self.st
+        t0 = time.perf_counter()
+        V = st.veff(st.rho_in)
+        t1 = time.perf_counter()
+        st.solve(V, int(self.cfg["n_pass"]))
+        t2 = time.perf_counter()
+        q, mu, occ, rho_part = st.density_stage()
+        import numpy as np
+        eps_all = np.concatenate([st.eps[f] for f in st.active])
+        q_all = np.concatenate([q[f] for f in st.active])
+        occ_all = np.concatenate([occ[f] for f in st.active])
+        eb = energy.band_sum(eps_all, q_all, occ_all)
+        energy.total_energy(st.grid, st.hxc, eb, V, rho_part, st.rhoiG)
+        fermi.entropy(eps_all, q_all, mu, st.kT)
+        energy.residual(st.grid, rho_part, st.rho_in, st.ne)
+        energy.mix(st.rho_in, rho_part, 0.0)
+        t3 = time.perf_counter()
+        frag = (t2 - t1) * self.nf / len(self.sample)
+        return (t1 - t0) + (t3 - t2) + frag
+
+    def describe(self):
+        return (f"FP64 oracle: CheFSI pass on {len(self.sample)} of {self.nf} fragments (stride-chosen), "
+                f"scaled x{self.nf / len(self.sample):g}, plus the whole global stages (Poisson/exchange, Fermi, "
+                f"density, energy, mixing)")
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        n = 1
+    return n
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    cfg = workloads.make_config(args.workload, precision="fp64")
+    samp = OracleSample(cfg, args.sample_frags)
+    for _ in range(args.warmup):
+        samp.step()
+    ts = [samp.step() for _ in range(args.steps)]
+    sec = sum(ts) / len(ts)
+    val = 1.0 / sec
+    cores = os.cpu_count()
+    line = dict(impl="reference", metric=_metric(), value=val, unit="SCF steps/s", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=sec * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD_TEXT[args.workload], precision="fp64 (oracle)"),
+                cpu_baseline=dict(value=val, unit="SCF steps/s", cores=cores, threads=cpu_threads(), kind="oracle",
+                                  sample=samp.describe()),
+                e2e=dict(value=val, unit="SCF steps/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads
+    from paper_2606_21125_b300 import DCSolver
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cfg = workloads.make_config(args.workload, precision=args.precision)
+    solver = DCSolver(cfg)
+    t0 = time.perf_counter()
+    solver.warmup()
+    torch.cuda.synchronize()
+    init_s = time.perf_counter() - t0
+    _, rho0 = solver.initial()
+    rho = rho0.clone()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        solver.scf_step(rho)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K SCF steps with inputs resident in HBM ----
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    solver.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = None
+    for _ in range(args.steps):
+        stats = solver.scf_step(rho)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    prof = solver.profile_read()
+    solver.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = ws * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through the public API with host buffers (H2D rho_in, D2H rho + stats) ----
+    host = torch.empty(solver.layout.npts, dtype=torch.float64, pin_memory=True)
+    host.copy_(rho.cpu())
+    hnp = host.numpy()
+    solver.scf_step(hnp)
+    barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.scf_step(hnp)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_val = ws * args.steps / float(t.item())
+    nb = 8 * solver.layout.npts
+
+    # ---- roofline of the dominant kernel (stencil H-apply, all launches of the timed region) ----
+    peaks, peak_kind = measured_peaks()
+    h = prof["hpsi"]
+    achieved = h["bytes"] / (h["ms"] * 1e-3) / 1e9 if h["ms"] > 0 else 0.0
+    traffic, traffic_note = kernel_traffic("k_hamiltonian.cu")
+    per_launch_bytes = h["bytes"] / max(1, h["launches"])
+    launches = sum(v["launches"] for v in prof.values())
+
+    line = dict(metric=_metric(), value=value, unit="SCF steps/s", n_gpus=ws, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype={"fp32": "f32", "fp64": "f64", "mixed": "f32+bf16x3"}[args.precision],
+                data="synthetic",
+                config=dict(workload=WORKLOAD_TEXT[args.workload], precision=args.precision,
+                            subspace_dtype="f64", cheb_degree=cfg["cheb_degree"], n_pass=cfg["n_pass"],
+                            l2="orbital block larger than L2 (no flush needed)",
+                            parallelism=f"replicas x{ws}" if ws > 1 else "single GPU"),
+                roofline=dict(kernel="k_hstep (fused stencil + local + nonlocal H-apply, Chebyshev step)",
+                              bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                              frac=achieved / peaks["hbm_gbs"], peak_kind=peak_kind + " (hbm_gbs)",
+                              traffic=traffic, traffic_note=traffic_note,
+                              algorithmic_bytes_per_launch=per_launch_bytes, launches=h["launches"],
+                              avg_launch_ms=h["ms"] / max(1, h["launches"])),
+                stages_ms_per_step={k: v["ms"] / args.steps for k, v in prof.items()},
+                e2e=dict(value=e2e_val, unit="SCF steps/s", h2d_bytes_per_step=nb, d2h_bytes_per_step=nb + 8 * 16),
+                gpu_launches=launches, init_s=init_s,
+                last_step=dict(E_per_atom=stats["E"] / len(cfg["pos"]), mu=stats["mu"], drho=stats["drho"]),
+                clocks=clocks)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        samp = OracleSample(workloads.make_config(args.workload, precision="fp64"), args.sample_frags)
+        sec = samp.step()
+        line["cpu_baseline"] = dict(value=1.0 / sec, unit="SCF steps/s", cores=os.cpu_count(), threads=cpu_threads(),
+                                    kind="oracle", sample=samp.describe())
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,257 @@
+/*
+ * dcdft.h -- C ABI of the B300-native divide-and-conquer DFT fragment solver.
+ *
+ * The library implements the data-parallel inner part of one DC-DFT SCF
+ * iteration (Sec. 2.2 of "SALMON 2.3: Implementation of divide-and-conquer
+ * ground-state initialization for large-scale real-time TDDFT"): the periodic
+ * cell is split into overlapping fragments (core plus buffer, Sec. 2.2 and
+ * Table 1), each fragment Kohn-Sham problem (Eq. 1, Hamiltonian Eq. 5) is
+ * solved for its lowest states, the global chemical potential fixes N_e, and
+ * the fragment densities are projected onto their cores and summed (Eqs. 2-4).
+ *
+ * Conventions used by every call:
+ *  - Units: Hartree atomic units (Ha, bohr).
+ *  - Status: every int-returning call gives 0 (DC_OK) or a negative DC_ERR_*
+ *    code; no call aborts, throws, or leaves a CUDA error pending on return.
+ *    dc_error_string() names a code; dc_last_error() returns a one-line
+ *    description of the last failure in this process.
+ *  - Ownership: the caller owns every pointer argument; the library never
+ *    keeps a pointer after a call returns.  The library owns the context
+ *    (maps, projector tables, the orbital state and its work blocks, FFT
+ *    plans), allocated in dc_init and freed in dc_finalize.
+ *  - Memory spaces: arguments named d_* are device pointers (CUDA global
+ *    memory on the current device); h_* are host pointers.
+ *  - Streams: device work is issued on the given cudaStream_t (passed as
+ *    void*, NULL = legacy default stream); calls that return host results
+ *    synchronise that stream.  A context is not thread-safe.
+ *  - Layouts:
+ *      global grid arrays  [Nz][Ny][Nx], x fastest, g = x + Nx (y + Ny z);
+ *      fragment id         f = kx + Fx (ky + Fy kz);
+ *      orbital blocks      concatenation over f of [n_f][Ez][Ey][Ex] (x fastest),
+ *                          fragment f starting at element psi_offset[f];
+ *      per-state arrays    concatenation over f of [n_f] (state_offset[f]).
+ *  - Element type of orbital blocks: double for DC_FP64, float for DC_FP32 and
+ *    DC_MIXED (the "dtype" arguments take DC_FP64 or DC_FP32).
+ */
+#ifndef DCDFT_H
+#define DCDFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define DC_OK 0
+#define DC_ERR_ARG (-1)       /* invalid argument, size or configuration */
+#define DC_ERR_CUDA (-2)      /* a CUDA runtime or cuFFT call failed */
+#define DC_ERR_OOM (-3)       /* device allocation failed */
+#define DC_ERR_NOCONV (-4)    /* a Gram matrix was not positive definite (Cholesky failed) */
+#define DC_ERR_TIMEOUT (-5)   /* a bounded device-side wait ran out; the kernel returned early */
+#define DC_ERR_NONFINITE (-6) /* NaN or Inf in an energy, mu or an eigenvalue */
+#define DC_ERR_STATE (-7)     /* call out of order (e.g. dc_scf_step before dc_warmup) */
+
+/* ---- enumerations ---------------------------------------------------------------------- */
+#define DC_FP64 0  /* all fragment arithmetic in FP64 */
+#define DC_FP32 1  /* FP32 stencil, Gram and rotation; FP64 subspace solves and Fermi level */
+#define DC_MIXED 2 /* FP32 stencil; Gram/Rayleigh-Ritz on tensor cores from split BF16 words */
+
+#define DC_BC_ZERO 0     /* fragment ghost points are zero (buffer edge) */
+#define DC_BC_PERIODIC 1 /* ghost points wrap within the fragment extent (Sec. 2.2) */
+
+#define DC_HXC_NONE 0      /* V_eff = V_loc only (non-interacting model) */
+#define DC_HXC_HARTREE_X 1 /* V_eff = V_loc + V_H[rho] + v_x[rho] (Eq. 5, LDA exchange) */
+
+/* ---- configuration --------------------------------------------------------------------- */
+/* Periodic orthorhombic cell: n grid points and length L (bohr) per axis; h = L/n. */
+typedef struct {
+  int n[3];
+  double L[3];
+} dc_grid_t;
+
+/* Table 1: num_fragment(1:3), nstate_frag.  nstate_frag > 0 fixes the orbital count of every
+ * fragment; nstate_frag == 0 derives it from the electrons of the atoms that have an image in the
+ * fragment box: n_f = ceil(Ne_f/2) + max(4, ceil(0.2 ceil(Ne_f/2))).  bc: DC_BC_*. */
+typedef struct {
+  int num_fragment[3];
+  int bc;
+  int nstate_frag;
+} dc_fragments_t;
+
+/* Table 1: num_rgrid_buffer(1:3), the buffer thickness b in grid points (Sec. 2.2). */
+typedef struct {
+  int num_rgrid_buffer[3];
+} dc_buffers_t;
+
+/* Atoms (host arrays, read during dc_init only).  pos[natom][3] in bohr; species[natom] in
+ * [0, nspecies).  Per species: valence charge Z, Gaussian width of the local ion charge
+ * sigma_loc, projector width sigma_proj and projector strength D (Ha). */
+typedef struct {
+  int natom;
+  const double *pos;
+  const int *species;
+  int nspecies;
+  const double *Z;
+  const double *sigma_loc;
+  const double *sigma_proj;
+  const double *D;
+} dc_atoms_t;
+
+/* Solver parameters.  precision: DC_FP64/DC_FP32/DC_MIXED.  cheb_degree: Chebyshev filter degree
+ * m (>= 1).  n_pass: CheFSI passes per SCF step.  n_warmup: passes in the starting potential before
+ * the first step (run in FP64 for every precision).  hxc: DC_HXC_*.  kT: electronic temperature
+ * (Ha, > 0).  mix_alpha: linear mixing weight in (0, 1].  seed: initial-orbital seed. */
+typedef struct {
+  int precision;
+  int cheb_degree;
+  int n_pass;
+  int n_warmup;
+  int hxc;
+  double kT;
+  double mix_alpha;
+  uint64_t seed;
+} dc_params_t;
+
+/* Sizes of everything a caller allocates for the calls below. */
+typedef struct {
+  int nfrag;           /* number of fragments F = Fx Fy Fz */
+  int natom;           /* atoms */
+  int64_t npts;        /* global grid points Nx Ny Nz */
+  int64_t psi_elems;   /* elements of one orbital block: sum_f n_f P_f */
+  int64_t frag_points; /* sum_f P_f (length of the fragment-point maps) */
+  int64_t nstates;     /* sum_f n_f */
+  int64_t natom_frag;  /* sum_f |A_f| (atoms whose projector touches fragment f) */
+  int max_norb;        /* max_f n_f */
+  int element_bytes;   /* 8 for DC_FP64, 4 otherwise */
+} dc_layout_t;
+
+/* Per-step results (host struct filled by dc_scf_step). */
+typedef struct {
+  double E;     /* total energy (Ha) */
+  double F;     /* free energy E - kT S (Ha) */
+  double eband; /* sum_f sum_i 2 f_i eps_i q_i (Ha) */
+  double mu;    /* chemical potential (Ha) */
+  double drho;  /* int |rho_out - rho_in| / N_e */
+  double ne;    /* int rho_out (should equal N_e) */
+  int step;     /* SCF steps done so far */
+  int status;   /* DC_OK or the first error seen during the step */
+} dc_stats_t;
+
+typedef struct dc_ctx dc_ctx;
+
+/* ---- lifecycle ------------------------------------------------------------------------- */
+/* Build the fragment decomposition (Sec. 2.2, Table 1), the per-fragment atom lists and
+ * projector factors, the ionic potential V_loc and ion charge rho_ion(G) (on the device, via
+ * cuFFT), the starting density (band-limited ion charge scaled to N_e) and the random starting
+ * orbitals; allocate the orbital state and work blocks.  Synchronous.  On failure *out is NULL
+ * and nothing is leaked.  Errors: DC_ERR_ARG (sizes, counts, f >= 4096 fragments or n_f > 1024),
+ * DC_ERR_OOM, DC_ERR_CUDA. */
+int dc_init(const dc_grid_t *grid, const dc_fragments_t *fragments, const dc_buffers_t *buffers,
+            const dc_atoms_t *atoms, const dc_params_t *params, dc_ctx **out);
+void dc_finalize(dc_ctx *ctx);
+const char *dc_error_string(int status);
+const char *dc_last_error(void);
+
+/* Sizes of caller-allocated arrays. */
+int dc_query(const dc_ctx *ctx, dc_layout_t *out);
+
+/* Fragment maps (Sec. 2.2), host outputs, for bit-exact checks; any pointer may be NULL.
+ *  h_frag[f*12 + 0..11] = origin[3] (s_k - b, may be negative), extent[3], core[3], n_f,
+ *                         |A_f|, 0;
+ *  h_idx_map[frag_points]  = global index of each fragment point (fragment f at
+ *                            sum_{f'<f} P_f');
+ *  h_owner[npts], h_core_local[npts] = fragment whose core holds g and g's local index there;
+ *  h_atoms[natom_frag]     = global indices of A_f, ascending, concatenated over f. */
+int dc_get_maps(const dc_ctx *ctx, int32_t *h_frag, int32_t *h_idx_map, int32_t *h_owner,
+                int32_t *h_core_local, int32_t *h_atoms);
+
+/* ---- potentials ------------------------------------------------------------------------ */
+/* Copy the ionic potential V_loc[npts] and the starting density rho_0[npts] (FP64, device). */
+int dc_get_initial(dc_ctx *ctx, double *d_vion, double *d_rho0, void *stream);
+
+/* V_eff = V_loc + V_H[rho] + v_x[rho] (or V_loc for DC_HXC_NONE) from d_rho[npts] (Eq. 5);
+ * stores it in the context (used by every later H application) and copies it to d_veff
+ * (may be NULL).  Poisson by cuFFT, G=0 dropped. */
+int dc_potential(dc_ctx *ctx, const double *d_rho, double *d_veff, void *stream);
+
+/* Store an arbitrary V_eff[npts] (FP64, device) as the context's potential. */
+int dc_set_potential(dc_ctx *ctx, const double *d_veff, void *stream);
+
+/* ---- fragment Hamiltonian ---------------------------------------------------------------- */
+/* d_hpsi = H_f d_psi for every fragment and orbital of a caller block in the layout above (Eq. 5
+ * model Hamiltonian: -1/2 of the 8th-order FD Laplacian with the fragment boundary condition,
+ * the context's V_eff restricted to the fragment, and sum_a D_a p_a <p_a|psi>).  dtype selects
+ * double or float elements (DC_FP64 or DC_FP32).  d_psi and d_hpsi must not overlap. */
+int dc_hpsi(dc_ctx *ctx, const void *d_psi, void *d_hpsi, int dtype, void *stream);
+
+/* ---- fragment eigensolver (CheFSI) ------------------------------------------------------ */
+/* Rayleigh-Ritz of the current orbital block without filtering (used once on the random start). */
+int dc_subspace(dc_ctx *ctx, void *stream);
+/* n_pass CheFSI passes on every fragment in the current V_eff: degree-m scaled Chebyshev filter
+ * with bounds from the previous Ritz values, Cholesky orthonormalisation of the Gram matrix,
+ * Rayleigh-Ritz and rotation (Eq. 1).  Gram/RR in the context precision, subspace solves FP64. */
+int dc_chefsi(dc_ctx *ctx, int n_pass, void *stream);
+/* Starting potential from the starting density, Rayleigh-Ritz of the random block and n_warmup
+ * CheFSI passes (all in FP64; the state is then converted to the context precision). */
+int dc_warmup(dc_ctx *ctx, void *stream);
+
+/* Copy the orbital state (element type of the context) and the Ritz values eps[nstates] out
+ * (device); either pointer may be NULL.  dc_set_state loads them in. */
+int dc_get_state(dc_ctx *ctx, void *d_psi, double *d_eps, void *stream);
+int dc_set_state(dc_ctx *ctx, const void *d_psi, const double *d_eps, void *stream);
+
+/* ---- density -------------------------------------------------------------------------- */
+/* From the current state: core weights q_i^f = <psi_i|1_core|psi_i>, the chemical potential with
+ * sum_f sum_i 2 f((eps_i^f - mu)/kT) q_i^f = N_e (FP64 bisection, Sec. 2.2), and the
+ * core-projected density rho_out(g) = sum_i 2 f_i^f psi_i^f(j)^2 with f = owner(g) (Eqs. 2-4).
+ * Outputs (device, FP64): d_rho[npts]; d_q[nstates] and d_mu[1] may be NULL. */
+int dc_density(dc_ctx *ctx, double *d_rho, double *d_q, double *d_mu, void *stream);
+
+/* ---- SCF step ------------------------------------------------------------------------- */
+/* One DC-DFT SCF iteration (Sec. 2.2): V_eff[rho_in], n_pass CheFSI passes, q, mu, rho_out,
+ * energies, and linear mixing written back: rho_in <- rho_in + alpha (rho_out - rho_in).
+ * rho_in_out[npts] FP64 is a device pointer if rho_on_host == 0, else a host pointer (then
+ * copied in and out on the stream inside the call).  *h_stats is filled (host); the stream is
+ * synchronised.  Requires dc_warmup first (DC_ERR_STATE otherwise). */
+int dc_scf_step(dc_ctx *ctx, double *rho_in_out, int rho_on_host, dc_stats_t *h_stats, void *stream);
+
+/* rho_out of the last dc_scf_step (device, FP64 [npts]). */
+int dc_get_rho_out(dc_ctx *ctx, double *d_rho, void *stream);
+
+/* ---- band-energy adjoint --------------------------------------------------------------- */
+/* E_b = sum_f sum_i occ_i <psi_i^f|H_f|psi_i^f> for a caller block d_psi (dtype), occupations
+ * d_occ[nstates] (FP64, any values), potential d_V[npts] and per-atom strengths d_D[natom]
+ * (FP64).  Writes h_Eb (host, may be NULL), d_dpsi = 2 occ_i dV H_f psi_i (dtype, may be NULL),
+ * d_dV[npts] = dV sum over all fragments covering g of sum_i occ_i psi_i^2 (FP64, unweighted,
+ * deterministic gather; may be NULL), d_dD[natom] = sum_f sum_i occ_i <p_a|psi_i>^2 (FP64, may
+ * be NULL).  H psi is recomputed, never stored across calls.  Does not change the context's
+ * potential. */
+int dc_eb_adjoint(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_occ, const double *d_V,
+                  const double *d_D, double *h_Eb, void *d_dpsi, double *d_dV, double *d_dD, void *stream);
+
+/* ---- stage profiler -------------------------------------------------------------------- */
+/* Stages of the step, in the order they run. */
+#define DC_STAGE_POTENTIAL 0 /* Poisson + exchange (cuFFT and pointwise kernels) */
+#define DC_STAGE_GATHER 1    /* V_eff restricted to every fragment, spectral bounds */
+#define DC_STAGE_PROJECT 2   /* projections <p_a|psi> of the first filter input */
+#define DC_STAGE_HPSI 3      /* stencil H-apply kernels (Chebyshev steps and the last H Y) */
+#define DC_STAGE_GRAM 4      /* Gram and Rayleigh-Ritz contractions */
+#define DC_STAGE_SUBSPACE 5  /* FP64 Cholesky, eigensolve, filter coefficients */
+#define DC_STAGE_ROTATE 6    /* Psi = Y C */
+#define DC_STAGE_DENSITY 7   /* core weights, Fermi level, rho_out */
+#define DC_STAGE_ENERGY 8    /* energies and mixing */
+#define DC_NSTAGES 9
+
+/* enable = 1 clears the counters and starts recording CUDA events around every stage launched
+ * by later calls on their stream; enable = 0 stops recording.  dc_profile_read synchronises the
+ * device and writes, per stage, the summed device time in ms, the number of this library's kernel
+ * launches and the algorithmic bytes those launches must move (reads + writes of their operands,
+ * each counted once; host arrays of DC_NSTAGES entries, any may be NULL). */
+int dc_profile(dc_ctx *ctx, int enable);
+int dc_profile_read(dc_ctx *ctx, double *h_ms, int64_t *h_launches, double *h_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DCDFT_H */

@@ -203,17 +203,12 @@ def periodic_gaussian_1d(x, X, sigma, cut, L):
 
 
 def initial_density(grid: Grid, pos, species, spec):
-    """Superposition of the Gaussian ion charges (cut at 8 sigma per axis), scaled to N_e."""
-    rho = np.zeros(grid.shape())
-    for a in range(len(pos)):
-        s = species[a]
-        sig = spec["sigma_loc"][s]
-        f = []
-        for d in range(3):
-            x = np.arange(grid.n[d]) * grid.h[d]
-            v, _ = periodic_gaussian_1d(x, pos[a, d], sig, 8.0 * sig, grid.L[d])
-            f.append(v / np.sqrt(2.0 * np.pi * sig * sig))
-        rho += spec["Z"][s] * (f[2][:, None, None] * f[1][None, :, None] * f[0][None, None, :])
+    """Starting density: the Gaussian ion charges band-limited to the FFT grid, clamped at 0, scaled to N_e.
+
+    rho_0(r) = max(Re sum_G rho_ion(G) e^{iG.r}, 0) * N_e / int(...).  (The paper does not state its
+    starting density; this reading costs one inverse FFT on either side.)
+    """
+    rho = np.maximum(np.real(np.fft.ifftn(rho_ion_G(grid, pos, species, spec))) * grid.npts, 0.0)
     ne = float(np.sum(spec["Z"][species]))
     return rho * (ne / (grid.dV * np.sum(rho)))
 

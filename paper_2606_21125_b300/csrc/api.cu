@@ -1,0 +1,755 @@
+// C ABI of the DC-DFT fragment solver: context lifecycle and the per-step pipeline.
+//
+// One SCF iteration (Sec. 2.2): V_eff[rho_in] -> per-fragment potential and spectral bounds ->
+// n_pass CheFSI passes on all fragments at once -> core weights, mu, rho_out (Eqs. 2-4) ->
+// energies -> linear mixing.  Every stage is a kernel on the caller's stream; the only host round
+// trip is the final copy of the step statistics.
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+
+#include "dc_internal.h"
+
+namespace {
+thread_local std::string g_last_error = "";
+}
+
+void dc_set_error(const std::string &msg) { g_last_error = msg; }
+
+int dc_cuda_status(cudaError_t e, const char *what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return DC_ERR_OOM;
+  }
+  return DC_ERR_CUDA;
+}
+
+namespace {
+
+template <typename T>
+int dmalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  const cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return dc_cuda_status(e, "cudaMalloc");
+  }
+  return DC_OK;
+}
+
+template <typename T>
+int upload(T **p, const std::vector<T> &v) {
+  DC_TRY(dmalloc(p, v.size()));
+  if (!v.empty()) DC_CUDA(cudaMemcpy(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return DC_OK;
+}
+
+void free_ctx(dc_ctx *c) {
+  if (!c) return;
+  void *ptrs[] = {c->d_desc, c->d_items, c->d_idx_map, c->d_owner, c->d_core_local, c->d_slots, c->d_tab64,
+                  c->d_tab32, c->d_zl_beg, c->d_zl_items, c->d_atom_D, c->d_atom_pos, c->d_atom_species,
+                  c->d_species, c->d_cover_beg[0], c->d_cover_beg[1], c->d_cover_beg[2], c->d_cover[0],
+                  c->d_cover[1], c->d_cover[2], c->d_vion, c->d_rho0, c->d_veff, c->d_rho_out, c->d_work,
+                  c->d_rhoiG, c->d_cplx, c->d_vf64, c->d_vf32, c->blk[0], c->blk[1], c->blk[2], c->blk64[0],
+                  c->blk64[1], c->blk64[2], c->d_hy64, c->d_c64[0], c->d_c64[1], c->d_c32[0], c->d_c32[1],
+                  c->d_eps, c->d_q, c->d_occ, c->d_bounds, c->d_gram, c->d_gram_off, c->d_gram_nchunk, c->d_C64,
+                  c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
+                  c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
+                  c->d_dots};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  if (c->have_plan) cufftDestroy(c->plan_z2z);
+  cudaGetLastError();
+  delete c;
+}
+
+int check_flags(dc_ctx *c, cudaStream_t s) {
+  unsigned fl = 0;
+  DC_CUDA(cudaMemcpyAsync(&fl, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaStreamSynchronize(s));
+  if (fl) {
+    DC_CUDA(cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), s));
+    DC_CUDA(cudaStreamSynchronize(s));
+    if (fl & DC_FLAG_TIMEOUT) {
+      dc_set_error("a bounded device wait ran out (grid barrier)");
+      return DC_ERR_TIMEOUT;
+    }
+    if (fl & DC_FLAG_NOTSPD) {
+      dc_set_error("Gram matrix not positive definite in at least one fragment");
+      return DC_ERR_NOCONV;
+    }
+    if (fl & DC_FLAG_NONFINITE) {
+      dc_set_error("non-finite eigenvalue or chemical potential");
+      return DC_ERR_NONFINITE;
+    }
+  }
+  return DC_OK;
+}
+
+// Records a CUDA event pair around one stage launch on its stream when the profiler is on.
+struct StageScope {
+  dc_ctx *c;
+  cudaStream_t s;
+  int stage, nk, idx = -1;
+  double bytes;
+  StageScope(dc_ctx *c_, int stage_, cudaStream_t s_, double bytes_, int nk_)
+      : c(c_), s(s_), stage(stage_), nk(nk_), bytes(bytes_) {
+    if (c->prof_on && c->prof_used + 2 <= (int)c->prof_pool.size()) {
+      idx = c->prof_used;
+      c->prof_used += 2;
+      cudaEventRecord(c->prof_pool[idx], s);
+    }
+  }
+  ~StageScope() {
+    if (idx >= 0) {
+      cudaEventRecord(c->prof_pool[idx + 1], s);
+      c->prof_stage.push_back(stage);
+      c->prof_bytes.push_back(bytes);
+      c->prof_nk.push_back(nk);
+    }
+  }
+};
+
+double core_elems(const dc_ctx *c) {
+  double s = 0.0;
+  for (const auto &D : c->h_desc) s += (double)D.norb * D.c[0] * D.c[1] * D.c[2];
+  return s;
+}
+double proj_elems(const dc_ctx *c) {
+  double s = 0.0;
+  for (const auto &D : c->h_desc) s += (double)D.norb * D.natom;
+  return s;
+}
+
+template <typename T>
+T *cproj(dc_ctx *c, int k);
+template <>
+double *cproj<double>(dc_ctx *c, int k) { return c->d_c64[k]; }
+template <>
+float *cproj<float>(dc_ctx *c, int k) { return c->d_c32[k]; }
+
+// One CheFSI pass on the rotating blocks B (state in B[ib]); filter = false gives the plain
+// Rayleigh-Ritz of the current block.  Leaves the new state index in ib.
+template <typename T>
+int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
+  const int m = c->params.cheb_degree;
+  const double es = sizeof(T), blk = es * (double)c->layout.psi_elems, vfb = es * (double)c->layout.frag_points;
+  const double pj = es * proj_elems(c);
+  int cur = ib;
+  int cbuf = 0;
+  {
+    StageScope sc(c, DC_STAGE_PROJECT, s, blk + pj, 1);
+    DC_TRY(dck::launch_project<T>(c, B[cur], cproj<T>(c, 0), s));
+  }
+  if (filter) {
+    {
+      StageScope sc(c, DC_STAGE_SUBSPACE, s, 8.0 * c->layout.nstates, 1);
+      DC_TRY(dck::launch_bounds(c, 0, s));
+    }
+    int prev = -1;
+    for (int k = 0; k < m; ++k) {
+      int nxt = 0;
+      while (nxt == cur || nxt == prev) ++nxt;
+      StageScope sc(c, DC_STAGE_HPSI, s, (k > 0 ? 3.0 : 2.0) * blk + vfb + 2.0 * pj, 1);
+      DC_TRY(dck::launch_hstep<T>(c, HSTEP_CHEB, k, B[cur], prev >= 0 ? B[prev] : nullptr, B[nxt],
+                                  cproj<T>(c, cbuf), cproj<T>(c, cbuf ^ 1), nullptr, nullptr, nullptr, nullptr, s));
+      cbuf ^= 1;
+      prev = cur;
+      cur = nxt;
+    }
+  }
+  const int hy = (cur + 1) % 3;
+  {
+    StageScope sc(c, DC_STAGE_HPSI, s, 2.0 * blk + vfb + pj, 1);
+    DC_TRY(dck::launch_hstep<T>(c, HSTEP_HPSI, 0, B[cur], nullptr, B[hy], cproj<T>(c, cbuf), nullptr, nullptr,
+                                nullptr, nullptr, nullptr, s));
+  }
+  {
+    StageScope sc(c, DC_STAGE_GRAM, s, 2.0 * blk + 8.0 * c->gram_elems, 1);
+    DC_TRY(dck::launch_gram<T>(c, B[cur], B[hy], s));
+  }
+  {
+    StageScope sc(c, DC_STAGE_SUBSPACE, s, 8.0 * c->gram_elems, 1);
+    DC_TRY(dck::launch_subspace(c, sizeof(T) == 4 ? 32 : 64, s));
+  }
+  {
+    StageScope sc(c, DC_STAGE_ROTATE, s, 2.0 * blk, 1);
+    DC_TRY(dck::launch_rotate<T>(c, B[cur], B[hy], s));
+  }
+  ib = hy;
+  return DC_OK;
+}
+
+int pass_ctx(dc_ctx *c, bool filter, int npass, cudaStream_t s) {
+  for (int p = 0; p < npass; ++p) {
+    if (c->params.precision == DC_FP64) {
+      double *B[3] = {(double *)c->blk[0], (double *)c->blk[1], (double *)c->blk[2]};
+      DC_TRY(chefsi_pass<double>(c, B, c->ib_psi, filter, s));
+    } else {
+      float *B[3] = {(float *)c->blk[0], (float *)c->blk[1], (float *)c->blk[2]};
+      DC_TRY(chefsi_pass<float>(c, B, c->ib_psi, filter, s));
+    }
+  }
+  return DC_OK;
+}
+
+int density_stage(dc_ctx *c, double *rho, cudaStream_t s) {
+  const double es = c->params.precision == DC_FP64 ? 8.0 : 4.0;
+  StageScope sc(c, DC_STAGE_DENSITY, s, 2.0 * es * core_elems(c) + 8.0 * c->npts + 32.0 * c->layout.nstates, 3);
+  if (c->params.precision == DC_FP64) {
+    DC_TRY(dck::launch_core_weights<double>(c, (const double *)c->blk[c->ib_psi], s));
+    DC_TRY(dck::launch_fermi(c, s));
+    DC_TRY(dck::launch_density<double>(c, (const double *)c->blk[c->ib_psi], rho, s));
+  } else {
+    DC_TRY(dck::launch_core_weights<float>(c, (const float *)c->blk[c->ib_psi], s));
+    DC_TRY(dck::launch_fermi(c, s));
+    DC_TRY(dck::launch_density<float>(c, (const float *)c->blk[c->ib_psi], rho, s));
+  }
+  return DC_OK;
+}
+
+inline cudaStream_t S(void *p) { return reinterpret_cast<cudaStream_t>(p); }
+
+}  // namespace
+
+extern "C" {
+
+const char *dc_error_string(int status) {
+  switch (status) {
+    case DC_OK: return "DC_OK";
+    case DC_ERR_ARG: return "DC_ERR_ARG";
+    case DC_ERR_CUDA: return "DC_ERR_CUDA";
+    case DC_ERR_OOM: return "DC_ERR_OOM";
+    case DC_ERR_NOCONV: return "DC_ERR_NOCONV";
+    case DC_ERR_TIMEOUT: return "DC_ERR_TIMEOUT";
+    case DC_ERR_NONFINITE: return "DC_ERR_NONFINITE";
+    case DC_ERR_STATE: return "DC_ERR_STATE";
+    default: return "DC_ERR_UNKNOWN";
+  }
+}
+
+const char *dc_last_error(void) { return g_last_error.c_str(); }
+
+static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, const dc_buffers_t *buffers,
+                        const dc_atoms_t *atoms, const dc_params_t *params, dc_ctx *c) {
+  c->grid = *grid;
+  c->frag_cfg = *fragments;
+  c->buf_cfg = *buffers;
+  c->params = *params;
+  const dc_params_t &P = c->params;
+  if (P.precision < DC_FP64 || P.precision > DC_MIXED || P.cheb_degree < 1 || P.cheb_degree > 64 || P.n_pass < 1 ||
+      P.n_warmup < 0 || !(P.kT > 0.0) || !(P.mix_alpha > 0.0) || P.mix_alpha > 1.0 ||
+      (P.hxc != DC_HXC_NONE && P.hxc != DC_HXC_HARTREE_X)) {
+    dc_set_error("dc_init: invalid parameters");
+    return DC_ERR_ARG;
+  }
+  if (atoms->natom > 0 && (!atoms->pos || !atoms->species)) {
+    dc_set_error("dc_init: atoms->pos and atoms->species required");
+    return DC_ERR_ARG;
+  }
+  if (!atoms->Z || !atoms->sigma_loc || !atoms->sigma_proj || !atoms->D) {
+    dc_set_error("dc_init: species tables required");
+    return DC_ERR_ARG;
+  }
+  HostTables ht;
+  DC_TRY(dc_build_host(c, atoms, ht));
+  int dev = 0;
+  DC_CUDA(cudaGetDevice(&dev));
+  DC_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
+
+  const dc_layout_t &Lo = c->layout;
+  // maps and tables
+  DC_TRY(upload(&c->d_desc, c->h_desc));
+  DC_TRY(upload(&c->d_items, c->h_items));
+  DC_TRY(upload(&c->d_idx_map, c->h_idx_map));
+  DC_TRY(upload(&c->d_owner, c->h_owner));
+  DC_TRY(upload(&c->d_core_local, c->h_core_local));
+  DC_TRY(upload(&c->d_slots, ht.slots));
+  DC_TRY(upload(&c->d_tab64, ht.tab));
+  std::vector<float> tab32(ht.tab.begin(), ht.tab.end());
+  DC_TRY(upload(&c->d_tab32, tab32));
+  DC_TRY(upload(&c->d_zl_beg, ht.zl_beg));
+  DC_TRY(upload(&c->d_zl_items, ht.zl_items));
+  std::vector<double> Datom(c->natom), posv(c->h_pos);
+  for (int a = 0; a < c->natom; ++a) Datom[a] = c->h_Ds[c->h_species[a]];
+  DC_TRY(upload(&c->d_atom_D, Datom));
+  DC_TRY(upload(&c->d_atom_pos, posv));
+  DC_TRY(upload(&c->d_atom_species, c->h_species));
+  std::vector<double> spec;
+  for (auto *v : {&c->h_Zs, &c->h_sigloc, &c->h_sigproj, &c->h_Ds}) spec.insert(spec.end(), v->begin(), v->end());
+  DC_TRY(upload(&c->d_species, spec));
+  std::vector<int> Fn(c->frag_cfg.num_fragment, c->frag_cfg.num_fragment + 3);
+  DC_TRY(upload(&c->d_Fn, Fn));
+  for (int d = 0; d < 3; ++d) {
+    std::vector<int> beg;
+    std::vector<int2> items;
+    dc_build_cover(c, d, beg, items);
+    DC_TRY(upload(&c->d_cover_beg[d], beg));
+    DC_TRY(upload(&c->d_cover[d], items));
+  }
+  // per-atom slot lists (for dE/dD), fixed order by fragment
+  {
+    std::vector<std::vector<int>> per(c->natom);
+    for (int f = 0; f < c->nfrag; ++f)
+      for (int k = 0; k < c->h_desc[f].natom; ++k) per[c->h_atoms[c->h_desc[f].at_off + k]].push_back(c->h_desc[f].at_off + k);
+    std::vector<int> beg(c->natom + 1, 0), sl;
+    for (int a = 0; a < c->natom; ++a) {
+      beg[a] = (int)sl.size();
+      sl.insert(sl.end(), per[a].begin(), per[a].end());
+    }
+    beg[c->natom] = (int)sl.size();
+    DC_TRY(upload(&c->d_atom_slot_beg, beg));
+    DC_TRY(upload(&c->d_atom_slots, sl));
+  }
+  // work lists for the Gram and rotation kernels
+  {
+    c->gram_chunk = 2048;
+    std::vector<int2> gi, ri;
+    std::vector<long long> goff(c->nfrag);
+    std::vector<int> gn(c->nfrag);
+    long long off = 0;
+    for (int f = 0; f < c->nfrag; ++f) {
+      const FragDesc &D = c->h_desc[f];
+      const long long Pf = (long long)D.E[0] * D.E[1] * D.E[2];
+      const int nch = (int)((Pf + c->gram_chunk - 1) / c->gram_chunk);
+      gn[f] = nch;
+      goff[f] = off;
+      off += (long long)nch * 2 * D.norb * D.norb;
+      for (int ch = 0; ch < nch; ++ch) gi.push_back(make_int2(f, ch));
+      const int nr = (int)((Pf + 127) / 128);
+      for (int ch = 0; ch < nr; ++ch) ri.push_back(make_int2(f, ch));
+    }
+    c->gram_elems = off;
+    c->n_gram_items = (int)gi.size();
+    c->n_rot_items = (int)ri.size();
+    DC_TRY(upload(&c->d_gram_items, gi));
+    DC_TRY(upload(&c->d_rot_items, ri));
+    DC_TRY(upload(&c->d_gram_off, goff));
+    DC_TRY(upload(&c->d_gram_nchunk, gn));
+    DC_TRY(dmalloc(&c->d_gram, (size_t)off));
+  }
+  // global grid arrays
+  const size_t N = (size_t)c->npts;
+  DC_TRY(dmalloc(&c->d_vion, N));
+  DC_TRY(dmalloc(&c->d_rho0, N));
+  DC_TRY(dmalloc(&c->d_veff, N));
+  DC_TRY(dmalloc(&c->d_rho_out, N));
+  DC_TRY(dmalloc(&c->d_work, N));
+  DC_TRY(dmalloc(&c->d_rhoiG, N));
+  DC_TRY(dmalloc(&c->d_cplx, N));
+  if (cufftPlan3d(&c->plan_z2z, c->grid.n[2], c->grid.n[1], c->grid.n[0], CUFFT_Z2Z) != CUFFT_SUCCESS) {
+    dc_set_error("cufftPlan3d failed");
+    return DC_ERR_CUDA;
+  }
+  c->have_plan = true;
+  // fragment-point and per-state arrays
+  DC_TRY(dmalloc(&c->d_vf64, (size_t)Lo.frag_points));
+  DC_TRY(dmalloc(&c->d_vf32, (size_t)Lo.frag_points));
+  long long cn = 0;
+  for (auto &D : c->h_desc) cn += (long long)D.natom * D.norb;
+  for (int k = 0; k < 2; ++k) {
+    DC_TRY(dmalloc(&c->d_c64[k], (size_t)cn));
+    DC_TRY(dmalloc(&c->d_c32[k], (size_t)cn));
+  }
+  long long sub = 0;
+  for (auto &D : c->h_desc) sub += (long long)D.norb * D.norb;
+  DC_TRY(dmalloc(&c->d_C64, (size_t)sub));
+  DC_TRY(dmalloc(&c->d_C32, (size_t)sub));
+  DC_TRY(dmalloc(&c->d_eps, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_q, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_occ, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_dots, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_bounds, (size_t)c->nfrag * (4 + 2 * P.cheb_degree)));
+  DC_CUDA(cudaMemset(c->d_bounds, 0, sizeof(double) * (size_t)c->nfrag * (4 + 2 * P.cheb_degree)));
+  DC_TRY(dmalloc(&c->d_flags, 8));
+  DC_CUDA(cudaMemset(c->d_flags, 0, 8 * sizeof(unsigned)));
+  DC_TRY(dmalloc(&c->d_scalar, 16));
+  DC_CUDA(cudaMemset(c->d_scalar, 0, 16 * sizeof(double)));
+  c->n_partials = 4096;
+  DC_TRY(dmalloc(&c->d_partials, (size_t)c->n_partials));
+  DC_TRY(dmalloc(&c->d_slot_w, (size_t)std::max<long long>(1, Lo.natom_frag)));
+  DC_CUDA(cudaMallocHost((void **)&c->h_scalar_pinned, 16 * sizeof(double)));
+  // orbital blocks
+  const size_t eb = (size_t)Lo.element_bytes;
+  for (int k = 0; k < 3; ++k) {
+    const cudaError_t e = cudaMalloc(&c->blk[k], eb * (size_t)Lo.psi_elems);
+    if (e != cudaSuccess) {
+      c->blk[k] = nullptr;
+      return dc_cuda_status(e, "cudaMalloc(orbital block)");
+    }
+  }
+  // ionic potential, starting density, starting orbitals
+  cudaStream_t s = 0;
+  DC_TRY(dck::launch_vion(c, s));
+  if (P.precision == DC_FP64) {
+    DC_TRY(dck::launch_init_psi(c, (double *)c->blk[0], s));
+  } else {
+    double *tmp = nullptr;
+    DC_TRY(dmalloc(&tmp, (size_t)Lo.psi_elems));
+    int st = dck::launch_init_psi(c, tmp, s);
+    if (st == DC_OK) st = dck::launch_convert(tmp, (float *)c->blk[0], Lo.psi_elems, s);
+    cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    DC_TRY(st);
+  }
+  c->ib_psi = 0;
+  DC_CUDA(cudaMemcpy(c->d_veff, c->d_vion, sizeof(double) * N, cudaMemcpyDeviceToDevice));
+  DC_TRY(dck::launch_gather(c, s));
+  DC_CUDA(cudaDeviceSynchronize());
+  return check_flags(c, s);
+}
+
+int dc_init(const dc_grid_t *grid, const dc_fragments_t *fragments, const dc_buffers_t *buffers,
+            const dc_atoms_t *atoms, const dc_params_t *params, dc_ctx **out) {
+  if (!out) {
+    dc_set_error("dc_init: out is NULL");
+    return DC_ERR_ARG;
+  }
+  *out = nullptr;
+  if (!grid || !fragments || !buffers || !atoms || !params) {
+    dc_set_error("dc_init: NULL argument");
+    return DC_ERR_ARG;
+  }
+  dc_ctx *c = new (std::nothrow) dc_ctx();
+  if (!c) {
+    dc_set_error("dc_init: host allocation failed");
+    return DC_ERR_OOM;
+  }
+  int st;
+  try {
+    st = dc_init_impl(grid, fragments, buffers, atoms, params, c);
+  } catch (...) {
+    dc_set_error("dc_init: host exception (out of memory?)");
+    st = DC_ERR_OOM;
+  }
+  if (st != DC_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return DC_OK;
+}
+
+void dc_finalize(dc_ctx *ctx) { free_ctx(ctx); }
+
+int dc_query(const dc_ctx *ctx, dc_layout_t *out) {
+  if (!ctx || !out) {
+    dc_set_error("dc_query: NULL argument");
+    return DC_ERR_ARG;
+  }
+  *out = ctx->layout;
+  return DC_OK;
+}
+
+int dc_get_maps(const dc_ctx *c, int32_t *h_frag, int32_t *h_idx_map, int32_t *h_owner, int32_t *h_core_local,
+                int32_t *h_atoms) {
+  if (!c) {
+    dc_set_error("dc_get_maps: NULL context");
+    return DC_ERR_ARG;
+  }
+  if (h_frag)
+    for (int f = 0; f < c->nfrag; ++f) {
+      const FragDesc &D = c->h_desc[f];
+      int32_t *o = h_frag + 12 * f;
+      for (int d = 0; d < 3; ++d) {
+        o[d] = D.org[d];
+        o[3 + d] = D.E[d];
+        o[6 + d] = D.c[d];
+      }
+      o[9] = D.norb;
+      o[10] = D.natom;
+      o[11] = 0;
+    }
+  if (h_idx_map) memcpy(h_idx_map, c->h_idx_map.data(), sizeof(int32_t) * c->h_idx_map.size());
+  if (h_owner) memcpy(h_owner, c->h_owner.data(), sizeof(int32_t) * c->h_owner.size());
+  if (h_core_local) memcpy(h_core_local, c->h_core_local.data(), sizeof(int32_t) * c->h_core_local.size());
+  if (h_atoms) memcpy(h_atoms, c->h_atoms.data(), sizeof(int32_t) * c->h_atoms.size());
+  return DC_OK;
+}
+
+int dc_get_initial(dc_ctx *c, double *d_vion, double *d_rho0, void *stream) {
+  if (!c) return DC_ERR_ARG;
+  const size_t N = (size_t)c->npts;
+  if (d_vion) DC_CUDA(cudaMemcpyAsync(d_vion, c->d_vion, N * 8, cudaMemcpyDeviceToDevice, S(stream)));
+  if (d_rho0) DC_CUDA(cudaMemcpyAsync(d_rho0, c->d_rho0, N * 8, cudaMemcpyDeviceToDevice, S(stream)));
+  return DC_OK;
+}
+
+int dc_potential(dc_ctx *c, const double *d_rho, double *d_veff, void *stream) {
+  if (!c || !d_rho) {
+    dc_set_error("dc_potential: NULL argument");
+    return DC_ERR_ARG;
+  }
+  DC_TRY(dck::launch_potential(c, d_rho, S(stream)));
+  DC_TRY(dck::launch_gather(c, S(stream)));
+  if (d_veff) DC_CUDA(cudaMemcpyAsync(d_veff, c->d_veff, 8 * (size_t)c->npts, cudaMemcpyDeviceToDevice, S(stream)));
+  return DC_OK;
+}
+
+int dc_set_potential(dc_ctx *c, const double *d_veff, void *stream) {
+  if (!c || !d_veff) {
+    dc_set_error("dc_set_potential: NULL argument");
+    return DC_ERR_ARG;
+  }
+  DC_CUDA(cudaMemcpyAsync(c->d_veff, d_veff, 8 * (size_t)c->npts, cudaMemcpyDeviceToDevice, S(stream)));
+  DC_TRY(dck::launch_gather(c, S(stream)));
+  return DC_OK;
+}
+
+int dc_hpsi(dc_ctx *c, const void *d_psi, void *d_hpsi, int dtype, void *stream) {
+  if (!c || !d_psi || !d_hpsi || (dtype != DC_FP64 && dtype != DC_FP32)) {
+    dc_set_error("dc_hpsi: invalid argument");
+    return DC_ERR_ARG;
+  }
+  const double es = dtype == DC_FP64 ? 8.0 : 4.0, blk = es * (double)c->layout.psi_elems;
+  const double vfb = es * (double)c->layout.frag_points, pj = es * proj_elems(c);
+  if (dtype == DC_FP64) {
+    {
+      StageScope sc(c, DC_STAGE_PROJECT, S(stream), blk + pj, 1);
+      DC_TRY(dck::launch_project<double>(c, (const double *)d_psi, c->d_c64[0], S(stream)));
+    }
+    StageScope sc(c, DC_STAGE_HPSI, S(stream), 2.0 * blk + vfb + pj, 1);
+    DC_TRY(dck::launch_hstep<double>(c, HSTEP_HPSI, 0, (const double *)d_psi, nullptr, (double *)d_hpsi, c->d_c64[0],
+                                     nullptr, nullptr, nullptr, nullptr, nullptr, S(stream)));
+  } else {
+    {
+      StageScope sc(c, DC_STAGE_PROJECT, S(stream), blk + pj, 1);
+      DC_TRY(dck::launch_project<float>(c, (const float *)d_psi, c->d_c32[0], S(stream)));
+    }
+    StageScope sc(c, DC_STAGE_HPSI, S(stream), 2.0 * blk + vfb + pj, 1);
+    DC_TRY(dck::launch_hstep<float>(c, HSTEP_HPSI, 0, (const float *)d_psi, nullptr, (float *)d_hpsi, c->d_c32[0],
+                                    nullptr, nullptr, nullptr, nullptr, nullptr, S(stream)));
+  }
+  return DC_OK;
+}
+
+int dc_subspace(dc_ctx *c, void *stream) {
+  if (!c) return DC_ERR_ARG;
+  DC_TRY(pass_ctx(c, false, 1, S(stream)));
+  return check_flags(c, S(stream));
+}
+
+int dc_chefsi(dc_ctx *c, int n_pass, void *stream) {
+  if (!c || n_pass < 0) {
+    dc_set_error("dc_chefsi: invalid argument");
+    return DC_ERR_ARG;
+  }
+  DC_TRY(pass_ctx(c, true, n_pass, S(stream)));
+  return check_flags(c, S(stream));
+}
+
+int dc_warmup(dc_ctx *c, void *stream) {
+  if (!c) return DC_ERR_ARG;
+  cudaStream_t s = S(stream);
+  DC_TRY(dck::launch_potential(c, c->d_rho0, s));
+  DC_TRY(dck::launch_gather(c, s));
+  if (c->params.precision == DC_FP64) {
+    DC_TRY(dck::launch_init_psi(c, (double *)c->blk[0], s));
+    c->ib_psi = 0;
+    DC_TRY(pass_ctx(c, false, 1, s));
+    DC_TRY(check_flags(c, s));
+    DC_TRY(pass_ctx(c, true, c->params.n_warmup, s));
+  } else {
+    // FP64 blocks for the warm-up, then convert the state to FP32
+    const size_t ne = (size_t)c->layout.psi_elems;
+    for (int k = 0; k < 3; ++k) DC_TRY(dmalloc(&c->blk64[k], ne));
+    int ib = 0;
+    int st = dck::launch_init_psi(c, c->blk64[0], s);
+    if (st == DC_OK) st = chefsi_pass<double>(c, c->blk64, ib, false, s);
+    if (st == DC_OK) st = check_flags(c, s);
+    for (int p = 0; st == DC_OK && p < c->params.n_warmup; ++p) st = chefsi_pass<double>(c, c->blk64, ib, true, s);
+    if (st == DC_OK) st = dck::launch_convert(c->blk64[ib], (float *)c->blk[0], (long long)ne, s);
+    cudaStreamSynchronize(s);
+    for (int k = 0; k < 3; ++k) {
+      cudaFree(c->blk64[k]);
+      c->blk64[k] = nullptr;
+    }
+    DC_TRY(st);
+    c->ib_psi = 0;
+  }
+  DC_TRY(check_flags(c, s));
+  c->warmed = true;
+  c->steps_done = 0;
+  return DC_OK;
+}
+
+int dc_get_state(dc_ctx *c, void *d_psi, double *d_eps, void *stream) {
+  if (!c) return DC_ERR_ARG;
+  if (d_psi)
+    DC_CUDA(cudaMemcpyAsync(d_psi, c->blk[c->ib_psi], (size_t)c->layout.element_bytes * c->layout.psi_elems,
+                            cudaMemcpyDeviceToDevice, S(stream)));
+  if (d_eps) DC_CUDA(cudaMemcpyAsync(d_eps, c->d_eps, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, S(stream)));
+  return DC_OK;
+}
+
+int dc_set_state(dc_ctx *c, const void *d_psi, const double *d_eps, void *stream) {
+  if (!c) return DC_ERR_ARG;
+  if (d_psi)
+    DC_CUDA(cudaMemcpyAsync(c->blk[c->ib_psi], d_psi, (size_t)c->layout.element_bytes * c->layout.psi_elems,
+                            cudaMemcpyDeviceToDevice, S(stream)));
+  if (d_eps) DC_CUDA(cudaMemcpyAsync(c->d_eps, d_eps, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, S(stream)));
+  c->warmed = true;
+  return DC_OK;
+}
+
+int dc_density(dc_ctx *c, double *d_rho, double *d_q, double *d_mu, void *stream) {
+  if (!c || !d_rho) {
+    dc_set_error("dc_density: NULL argument");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  DC_TRY(density_stage(c, d_rho, s));
+  if (d_q) DC_CUDA(cudaMemcpyAsync(d_q, c->d_q, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, s));
+  if (d_mu) DC_CUDA(cudaMemcpyAsync(d_mu, c->d_scalar, 8, cudaMemcpyDeviceToDevice, s));
+  return check_flags(c, s);
+}
+
+int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, void *stream) {
+  if (!c || !rho) {
+    dc_set_error("dc_scf_step: NULL argument");
+    return DC_ERR_ARG;
+  }
+  if (!c->warmed) {
+    dc_set_error("dc_scf_step: call dc_warmup (or dc_set_state) first");
+    return DC_ERR_STATE;
+  }
+  cudaStream_t s = S(stream);
+  const size_t nb = 8 * (size_t)c->npts;
+  double *rin = rho;
+  if (rho_on_host) {
+    DC_CUDA(cudaMemcpyAsync(c->d_work, rho, nb, cudaMemcpyHostToDevice, s));
+    rin = c->d_work;
+  }
+  const double N8 = 8.0 * (double)c->npts;
+  {
+    StageScope sc(c, DC_STAGE_POTENTIAL, s, 7.0 * N8, 3);
+    DC_TRY(dck::launch_potential(c, rin, s));
+  }
+  {
+    StageScope sc(c, DC_STAGE_GATHER, s, 24.0 * (double)c->layout.frag_points, 1);
+    DC_TRY(dck::launch_gather(c, s));
+  }
+  DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
+  DC_TRY(density_stage(c, c->d_rho_out, s));
+  {
+    StageScope sc(c, DC_STAGE_ENERGY, s, 13.0 * N8, 17);
+    DC_TRY(dck::launch_energy(c, rin, s));
+    DC_TRY(dck::launch_mix(c, rin, s));
+  }
+  if (rho_on_host) DC_CUDA(cudaMemcpyAsync(rho, c->d_work, nb, cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned, c->d_scalar, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const int st = check_flags(c, s);
+  c->steps_done++;
+  if (h_stats) {
+    const double *v = c->h_scalar_pinned;
+    h_stats->mu = v[0];
+    h_stats->eband = v[1];
+    h_stats->drho = v[5];
+    h_stats->ne = v[6];
+    h_stats->E = v[8];
+    h_stats->F = v[9];
+    h_stats->step = c->steps_done;
+    h_stats->status = st;
+  }
+  if (st != DC_OK) return st;
+  const double *v = c->h_scalar_pinned;
+  if (!(v[8] == v[8]) || !(v[0] == v[0]) || v[8] - v[8] != 0.0) {
+    dc_set_error("dc_scf_step: non-finite energy or mu");
+    return DC_ERR_NONFINITE;
+  }
+  return DC_OK;
+}
+
+int dc_get_rho_out(dc_ctx *c, double *d_rho, void *stream) {
+  if (!c || !d_rho) return DC_ERR_ARG;
+  DC_CUDA(cudaMemcpyAsync(d_rho, c->d_rho_out, 8 * (size_t)c->npts, cudaMemcpyDeviceToDevice, S(stream)));
+  return DC_OK;
+}
+
+int dc_eb_adjoint(dc_ctx *c, const void *d_psi, int dtype, const double *d_occ, const double *d_V, const double *d_D,
+                  double *h_Eb, void *d_dpsi, double *d_dV, double *d_dD, void *stream) {
+  if (!c || !d_psi || !d_occ || !d_V || !d_D || (dtype != DC_FP64 && dtype != DC_FP32)) {
+    dc_set_error("dc_eb_adjoint: invalid argument");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  if (!c->d_adj_vf64) {
+    DC_TRY(dmalloc(&c->d_adj_vf64, (size_t)c->layout.frag_points));
+    DC_TRY(dmalloc(&c->d_adj_vf32, (size_t)c->layout.frag_points));
+    DC_TRY(dmalloc(&c->d_adj_fd, (size_t)c->layout.frag_points));
+  }
+  DC_TRY(dck::launch_gather_plain(c, d_V, c->d_adj_vf64, c->d_adj_vf32, s));
+  if (dtype == DC_FP64) {
+    const double *psi = (const double *)d_psi;
+    DC_TRY(dck::launch_project<double>(c, psi, c->d_c64[0], s));
+    DC_TRY(dck::launch_hstep<double>(c, HSTEP_ADJ, 0, psi, nullptr, (double *)d_dpsi, c->d_c64[0], nullptr, d_D, d_occ,
+                                     c->d_dots, c->d_adj_vf64, s));
+    if (d_dV) {
+      DC_TRY(dck::launch_frag_density<double>(c, psi, d_occ, c->d_adj_fd, s));
+      DC_TRY(dck::launch_gather_dV(c, c->d_adj_fd, d_dV, s));
+    }
+    if (d_dD) DC_TRY(dck::launch_dD(c, c->d_c64[0], nullptr, d_occ, d_dD, s));
+  } else {
+    const float *psi = (const float *)d_psi;
+    DC_TRY(dck::launch_project<float>(c, psi, c->d_c32[0], s));
+    DC_TRY(dck::launch_hstep<float>(c, HSTEP_ADJ, 0, psi, nullptr, (float *)d_dpsi, c->d_c32[0], nullptr, d_D, d_occ,
+                                    c->d_dots, c->d_adj_vf32, s));
+    if (d_dV) {
+      DC_TRY(dck::launch_frag_density<float>(c, psi, d_occ, c->d_adj_fd, s));
+      DC_TRY(dck::launch_gather_dV(c, c->d_adj_fd, d_dV, s));
+    }
+    if (d_dD) DC_TRY(dck::launch_dD(c, nullptr, c->d_c32[0], d_occ, d_dD, s));
+  }
+  if (h_Eb) {
+    DC_TRY(dck::launch_sum(c->d_dots, c->layout.nstates, c->d_scalar + 14, c->d_partials, 0, s));
+    DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned + 14, c->d_scalar + 14, 8, cudaMemcpyDeviceToHost, s));
+    DC_CUDA(cudaStreamSynchronize(s));
+    *h_Eb = c->h_scalar_pinned[14];
+  }
+  return DC_OK;
+}
+
+int dc_profile(dc_ctx *c, int enable) {
+  if (!c) return DC_ERR_ARG;
+  if (enable) {
+    if (c->prof_pool.empty()) {
+      c->prof_pool.resize(8192);
+      for (auto &e : c->prof_pool) DC_CUDA(cudaEventCreate(&e));
+    }
+    c->prof_used = 0;
+    c->prof_stage.clear();
+    c->prof_bytes.clear();
+    c->prof_nk.clear();
+  }
+  c->prof_on = enable != 0;
+  return DC_OK;
+}
+
+int dc_profile_read(dc_ctx *c, double *h_ms, int64_t *h_launches, double *h_bytes) {
+  if (!c) return DC_ERR_ARG;
+  DC_CUDA(cudaDeviceSynchronize());
+  double ms[DC_NSTAGES] = {0}, by[DC_NSTAGES] = {0};
+  int64_t nl[DC_NSTAGES] = {0};
+  for (size_t k = 0; k < c->prof_stage.size(); ++k) {
+    float t = 0.f;
+    DC_CUDA(cudaEventElapsedTime(&t, c->prof_pool[2 * k], c->prof_pool[2 * k + 1]));
+    const int st = c->prof_stage[k];
+    ms[st] += t;
+    by[st] += c->prof_bytes[k];
+    nl[st] += c->prof_nk[k];
+  }
+  for (int i = 0; i < DC_NSTAGES; ++i) {
+    if (h_ms) h_ms[i] = ms[i];
+    if (h_bytes) h_bytes[i] = by[i];
+    if (h_launches) h_launches[i] = nl[i];
+  }
+  return DC_OK;
+}
+
+}  // extern "C"

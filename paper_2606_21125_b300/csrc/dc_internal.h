@@ -1,0 +1,234 @@
+// Internal declarations of the DC-DFT fragment solver (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dcdft.h"
+
+// ---------------------------------------------------------------------------------------------
+// Fragment descriptor, one per fragment, resident on the device.
+// ---------------------------------------------------------------------------------------------
+struct FragDesc {
+  int E[3];      // extent (core + 2b) per axis
+  int b[3];      // buffer thickness = first core index in local coordinates
+  int c[3];      // core length per axis
+  int org[3];    // global index of local 0 (s_k - b, may be negative)
+  int norb;      // n_f
+  int natom;     // |A_f|
+  int st_off;    // offset of the fragment's states in per-state arrays
+  int at_off;    // offset of the fragment's atoms in per-(f,k) arrays
+  long long psi_off;  // element offset of the fragment's orbital block
+  long long pt_off;   // offset of the fragment's points in per-point arrays
+  long long tab_off;  // offset of the fragment's projector factors (A_f * (Ex+Ey+Ez) values)
+  long long c_off;    // offset of the fragment's projections (n_f * A_f values, orbital-major)
+  long long sub_off;  // offset of the fragment's n_f x n_f matrices
+  int zl_off;         // offset into the per-plane atom list starts (Ez + 1 entries)
+  int pad;
+};
+
+// Per-(fragment, atom slot) projector data.
+struct ProjSlot {
+  int atom;       // global atom index
+  int lo[3];      // support [lo, hi) of the 1-D factor on each local axis
+  int hi[3];
+  double coef;    // (pi sigma^2)^(-3/4)
+};
+
+#define DC_MAX_NORB 64     // subspace kernels hold n x n FP64 matrices in shared memory
+#define DC_MAX_EXTENT 64   // stencil kernels hold padded planes of (E+8)^2 points
+
+// Bounded device waits: number of polls before a wait gives up and sets the error flag.
+#define DC_SPIN_LIMIT (1u << 22)
+
+// Device-side error flags (bit set in ctx->d_flags[0]).
+#define DC_FLAG_NOTSPD 1u
+#define DC_FLAG_TIMEOUT 2u
+#define DC_FLAG_NONFINITE 4u
+
+struct dc_ctx {
+  // configuration
+  dc_grid_t grid;
+  dc_fragments_t frag_cfg;
+  dc_buffers_t buf_cfg;
+  dc_params_t params;
+  double h[3], dV, volume, ne;
+  int natom, nspecies, nfrag;
+  long long npts;
+  dc_layout_t layout;
+  int max_E[3];
+  int max_atoms;      // max |A_f|
+  int max_zlist;      // max over f of total per-plane list length
+
+  // host copies of maps (for dc_get_maps and launch planning)
+  std::vector<FragDesc> h_desc;
+  std::vector<int32_t> h_idx_map, h_owner, h_core_local, h_atoms;
+  std::vector<double> h_pos, h_Zs, h_sigloc, h_sigproj, h_Ds;
+  std::vector<int> h_species;
+  std::vector<int2> h_items;  // (f, i) per state
+
+  // device maps and tables
+  FragDesc *d_desc = nullptr;
+  int2 *d_items = nullptr;
+  int32_t *d_idx_map = nullptr, *d_owner = nullptr, *d_core_local = nullptr;
+  ProjSlot *d_slots = nullptr;
+  double *d_tab64 = nullptr;   // projector 1-D factors (FP64)
+  float *d_tab32 = nullptr;    // same in FP32
+  int *d_zl_beg = nullptr;     // per-plane atom list starts
+  int *d_zl_items = nullptr;   // per-plane atom slots
+  double *d_atom_D = nullptr;  // D per atom (global index)
+  double *d_atom_pos = nullptr;
+  int *d_atom_species = nullptr;
+  double *d_species = nullptr;  // [4][nspecies]: Z, sigma_loc, sigma_proj, D
+  // cover lists for the deterministic gather of dE/dV: per axis and global coordinate the
+  // (fragment index along the axis, local index) pairs that cover it
+  int *d_cover_beg[3] = {nullptr, nullptr, nullptr};
+  int2 *d_cover[3] = {nullptr, nullptr, nullptr};
+
+  // global grid arrays (FP64)
+  double *d_vion = nullptr, *d_rho0 = nullptr, *d_veff = nullptr, *d_rho_out = nullptr, *d_work = nullptr;
+  double2 *d_rhoiG = nullptr;  // rho_ion(G), full complex grid
+  double2 *d_cplx = nullptr;   // FFT work (full complex grid)
+  cufftHandle plan_z2z = 0;
+  bool have_plan = false;
+
+  // per-fragment-point potential
+  double *d_vf64 = nullptr;
+  float *d_vf32 = nullptr;
+
+  // orbital blocks: 3 rotating blocks of the context precision (index of the state in ib_psi)
+  void *blk[3] = {nullptr, nullptr, nullptr};
+  int ib_psi = 0;
+  // FP64 blocks used by the warm-up of FP32/mixed contexts (freed after warm-up)
+  double *blk64[3] = {nullptr, nullptr, nullptr};
+  double *d_hy64 = nullptr;  // scratch for mixed (unused in FP64)
+
+  // projections (n_f * A_f per fragment), two buffers (input / output of a step)
+  double *d_c64[2] = {nullptr, nullptr};
+  float *d_c32[2] = {nullptr, nullptr};
+
+  // subspace arrays
+  double *d_eps = nullptr;      // Ritz values [nstates]
+  double *d_q = nullptr;        // core weights [nstates]
+  double *d_occ = nullptr;      // occupations f [nstates]
+  double *d_bounds = nullptr;   // per fragment: a, b_up, aL, shift, then 2*m step coefficients
+  double *d_gram = nullptr;     // Gram partials [nchunk][2 n^2] per fragment
+  long long gram_elems = 0;
+  int gram_chunk = 0;           // points per Gram chunk
+  long long *d_gram_off = nullptr;   // per fragment offset into d_gram
+  int *d_gram_nchunk = nullptr;      // per fragment chunk count
+  double *d_C64 = nullptr;      // rotation matrices [sub] (FP64)
+  float *d_C32 = nullptr;       // same in FP32
+  unsigned *d_flags = nullptr;  // device error flags
+  double *d_scalar = nullptr;   // [16] mu, energies, reductions
+  double *d_partials = nullptr; // reduction partials
+  int n_partials = 0;
+  double *h_scalar_pinned = nullptr;
+
+  // work lists
+  int2 *d_gram_items = nullptr;  // (fragment, chunk) of the Gram kernel
+  int n_gram_items = 0;
+  int2 *d_rot_items = nullptr;   // (fragment, 128-point chunk) of the rotation kernel
+  int n_rot_items = 0;
+  int *d_Fn = nullptr;           // num_fragment on the device
+  // adjoint data: per-atom lists of (fragment, slot) entries, scratch
+  int *d_atom_slot_beg = nullptr, *d_atom_slots = nullptr;
+  double *d_slot_w = nullptr;
+  double *d_adj_vf64 = nullptr;
+  float *d_adj_vf32 = nullptr;
+  double *d_adj_fd = nullptr;
+  double *d_dots = nullptr;
+
+  // stage profiler
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<int> prof_stage;       // stage of each recorded (start, end) pair
+  std::vector<double> prof_bytes;    // algorithmic bytes of each pair
+  std::vector<int> prof_nk;          // kernel launches of each pair
+  int prof_used = 0;                 // events used in the pool
+
+  int steps_done = 0;
+  bool warmed = false;
+  int sm_count = 0;
+};
+
+// Host-built projector tables, uploaded by dc_init.
+struct HostTables {
+  std::vector<ProjSlot> slots;
+  std::vector<double> tab;
+  std::vector<int> zl_beg, zl_items;
+};
+int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out);
+void dc_build_cover(const dc_ctx *c, int d, std::vector<int> &beg, std::vector<int2> &items);
+
+// ---------------------------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------------------------
+void dc_set_error(const std::string &msg);
+int dc_cuda_status(cudaError_t e, const char *what);
+
+#define DC_CUDA(call)                                          \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return dc_cuda_status(_e, #call);   \
+  } while (0)
+
+#define DC_TRY(call)              \
+  do {                            \
+    int _s = (call);              \
+    if (_s != DC_OK) return _s;   \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------------------
+namespace dck {
+// global stages
+int launch_vion(dc_ctx *c, cudaStream_t s);
+int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s);
+int launch_gather(dc_ctx *c, cudaStream_t s);
+int launch_gather_plain(dc_ctx *c, const double *V, double *vf64, float *vf32, cudaStream_t s);
+int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s);
+int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s);
+int launch_init_psi(dc_ctx *c, double *psi64, cudaStream_t s);
+int launch_convert(const double *src, float *dst, long long n, cudaStream_t s);
+int launch_convert(const float *src, double *dst, long long n, cudaStream_t s);
+
+// fragment Hamiltonian
+template <typename T>
+int launch_project(dc_ctx *c, const T *psi, T *cout, cudaStream_t s);
+template <typename T>
+int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T *yout, const T *cin, T *cout,
+                 const double *Datom, const double *occ, double *dots, const T *vf, cudaStream_t s);
+
+// subspace
+int launch_bounds(dc_ctx *c, int first, cudaStream_t s);
+template <typename T>
+int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s);
+int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s);
+template <typename T>
+int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s);
+
+// density
+template <typename T>
+int launch_core_weights(dc_ctx *c, const T *psi, cudaStream_t s);
+int launch_fermi(dc_ctx *c, cudaStream_t s);
+template <typename T>
+int launch_density(dc_ctx *c, const T *psi, double *rho, cudaStream_t s);
+
+// adjoint
+template <typename T>
+int launch_frag_density(dc_ctx *c, const T *psi, const double *occ, double *fd, cudaStream_t s);
+int launch_gather_dV(dc_ctx *c, const double *fd, double *dV, cudaStream_t s);
+int launch_dD(dc_ctx *c, const double *cproj64, const float *cproj32, const double *occ, double *dD, cudaStream_t s);
+int launch_sum(const double *x, long long n, double *out, double *partials, int npart, cudaStream_t s);
+}  // namespace dck
+
+// modes of launch_hstep
+#define HSTEP_HPSI 0  // out = H y
+#define HSTEP_CHEB 1  // out = alpha (H y - shift y) + beta yprev
+#define HSTEP_ADJ 2   // out = 2 occ dV H y ; dots[item] = occ dV <y|H y>

@@ -1,0 +1,213 @@
+// Density stage (Sec. 2.2, Eqs. 2-4): core weights, global chemical potential, occupations and the
+// core-projected density rho_tot(g) = sum_i 2 f_i^f psi_i^f(j)^2 with f = owner(g).
+#include "dc_internal.h"
+
+namespace {
+
+constexpr int QNT = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(QNT) k_core_weights(const FragDesc *desc, const int2 *items, const T *psi,
+                                                     double dV, double *q) {
+  __shared__ double red[QNT / 32];
+  const int2 it = items[blockIdx.x];
+  const FragDesc D = desc[it.x];
+  const int Ex = D.E[0], Ey = D.E[1];
+  const long long P = (long long)Ex * Ey * D.E[2];
+  const T *y = psi + D.psi_off + (long long)it.y * P;
+  const int cx = D.c[0], cy = D.c[1], cz = D.c[2];
+  const int ncore = cx * cy * cz;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < ncore; t += QNT) {
+    const int x = t % cx, yz = t / cx, yy = yz % cy, z = yz / cy;
+    const long long j = (x + D.b[0]) + (long long)Ex * ((yy + D.b[1]) + (long long)Ey * (z + D.b[2]));
+    const double v = (double)y[j];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < QNT / 32; ++w) tot += red[w];
+    q[D.st_off + it.y] = dV * tot;
+  }
+}
+
+// Grid-wide barrier for a cooperative launch.  The wait is bounded: after DC_SPIN_LIMIT polls the
+// block sets DC_FLAG_TIMEOUT and returns false, and the kernel then stops.
+__device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks, unsigned *flags) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = *((volatile unsigned *)gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u) + 1u;
+    if (arrived == nblocks) {
+      *((volatile unsigned *)count) = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned it = 0;
+      while (*((volatile unsigned *)gen) == g) {
+        if (++it > DC_SPIN_LIMIT) {
+          atomicOr(flags, DC_FLAG_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double fermi_occ(double e, double mu, double kT) {
+  return 0.5 * (1.0 - tanh(0.5 * (e - mu) / kT));
+}
+
+// FP64 bisection for mu (the bracket and stopping rule of the FP64 oracle), all blocks in step:
+// every block evaluates its share of sum 2 f q, the partial sums meet at a grid barrier and each
+// block adds them in the same fixed order, so all blocks take identical decisions.
+__global__ void __launch_bounds__(QNT) k_fermi(const double *eps, const double *q, int nst, double ne, double kT,
+                                              double *partials, unsigned *bar, unsigned *flags, double *mu_out,
+                                              double *occ) {
+  __shared__ double red[QNT / 32];
+  __shared__ double red2[QNT / 32];
+  const int nb = gridDim.x;
+  const int stride = nb * QNT;
+  const int base = blockIdx.x * QNT + threadIdx.x;
+  // global min / max of eps
+  double lo = 1e300, hi = -1e300;
+  for (int p = base; p < nst; p += stride) {
+    lo = fmin(lo, eps[p]);
+    hi = fmax(hi, eps[p]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = lo;
+    red2[threadIdx.x >> 5] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = red[0], b = red2[0];
+    for (int w = 1; w < QNT / 32; ++w) {
+      a = fmin(a, red[w]);
+      b = fmax(b, red2[w]);
+    }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+  if (!grid_sync(bar, bar + 1, nb, flags)) return;
+  // partial sums written by other blocks are read with L2-coherent loads (no stale L1 lines)
+  lo = __ldcg(&partials[0]);
+  hi = __ldcg(&partials[1]);
+  for (int b = 1; b < nb; ++b) {
+    lo = fmin(lo, __ldcg(&partials[2 * b]));
+    hi = fmax(hi, __ldcg(&partials[2 * b + 1]));
+  }
+  lo -= 40.0 * kT;
+  hi += 40.0 * kT;
+  double *pacc = partials + 2 * nb;  // [2][nb]
+  for (int itn = 0; itn < 200; ++itn) {
+    if (hi - lo < 1e-13) break;
+    const double mid = 0.5 * (lo + hi);
+    double s = 0.0;
+    for (int p = base; p < nst; p += stride) s += 2.0 * fermi_occ(eps[p], mid, kT) * q[p];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double *pa = pacc + (itn & 1) * nb;
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < QNT / 32; ++w) t += red[w];
+      pa[blockIdx.x] = t;
+    }
+    if (!grid_sync(bar, bar + 1, nb, flags)) return;
+    double tot = 0.0;
+    for (int b = 0; b < nb; ++b) tot += __ldcg(&pa[b]);
+    if (tot < ne) lo = mid;
+    else hi = mid;
+  }
+  const double mu = 0.5 * (lo + hi);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    mu_out[0] = mu;
+    if (!isfinite(mu)) atomicOr(flags, DC_FLAG_NONFINITE);
+  }
+  for (int p = base; p < nst; p += stride) occ[p] = fermi_occ(eps[p], mu, kT);
+}
+
+template <typename T>
+__global__ void k_density(const FragDesc *desc, const int32_t *owner, const int32_t *core_local, long long npts,
+                          const T *psi, const double *occ, double *rho) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= npts) return;
+  const FragDesc D = desc[owner[g]];
+  const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
+  const T *y = psi + D.psi_off + core_local[g];
+  const double *o = occ + D.st_off;
+  double s = 0.0;
+  for (int i = 0; i < D.norb; ++i) {
+    const double v = (double)y[(long long)i * P];
+    s += 2.0 * o[i] * v * v;
+  }
+  rho[g] = s;
+}
+
+}  // namespace
+
+namespace dck {
+
+template <typename T>
+int launch_core_weights(dc_ctx *c, const T *psi, cudaStream_t s) {
+  k_core_weights<T><<<(unsigned)c->layout.nstates, QNT, 0, s>>>(c->d_desc, c->d_items, psi, c->dV, c->d_q);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+int launch_fermi(dc_ctx *c, cudaStream_t s) {
+  int nb = 0;
+  DC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fermi, QNT, 0));
+  if (nb < 1) {
+    dc_set_error("fermi: kernel cannot be resident");
+    return DC_ERR_CUDA;
+  }
+  int grid = c->sm_count;  // one block per SM, all co-resident (cooperative launch checks it)
+  const int need = (int)((c->layout.nstates + QNT - 1) / QNT);
+  if (grid > need) grid = need > 0 ? need : 1;
+  DC_CUDA(cudaMemsetAsync(c->d_flags + 1, 0, 2 * sizeof(unsigned), s));
+  const double *eps = c->d_eps;
+  const double *q = c->d_q;
+  int nst = (int)c->layout.nstates;
+  double ne = c->ne, kT = c->params.kT;
+  double *partials = c->d_partials;
+  unsigned *bar = c->d_flags + 1;
+  unsigned *flags = c->d_flags;
+  double *mu = c->d_scalar;  // slot 0
+  double *occ = c->d_occ;
+  void *args[] = {&eps, &q, &nst, &ne, &kT, &partials, &bar, &flags, &mu, &occ};
+  DC_CUDA(cudaLaunchCooperativeKernel((const void *)k_fermi, dim3(grid), dim3(QNT), args, 0, s));
+  return DC_OK;
+}
+
+template <typename T>
+int launch_density(dc_ctx *c, const T *psi, double *rho, cudaStream_t s) {
+  const unsigned nb = (unsigned)((c->npts + 255) / 256);
+  k_density<T><<<nb, 256, 0, s>>>(c->d_desc, c->d_owner, c->d_core_local, c->npts, psi, c->d_occ, rho);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+template int launch_core_weights<double>(dc_ctx *, const double *, cudaStream_t);
+template int launch_core_weights<float>(dc_ctx *, const float *, cudaStream_t);
+template int launch_density<double>(dc_ctx *, const double *, double *, cudaStream_t);
+template int launch_density<float>(dc_ctx *, const float *, double *, cudaStream_t);
+
+}  // namespace dck

@@ -1,0 +1,484 @@
+// Subspace kernels of the fragment eigensolver (Eq. 1): filter bounds, Gram and Rayleigh-Ritz
+// contractions, FP64 Cholesky orthonormalisation and symmetric eigensolve, rotation.
+//
+// The paper's inner solver is "the same procedure as conventional DFT" (Sec. 2.2) and the
+// dominant costs are diagonalisation and orthonormalisation.  Here one pass is a scaled
+// Chebyshev filter (Zhou, Saad, Tiago & Chelikowsky, J. Comput. Phys. 219 (2006) 172) followed by
+// S = <Y|Y> = L L^T, Hs = L^-1 <Y|HY> L^-T = Q diag(eps) Q^T and Psi = Y L^-T Q.
+#include "dc_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Filter bounds and per-step coefficients (one thread per fragment)
+//   bounds[f] = {a, b_up, aL, c, alpha_0, beta_0, ..., alpha_{m-1}, beta_{m-1}}
+// b_up is written by the potential gather; a and aL come from the fragment's Ritz values.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_bounds(const FragDesc *desc, int nfrag, const double *eps, double *bounds, int m, int stride) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfrag) return;
+  const FragDesc D = desc[f];
+  double lo = eps[D.st_off], hi = eps[D.st_off];
+  for (int i = 1; i < D.norb; ++i) {
+    lo = fmin(lo, eps[D.st_off + i]);
+    hi = fmax(hi, eps[D.st_off + i]);
+  }
+  double *bd = bounds + (long long)f * stride;
+  const double a = hi, aL = lo, b = bd[1];
+  const double e = (b - a) / 2.0;
+  const double c = (b + a) / 2.0;
+  double sigma = e / (aL - c);
+  const double tau = 2.0 / sigma;
+  bd[0] = a;
+  bd[2] = aL;
+  bd[3] = c;
+  bd[4] = sigma / e;
+  bd[5] = 0.0;
+  for (int k = 1; k < m; ++k) {
+    const double sn = 1.0 / (tau - sigma);
+    bd[4 + 2 * k] = 2.0 * sn / e;
+    bd[5 + 2 * k] = -sigma * sn;
+    sigma = sn;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gram / Rayleigh-Ritz partial sums over a chunk of points: S_p = Y_c Y_c^T and A_p = Y_c (HY)_c^T
+// (no dV factor).  One CTA per (fragment, chunk); each of 256 threads owns a 4x4 tile of the
+// (padded) 64x64 outputs.  FP32 inputs: products of 32-point sub-tiles summed in FP32, then
+// accumulated as an unevaluated (hi, lo) FP32 pair (TwoSum); FP64 inputs: plain FP64.
+// ---------------------------------------------------------------------------------------------
+constexpr int GKT = 32;   // points per sub-tile
+constexpr int GPAD = 68;  // padded orbital stride in shared memory
+
+template <typename T>
+struct Vec4 {
+  T v[4];
+};
+__device__ __forceinline__ Vec4<float> ld4(const float *p) {
+  const float4 t = *reinterpret_cast<const float4 *>(p);
+  return {{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ Vec4<double> ld4(const double *p) {
+  const double2 a = *reinterpret_cast<const double2 *>(p);
+  const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+  return {{a.x, a.y, b.x, b.y}};
+}
+
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += err;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *gitems, const long long *goff,
+                                              int chunk, const T *Y, const T *HY, double *out) {
+  __shared__ __align__(16) T sY[GKT][GPAD];
+  __shared__ __align__(16) T sH[GKT][GPAD];
+  const int2 it = gitems[blockIdx.x];
+  const int f = it.x, ch = it.y;
+  const FragDesc D = desc[f];
+  const int n = D.norb;
+  const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
+  const long long p0 = (long long)ch * chunk;
+  const long long p1 = min(P, p0 + chunk);
+  const T *Yf = Y + D.psi_off;
+  const T *Hf = HY ? HY + D.psi_off : nullptr;
+  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  for (int t = threadIdx.x; t < GKT * GPAD; t += 256) {
+    (&sY[0][0])[t] = T(0);
+    (&sH[0][0])[t] = T(0);
+  }
+  float shi[16], slo[16], ahi[16], alo[16];
+  double sd[16], ad[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    shi[e] = slo[e] = ahi[e] = alo[e] = 0.f;
+    sd[e] = ad[e] = 0.0;
+  }
+  __syncthreads();
+  for (long long pb = p0; pb < p1; pb += GKT) {
+    for (int t = threadIdx.x; t < GKT * n; t += 256) {
+      const int r = t / GKT, p = t - r * GKT;
+      const long long pp = pb + p;
+      sY[p][r] = pp < p1 ? Yf[(long long)r * P + pp] : T(0);
+      if (Hf) sH[p][r] = pp < p1 ? Hf[(long long)r * P + pp] : T(0);
+    }
+    __syncthreads();
+    T ps[16], pa[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) ps[e] = pa[e] = T(0);
+#pragma unroll 4
+    for (int p = 0; p < GKT; ++p) {
+      const Vec4<T> a = ld4(&sY[p][4 * ti]);
+      const Vec4<T> b = ld4(&sY[p][4 * tj]);
+      const Vec4<T> h = ld4(&sH[p][4 * tj]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          ps[4 * r + cc] += a.v[r] * b.v[cc];
+          pa[4 * r + cc] += a.v[r] * h.v[cc];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if (sizeof(T) == 4) {
+        two_sum_acc(shi[e], slo[e], (float)ps[e]);
+        two_sum_acc(ahi[e], alo[e], (float)pa[e]);
+      } else {
+        sd[e] += (double)ps[e];
+        ad[e] += (double)pa[e];
+      }
+    }
+    __syncthreads();
+  }
+  double *o = out + goff[f] + (long long)ch * 2 * n * n;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int i = 4 * ti + r, j = 4 * tj + cc;
+      if (i < n && j < n) {
+        const int e = 4 * r + cc;
+        const double sv = sizeof(T) == 4 ? (double)shi[e] + (double)slo[e] : sd[e];
+        const double av = sizeof(T) == 4 ? (double)ahi[e] + (double)alo[e] : ad[e];
+        o[i * n + j] = sv;
+        o[n * n + i * n + j] = av;
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 subspace solve, one CTA per fragment: S = L L^T, Hs = L^-1 A L^-T, cyclic Jacobi
+// (round-robin ordering, n/2 disjoint rotations per round), C = L^-T Q sorted by eigenvalue.
+// ---------------------------------------------------------------------------------------------
+constexpr int SNT = 256;
+
+__device__ __forceinline__ double block_sum_d(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < SNT / 32; ++i) s += red[i];
+  __syncthreads();
+  return s;  // all threads
+}
+
+__global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const long long *goff, const int *gnchunk,
+                                                  const double *gram, double dV, double *eps, double *C64,
+                                                  float *C32, unsigned *flags) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int f = blockIdx.x;
+  const FragDesc D = desc[f];
+  const int n = D.norb;
+  const int np = n + (n & 1);  // even size for the round-robin pairing (index n is a dummy)
+  const int ld = np + 1;
+  double *M0 = reinterpret_cast<double *>(smem_raw);  // S -> L -> C
+  double *M1 = M0 + np * ld;                          // L^-1
+  double *M2 = M1 + np * ld;                          // A -> Hs -> diag
+  double *M3 = M2 + np * ld;                          // X -> V
+  __shared__ double red[SNT / 32];
+  __shared__ double rc[32], rs[32];
+  __shared__ int rp[32], rq[32];
+  __shared__ int failed;
+  const int tid = threadIdx.x;
+  if (tid == 0) failed = 0;
+
+  // 1. reduce the chunk partials in a fixed order
+  const double *g = gram + goff[f];
+  const int nch = gnchunk[f];
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    double s = 0.0, a = 0.0;
+    if (i < n && j < n) {
+      for (int ch = 0; ch < nch; ++ch) {
+        s += g[(long long)ch * 2 * n * n + i * n + j];
+        a += g[(long long)ch * 2 * n * n + n * n + i * n + j];
+      }
+      s *= dV;
+      a *= dV;
+    }
+    M0[i * ld + j] = s;
+    M2[i * ld + j] = a;
+  }
+  __syncthreads();
+
+  // 2. Cholesky S = L L^T (lower, in M0)
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const double d = M0[k * ld + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        failed = 1;
+        M0[k * ld + k] = 1.0;
+      } else {
+        M0[k * ld + k] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    const double piv = M0[k * ld + k];
+    for (int i = k + 1 + tid; i < n; i += SNT) M0[i * ld + k] /= piv;
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int t = tid; t < m * m; t += SNT) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) M0[i * ld + j] -= M0[i * ld + k] * M0[j * ld + k];
+    }
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(flags, DC_FLAG_NOTSPD);
+    return;
+  }
+
+  // 3. L^-1 (lower) by forward substitution, one column per thread
+  for (int j = tid; j < np; j += SNT) {
+    for (int i = 0; i < np; ++i) M1[i * ld + j] = 0.0;
+    if (j < n) {
+      for (int i = j; i < n; ++i) {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int k = j; k < i; ++k) s -= M0[i * ld + k] * M1[k * ld + j];
+        M1[i * ld + j] = s / M0[i * ld + i];
+      }
+    }
+  }
+  __syncthreads();
+  // 4. X = L^-1 A (M3), Hs = X L^-T (M2), symmetrised
+  for (int t = tid; t < n * n; t += SNT) {
+    const int i = t / n, j = t - i * n;
+    double s = 0.0;
+    for (int k = 0; k <= i; ++k) s += M1[i * ld + k] * M2[k * ld + j];
+    M3[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += SNT) {
+    const int i = t / n, j = t - i * n;
+    double s = 0.0;
+    for (int k = 0; k <= j; ++k) s += M3[i * ld + k] * M1[j * ld + k];
+    M2[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    double v = 0.0;
+    if (i < n && j < n) v = 0.5 * (M2[i * ld + j] + M2[j * ld + i]);
+    M3[i * ld + j] = v;  // temporarily the symmetrised Hs
+  }
+  __syncthreads();
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    M2[i * ld + j] = M3[i * ld + j];
+    M3[i * ld + j] = (i == j) ? 1.0 : 0.0;  // V = I
+  }
+  __syncthreads();
+
+  // 5. cyclic Jacobi
+  const int half = np / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int t = tid; t < np * np; t += SNT) {
+      const int i = t / np, j = t - i * np;
+      const double v = M2[i * ld + j];
+      if (i == j) dia += v * v;
+      else off += v * v;
+    }
+    off = block_sum_d(off, red);
+    dia = block_sum_d(dia, red);
+    if (!(off > 1e-30 * (dia + off))) break;
+    for (int r = 0; r < np - 1; ++r) {
+      if (tid < half) {
+        int p, q;
+        if (tid == 0) {
+          p = r;
+          q = np - 1;
+        } else {
+          p = (r + tid) % (np - 1);
+          q = (r - tid + (np - 1)) % (np - 1);
+        }
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        const double app = M2[p * ld + p], aqq = M2[q * ld + q], apq = M2[p * ld + q];
+        double c = 1.0, s = 0.0;
+        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        rp[tid] = p;
+        rq[tid] = q;
+        rc[tid] = c;
+        rs[tid] = s;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int t = tid; t < half * np; t += SNT) {
+        const int k = t / np, j = t - k * np;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], s = rs[k];
+        if (s == 0.0) continue;
+        const double ap = M2[p * ld + j], aq = M2[q * ld + j];
+        M2[p * ld + j] = c * ap - s * aq;
+        M2[q * ld + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int t = tid; t < half * np; t += SNT) {
+        const int k = t / np, i = t - k * np;
+        const int p = rp[k], q = rq[k];
+        const double c = rc[k], s = rs[k];
+        if (s == 0.0) continue;
+        const double ap = M2[i * ld + p], aq = M2[i * ld + q];
+        M2[i * ld + p] = c * ap - s * aq;
+        M2[i * ld + q] = s * ap + c * aq;
+        const double vp = M3[i * ld + p], vq = M3[i * ld + q];
+        M3[i * ld + p] = c * vp - s * vq;
+        M3[i * ld + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+
+  // 6. sort ascending (rank by value, ties by index) and C = L^-T V
+  __shared__ int rank[DC_MAX_NORB];
+  for (int i = tid; i < n; i += SNT) {
+    const double li = M2[i * ld + i];
+    int rk = 0;
+    for (int j = 0; j < n; ++j) {
+      const double lj = M2[j * ld + j];
+      rk += (lj < li) || (lj == li && j < i);
+    }
+    rank[i] = rk;
+    eps[D.st_off + rk] = li;
+    if (!isfinite(li)) atomicOr(flags, DC_FLAG_NONFINITE);
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += SNT) {
+    const int k = t / n, i = t - k * n;  // C[k][rank[i]] = sum_{m>=k} Linv[m][k] V[m][i]
+    double s = 0.0;
+    for (int m = k; m < n; ++m) s += M1[m * ld + k] * M3[m * ld + i];
+    const long long o = D.sub_off + (long long)k * n + rank[i];
+    C64[o] = s;
+    if (C32) C32[o] = (float)s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Rotation out[i][p] = sum_k C[k][i] Y[k][p].  One CTA per (fragment, 128-point chunk); thread
+// (pq, og) owns points 4pq..4pq+3 and orbitals 8og..8og+7.
+// ---------------------------------------------------------------------------------------------
+constexpr int RCH = 128;
+constexpr int RPAD = RCH + 4;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rotate(const FragDesc *desc, const int2 *ritems, const T *C, const T *Y,
+                                                T *out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 it = ritems[blockIdx.x];
+  const int f = it.x, ch = it.y;
+  const FragDesc D = desc[f];
+  const int n = D.norb;
+  const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
+  const long long p0 = (long long)ch * RCH;
+  T *sY = reinterpret_cast<T *>(smem_raw);  // [n][RPAD]
+  T *sC = sY + DC_MAX_NORB * RPAD;          // [n][64]
+  const T *Cf = C + D.sub_off;
+  for (int t = threadIdx.x; t < n * DC_MAX_NORB; t += 256) {
+    const int k = t / DC_MAX_NORB, i = t - k * DC_MAX_NORB;
+    sC[t] = i < n ? Cf[k * n + i] : T(0);
+  }
+  const T *Yf = Y + D.psi_off;
+  for (int t = threadIdx.x; t < n * RCH; t += 256) {
+    const int k = t / RCH, p = t - k * RCH;
+    const long long pp = p0 + p;
+    sY[k * RPAD + p] = pp < P ? Yf[(long long)k * P + pp] : T(0);
+  }
+  __syncthreads();
+  const int pq = threadIdx.x & 31, og = threadIdx.x >> 5;
+  if (8 * og >= n) return;
+  T acc[8][4];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int k = 0; k < n; ++k) {
+    const Vec4<T> y = ld4(&sY[k * RPAD + 4 * pq]);
+    const Vec4<T> c0 = ld4(&sC[k * DC_MAX_NORB + 8 * og]);
+    const Vec4<T> c1 = ld4(&sC[k * DC_MAX_NORB + 8 * og + 4]);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a][b] += c0.v[a] * y.v[b];
+        acc[a + 4][b] += c1.v[a] * y.v[b];
+      }
+    }
+  }
+  T *of = out + D.psi_off;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = 8 * og + a;
+    if (i >= n) break;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const long long pp = p0 + 4 * pq + b;
+      if (pp < P) of[(long long)i * P + pp] = acc[a][b];
+    }
+  }
+}
+
+}  // namespace
+
+namespace dck {
+
+int launch_bounds(dc_ctx *c, int, cudaStream_t s) {
+  const int m = c->params.cheb_degree;
+  k_bounds<<<(c->nfrag + 127) / 128, 128, 0, s>>>(c->d_desc, c->nfrag, c->d_eps, c->d_bounds, m, 4 + 2 * m);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+template <typename T>
+int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s) {
+  k_gram<T><<<c->n_gram_items, 256, 0, s>>>(c->d_desc, c->d_gram_items, c->d_gram_off, c->gram_chunk, Y, HY,
+                                            c->d_gram);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
+  const int np = c->layout.max_norb + (c->layout.max_norb & 1);
+  const size_t sm = 4 * (size_t)np * (np + 1) * sizeof(double);
+  DC_CUDA(cudaFuncSetAttribute(k_subspace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_subspace<<<c->nfrag, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, c->d_eps,
+                                       c->d_C64, precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+template <typename T>
+int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s) {
+  const size_t sm = ((size_t)DC_MAX_NORB * RPAD + (size_t)DC_MAX_NORB * DC_MAX_NORB) * sizeof(T);
+  DC_CUDA(cudaFuncSetAttribute(k_rotate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const T *C = nullptr;
+  if (sizeof(T) == 8) C = reinterpret_cast<const T *>(c->d_C64);
+  else C = reinterpret_cast<const T *>(c->d_C32);
+  k_rotate<T><<<c->n_rot_items, 256, sm, s>>>(c->d_desc, c->d_rot_items, C, Y, out);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+template int launch_gram<double>(dc_ctx *, const double *, const double *, cudaStream_t);
+template int launch_gram<float>(dc_ctx *, const float *, const float *, cudaStream_t);
+template int launch_rotate<double>(dc_ctx *, const double *, double *, cudaStream_t);
+template int launch_rotate<float>(dc_ctx *, const float *, float *, cudaStream_t);
+
+}  // namespace dck

@@ -1,0 +1,304 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances:
+  * maps, atom lists, starting orbitals: bit-exact;
+  * FP64 path: 1e-10 relative (rounding order only);
+  * FP32 / mixed path against the FP64 oracle: the targets of the method's accuracy budget,
+    1e-6 Ha/atom total energy, 1e-5 Ha eigenvalues, 1e-5 relative L1 density; the H-apply
+    itself at 2e-6 of max|H psi| (FP32 rounding of 25-point sums with O(10 Ha) coefficients).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import adjoint, chefsi, fermi, model
+from tests.oracle_pack import oracle_state, pack, unpack, unpack_states
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _solver(cfg):
+    from paper_2606_21125_b300 import DCSolver
+    return DCSolver(cfg)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+CASES = {
+    "si8": lambda **kw: workloads.make_config("si8", **kw),
+    "periodic": lambda **kw: workloads.small_config(n=(12, 12, 12), L=(7.2, 7.2, 7.2), bc="periodic", natom=4,
+                                                    **kw),
+    "uneven": lambda **kw: workloads.small_config(n=(21, 13, 16), L=(11.0, 7.0, 8.5), num_fragment=(2, 3, 2),
+                                                  buffer=(3, 2, 2), nstate=7, natom=6, seed=3, **kw),
+    "wide": lambda **kw: workloads.small_config(n=(8, 8, 8), L=(5.0, 5.0, 5.0), num_fragment=(1, 2, 1),
+                                                buffer=(3, 2, 3), nstate=5, natom=2, seed=5, **kw),
+    "water_auto": lambda **kw: workloads.small_config(n=(24, 24, 24), L=(9.0, 9.0, 9.0), num_fragment=(2, 2, 2),
+                                                      buffer=(3, 3, 3), nstate=0, natom=9, seed=8,
+                                                      species=("O", "H"), **kw),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_maps_bit_exact(case):
+    cfg = CASES[case]()
+    st = oracle_state(cfg)
+    with _solver(cfg) as s:
+        m = s.maps()
+    fr = st.frags
+    for f in range(fr.nfrag):
+        assert list(m["frag"][f, 0:3]) == list(fr.origin[f])
+        assert list(m["frag"][f, 3:6]) == list(fr.extent[f])
+        assert list(m["frag"][f, 6:9]) == list(fr.core[f])
+        assert m["frag"][f, 9] == st.norb[f]
+        assert m["frag"][f, 10] == len(st.proj[f].atoms)
+    idx = np.concatenate([fr.idx_map(f) for f in range(fr.nfrag)])
+    assert np.array_equal(m["idx_map"], idx)
+    assert np.array_equal(m["owner"], st.owner)
+    assert np.array_equal(m["core_local"], st.core_local)
+    atoms = np.concatenate([st.proj[f].atoms for f in range(fr.nfrag)])
+    assert np.array_equal(m["atoms"], atoms)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_ionic_potential_and_starting_density(case):
+    cfg = CASES[case]()
+    st = oracle_state(cfg)
+    with _solver(cfg) as s:
+        vion, rho0 = s.initial()
+        veff = s.potential(rho0)
+        torch.cuda.synchronize()
+    ref_v = st.vion.reshape(-1)
+    assert np.max(np.abs(_np(vion) - ref_v)) <= 1e-12 * np.max(np.abs(ref_v))
+    ref_r = st.rho_in.reshape(-1)
+    assert np.max(np.abs(_np(rho0) - ref_r)) <= 1e-12 * np.max(np.abs(ref_r))
+    ref_e = st.veff(st.rho_in).reshape(-1)
+    assert np.max(np.abs(_np(veff) - ref_e)) <= 1e-12 * np.max(np.abs(ref_e))
+
+
+def test_starting_orbitals_bit_exact():
+    cfg = CASES["uneven"](precision="fp64")
+    st = oracle_state(cfg)
+    with _solver(cfg) as s:
+        psi, _ = s.get_state()
+        got = _np(psi)
+    assert np.array_equal(got, pack(st, st.psi))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_hpsi(case, dtype):
+    cfg = CASES[case](precision=dtype)
+    st = oracle_state(cfg)
+    V = st.veff(st.rho_in)
+    r = np.random.default_rng(11)
+    with _solver(cfg) as s:
+        _, rho0 = s.initial()
+        s.potential(rho0)
+        x = r.standard_normal(s.layout.psi_elems)
+        tdt = torch.float64 if dtype == "fp64" else torch.float32
+        psi = torch.tensor(x, dtype=tdt, device="cuda")
+        out = _np(s.hpsi(psi))
+        xin = _np(psi).astype(np.float64)
+    blocks = unpack(st, xin)
+    ref = pack(st, {f: st.hamiltonian(f, V).apply(blocks[f]) for f in range(st.frags.nfrag)})
+    tol = 1e-12 if dtype == "fp64" else 2e-6
+    assert np.max(np.abs(out - ref)) <= tol * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", ["si8", "periodic", "uneven", "water_auto"])
+def test_subspace_and_one_chefsi_pass_fp64(case):
+    cfg = CASES[case](precision="fp64")
+    st = oracle_state(cfg)
+    V = st.veff(st.rho_in)
+    st.initial_rr(V)
+    eps_rr = pack(st, st.eps)
+    st.solve(V, 1)
+    eps_1 = pack(st, st.eps)
+    with _solver(cfg) as s:
+        _, rho0 = s.initial()
+        s.potential(rho0)
+        s.subspace()
+        _, e0 = s.get_state()
+        e0 = _np(e0)
+        s.chefsi(1)
+        _, e1 = s.get_state()
+        e1 = _np(e1)
+    assert np.max(np.abs(e0 - eps_rr)) < 1e-10 * max(1.0, np.max(np.abs(eps_rr)))
+    assert np.max(np.abs(e1 - eps_1)) < 1e-9 * max(1.0, np.max(np.abs(eps_1)))
+
+
+@pytest.fixture(scope="module")
+def si8_oracle_run():
+    cfg = workloads.make_config("si8")
+    st = oracle_state(cfg)
+    st.warmup()
+    warm = dict(eps=pack(st, st.eps))
+    q, mu, occ, rho = st.density_stage()
+    warm.update(q=pack(st, q), mu=mu, rho=rho.reshape(-1))
+    steps = [st.scf_step() for _ in range(cfg["scf_steps"])]
+    return cfg, st, warm, steps
+
+
+def test_warmup_and_density_fp64(si8_oracle_run):
+    cfg, st, warm, _ = si8_oracle_run
+    with _solver(dict(cfg, precision="fp64")) as s:
+        s.warmup()
+        _, eps = s.get_state()
+        rho, q, mu = s.density()
+        eps, rho, q, mu = _np(eps), _np(rho), _np(q), float(_np(mu)[0])
+    assert np.max(np.abs(eps - warm["eps"])) < 1e-9
+    assert np.max(np.abs(q - warm["q"])) < 1e-9
+    assert abs(mu - warm["mu"]) < 1e-9
+    assert np.sum(np.abs(rho - warm["rho"])) / np.sum(np.abs(warm["rho"])) < 1e-9
+    assert abs(st.grid.dV * rho.sum() - st.ne) < 1e-9 * st.ne
+
+
+@pytest.mark.parametrize("precision,tol_e,tol_eps,tol_rho", [("fp64", 1e-9, 1e-8, 1e-8),
+                                                             ("fp32", 1e-6, 1e-5, 1e-5)])
+def test_scf_steps_si8(si8_oracle_run, precision, tol_e, tol_eps, tol_rho):
+    """Ten SCF steps of Si8 (10^3 cores + 4-point buffers, 24 orbitals) against the FP64 oracle."""
+    cfg, st, _, steps = si8_oracle_run
+    natom = len(cfg["pos"])
+    with _solver(dict(cfg, precision=precision)) as s:
+        s.warmup()
+        _, rho = s.initial()
+        rho = rho.clone()
+        for k, ref in enumerate(steps):
+            got = s.scf_step(rho)
+            assert abs(got["E"] - ref["E"]) / natom < tol_e, (k, got["E"], ref["E"])
+            assert abs(got["F"] - ref["F"]) / natom < tol_e
+            assert abs(got["mu"] - ref["mu"]) < 10 * tol_eps
+            assert abs(got["drho"] - ref["drho"]) < 10 * tol_rho
+            assert abs(got["ne"] - st.ne) < 1e-9 * st.ne
+        _, eps = s.get_state()
+        rho_out = _np(s.rho_out())
+    ref_eps = pack(st, steps[-1]["eps"])
+    assert np.max(np.abs(_np(eps) - ref_eps)) < tol_eps
+    ref_rho = steps[-1]["rho_out"].reshape(-1)
+    assert np.sum(np.abs(rho_out - ref_rho)) / np.sum(np.abs(ref_rho)) < tol_rho
+
+
+def test_scf_step_host_buffers_match_device_buffers():
+    cfg = CASES["uneven"](precision="fp32", n_warmup=3)
+    res = []
+    for host in (False, True):
+        with _solver(cfg) as s:
+            s.warmup()
+            _, rho = s.initial()
+            if host:
+                rho = _np(rho).copy()
+            stats = [s.scf_step(rho) for _ in range(2)]
+            res.append((stats, rho if host else _np(rho)))
+    for a, b in zip(res[0][0], res[1][0]):
+        assert a["E"] == b["E"] and a["mu"] == b["mu"]
+    assert np.array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("case", ["si8", "periodic", "uneven", "wide"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_band_energy_adjoint(case, dtype):
+    cfg = CASES[case](precision=dtype)
+    st = oracle_state(cfg)
+    r = np.random.default_rng(21)
+    V = st.veff(st.rho_in) + 0.05 * r.standard_normal(st.grid.shape())
+    D = np.array([st.spec["D"][sp] for sp in st.species]) + 0.1 * r.uniform(size=len(st.species))
+    with _solver(cfg) as s:
+        tdt = torch.float64 if dtype == "fp64" else torch.float32
+        psi = torch.tensor(r.standard_normal(s.layout.psi_elems), dtype=tdt, device="cuda")
+        occ = torch.tensor(r.uniform(0, 2, s.layout.nstates), dtype=torch.float64, device="cuda")
+        Vt = torch.tensor(V.reshape(-1), dtype=torch.float64, device="cuda")
+        Dt = torch.tensor(D, dtype=torch.float64, device="cuda")
+        Eb, dpsi, dV, dD = s.eb_adjoint(psi, occ, Vt, Dt)
+        xin = _np(psi).astype(np.float64)
+        occ_n = _np(occ)
+        dpsi, dV, dD = _np(dpsi), _np(dV), _np(dD)
+    ps = unpack(st, xin)
+    oc = unpack_states(st, occ_n)
+    E_ref = adjoint.band_energy(st, ps, V, D, oc)
+    gpsi, gV, gD = adjoint.band_energy_grad(st, ps, V, D, oc)
+    tol = 1e-11 if dtype == "fp64" else 3e-6
+    assert abs(Eb - E_ref) <= tol * abs(E_ref) + tol
+    ref = pack(st, gpsi)
+    assert np.max(np.abs(dpsi - ref)) <= tol * np.max(np.abs(ref))
+    assert np.max(np.abs(dV - gV.reshape(-1))) <= tol * np.max(np.abs(gV))
+    assert np.max(np.abs(dD - gD)) <= tol * max(1e-30, np.max(np.abs(gD)))
+
+
+def test_autograd_band_energy_finite_differences():
+    """torch.autograd through the hand-written adjoint agrees with central differences (FP64)."""
+    from paper_2606_21125_b300 import Eb
+    cfg = CASES["uneven"](precision="fp64")
+    r = np.random.default_rng(5)
+    with _solver(cfg) as s:
+        _, rho0 = s.initial()
+        V = s.potential(rho0).clone().requires_grad_(True)
+        D = torch.tensor(np.array([cfg["spec"]["D"][sp] for sp in cfg["species"]]), dtype=torch.float64,
+                         device="cuda", requires_grad=True)
+        psi = torch.tensor(r.standard_normal(s.layout.psi_elems), dtype=torch.float64, device="cuda",
+                           requires_grad=True)
+        occ = torch.tensor(r.uniform(0, 2, s.layout.nstates), dtype=torch.float64, device="cuda")
+        E = Eb.apply(psi, V, D, occ, s)
+        E.backward()
+        t = 1e-4
+        for x in (psi, V, D):
+            d = torch.tensor(r.standard_normal(x.numel()), dtype=torch.float64, device="cuda")
+            with torch.no_grad():
+                args = [psi, V, D]
+                i = [id(a) for a in args].index(id(x))
+                ap = list(args)
+                am = list(args)
+                ap[i] = x + t * d
+                am[i] = x - t * d
+                fd = (Eb.apply(ap[0], ap[1], ap[2], occ, s) - Eb.apply(am[0], am[1], am[2], occ, s)) / (2 * t)
+            an = torch.dot(x.grad, d)
+            assert abs(float(fd) - float(an)) <= 1e-8 * abs(float(an))
+
+
+def test_errors_are_status_codes():
+    from paper_2606_21125_b300 import DCError
+    cfg = CASES["uneven"](precision="fp32", n_warmup=2)
+    with _solver(cfg) as s:
+        _, rho = s.initial()
+        with pytest.raises(DCError) as e:
+            s.scf_step(rho.clone())
+        assert e.value.status == -7  # DC_ERR_STATE: no warm-up yet
+        s.warmup()
+        bad = rho.clone()
+        bad[5] = float("nan")
+        with pytest.raises(DCError) as e:
+            s.scf_step(bad)
+        assert e.value.status in (-4, -6)
+        # the context stays usable after the error
+        s.warmup()
+        good = s.scf_step(rho.clone())
+        assert np.isfinite(good["E"])
+
+
+def test_full_size_hpsi_sampled_si512():
+    """Si512 at full size (80^3 grid, 512 fragments of 22^3, 48 orbitals), FP32 H-apply as the bench
+    launches it; a few fragments are recomputed by the oracle."""
+    cfg = workloads.make_config("si512", precision="fp32")
+    sample = [0, 137, 511]
+    st = oracle_state(cfg, subset=sample)
+    V = st.veff(st.rho_in)
+    r = np.random.default_rng(2)
+    with _solver(cfg) as s:
+        _, rho0 = s.initial()
+        s.potential(rho0)
+        psi = torch.tensor(r.standard_normal(s.layout.psi_elems), dtype=torch.float32, device="cuda")
+        out = s.hpsi(psi)
+        offs = {}
+        off = 0
+        for f in range(st.frags.nfrag):
+            n = int(st.norb[f] * np.prod(st.frags.extent[f]))
+            offs[f] = (off, n)
+            off += n
+        got = {f: _np(out[offs[f][0]:offs[f][0] + offs[f][1]]) for f in sample}
+        xin = {f: _np(psi[offs[f][0]:offs[f][0] + offs[f][1]]).astype(np.float64) for f in sample}
+    for f in sample:
+        shp = (int(st.norb[f]),) + tuple(int(v) for v in st.frags.extent[f][::-1])
+        ref = st.hamiltonian(f, V).apply(xin[f].reshape(shp)).reshape(-1)
+        assert np.max(np.abs(got[f] - ref)) <= 2e-6 * np.max(np.abs(ref)), f

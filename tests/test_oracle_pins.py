@@ -241,6 +241,15 @@ def _one_atom(L, N, sigma, Z=4.0):
     return grid, R, np.zeros(1, dtype=np.int64), spec
 
 
+def _sampled_gaussian(grid, R, sigma, Z):
+    """Z (2 pi sigma^2)^(-3/2) exp(-|r-R|^2/(2 sigma^2)) sampled on the grid (nearest image; box >> sigma)."""
+    coords = [np.arange(grid.n[d]) * grid.h[d] for d in range(3)]
+    d = [coords[k] - R[k] for k in range(3)]
+    d = [v - grid.L[k] * np.round(v / grid.L[k]) for k, v in enumerate(d)]
+    r2 = d[2][:, None, None] ** 2 + d[1][None, :, None] ** 2 + d[0][None, None, :] ** 2
+    return Z * (2 * np.pi * sigma * sigma) ** -1.5 * np.exp(-r2 / (2 * sigma * sigma))
+
+
 def test_vion_matches_gaussian_charge_potential():
     """V_loc near a Gaussian ion = -Z erf(r/(sqrt2 sigma))/r - (2 pi Z/3 Omega) r^2 + const (cubic images).
 
@@ -270,7 +279,7 @@ def test_hartree_cancels_ion_potential():
     """V_H of the Gaussian ion charge sampled on the grid cancels V_loc up to a constant."""
     L, N, sig = 16.0, 40, 0.8
     grid, R, spc, spec = _one_atom(L, N, sig)
-    rho = model.initial_density(grid, R, spc, spec)
+    rho = _sampled_gaussian(grid, R[0], sig, 4.0)
     tot = model.hartree(grid, rho) + model.v_ion(grid, R, spc, spec)
     assert np.ptp(tot) < 1e-6
 
@@ -294,14 +303,24 @@ def test_es_energy_neutral_pair():
     grid, R, spc, spec = _one_atom(L, N, sig, Z)
     d = 1.875  # four grid spacings... any value; the electron cloud is sampled at an offset centre
     Re = R + np.array([[d, 0.0, 0.0]])
-    rho = model.initial_density(grid, Re, spc, spec)
+    rho = _sampled_gaussian(grid, Re[0], sig, Z)
     E = model.es_energy(grid, rho, model.rho_ion_G(grid, R, spc, spec))
     ana = 2 * Z * Z / (2 * sig * math.sqrt(math.pi)) - Z * Z * erf(d / (2 * sig)) / d - 2 * math.pi * (Z * d) ** 2 / (
         3 * grid.volume)
     assert abs(E - ana) < 5e-5
     # an electron cloud identical to the ion gives zero
-    rho0 = model.initial_density(grid, R, spc, spec)
+    rho0 = _sampled_gaussian(grid, R[0], sig, Z)
     assert abs(model.es_energy(grid, rho0, model.rho_ion_G(grid, R, spc, spec))) < 1e-8
+
+
+def test_initial_density_is_band_limited_ion_charge():
+    """Starting density integrates to N_e and matches a sampled Gaussian where the latter is resolved."""
+    L, N, sig = 16.0, 40, 0.8
+    grid, R, spc, spec = _one_atom(L, N, sig)
+    rho = model.initial_density(grid, R, spc, spec)
+    assert abs(grid.dV * rho.sum() - 4.0) < 1e-12
+    ref = _sampled_gaussian(grid, R[0], sig, 4.0)
+    assert np.max(np.abs(rho - ref)) < 1e-6 * np.max(ref)
 
 
 def test_exchange_uniform_gas():
