@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     p.add_argument("--sample-frags", type=int, default=8, help="fragments in the oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     return p.parse_args()
 
 
@@ -274,6 +275,30 @@ def run_ours(args):
     ms_step = ms_max / args.steps
     value = ws * args.steps / (ms_max / 1e3)
 
+    # ---- the same steps in plain FP64: step time and energy difference per atom ----
+    compare = None
+    if args.precision != "fp64" and not args.no_compare:
+        ref = DCSolver(workloads.make_config(args.workload, precision="fp64"))
+        ref.warmup()
+        _, r64 = ref.initial()
+        r64 = r64.clone()
+        for _ in range(args.warmup):
+            ref.scf_step(r64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64 = None
+        for _ in range(args.steps):
+            s64 = ref.scf_step(r64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        natom = len(cfg["pos"])
+        compare = dict(precision="fp64", ms_per_step=e0.elapsed_time(e1) / args.steps,
+                       speedup=(e0.elapsed_time(e1) / args.steps) / ms_step,
+                       dE_per_atom=abs(stats["E"] - s64["E"]) / natom, dmu=abs(stats["mu"] - s64["mu"]),
+                       steps_compared=args.warmup + args.steps)
+        ref.close()
+
     # ---- end to end through the public API with host buffers (H2D rho_in, D2H rho + stats) ----
     host = torch.empty(solver.layout.npts, dtype=torch.float64, pin_memory=True)
     host.copy_(rho.cpu())
@@ -316,7 +341,7 @@ def run_ours(args):
                               avg_launch_ms=h["ms"] / max(1, h["launches"])),
                 stages_ms_per_step={k: v["ms"] / args.steps for k, v in prof.items()},
                 e2e=dict(value=e2e_val, unit="SCF steps/s", h2d_bytes_per_step=nb, d2h_bytes_per_step=nb + 8 * 16),
-                gpu_launches=launches, init_s=init_s,
+                gpu_launches=launches, init_s=init_s, fp64_compare=compare,
                 last_step=dict(E_per_atom=stats["E"] / len(cfg["pos"]), mu=stats["mu"], drho=stats["drho"]),
                 clocks=clocks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -101,7 +101,8 @@ typedef struct {
 /* Solver parameters.  precision: DC_FP64/DC_FP32/DC_MIXED.  cheb_degree: Chebyshev filter degree
  * m (>= 1).  n_pass: CheFSI passes per SCF step.  n_warmup: passes in the starting potential before
  * the first step (run in FP64 for every precision).  hxc: DC_HXC_*.  kT: electronic temperature
- * (Ha, > 0).  mix_alpha: linear mixing weight in (0, 1].  seed: initial-orbital seed. */
+ * (Ha, > 0).  mix_alpha: linear mixing weight in [0, 1]; 0 keeps rho_in fixed (the paper's fixed-density
+ * DC, Sec. 2.5 use case 3).  seed: initial-orbital seed. */
 typedef struct {
   int precision;
   int cheb_degree;
@@ -145,7 +146,7 @@ typedef struct dc_ctx dc_ctx;
  * projector factors, the ionic potential V_loc and ion charge rho_ion(G) (on the device, via
  * cuFFT), the starting density (band-limited ion charge scaled to N_e) and the random starting
  * orbitals; allocate the orbital state and work blocks.  Synchronous.  On failure *out is NULL
- * and nothing is leaked.  Errors: DC_ERR_ARG (sizes, counts, f >= 4096 fragments or n_f > 1024),
+ * and nothing is leaked.  Errors: DC_ERR_ARG (sizes, counts, >= 4096 fragments, n_f outside [1, 64], extents above 64),
  * DC_ERR_OOM, DC_ERR_CUDA. */
 int dc_init(const dc_grid_t *grid, const dc_fragments_t *fragments, const dc_buffers_t *buffers,
             const dc_atoms_t *atoms, const dc_params_t *params, dc_ctx **out);

@@ -172,7 +172,10 @@ int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
   }
   {
     StageScope sc(c, DC_STAGE_GRAM, s, 2.0 * blk + 8.0 * c->gram_elems, 1);
-    DC_TRY(dck::launch_gram<T>(c, B[cur], B[hy], s));
+    if (sizeof(T) == 4 && c->params.precision == DC_MIXED)
+      DC_TRY(dck::launch_gram_tc(c, (const float *)B[cur], (const float *)B[hy], s));
+    else
+      DC_TRY(dck::launch_gram<T>(c, B[cur], B[hy], s));
   }
   {
     StageScope sc(c, DC_STAGE_SUBSPACE, s, 8.0 * c->gram_elems, 1);
@@ -244,7 +247,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   c->params = *params;
   const dc_params_t &P = c->params;
   if (P.precision < DC_FP64 || P.precision > DC_MIXED || P.cheb_degree < 1 || P.cheb_degree > 64 || P.n_pass < 1 ||
-      P.n_warmup < 0 || !(P.kT > 0.0) || !(P.mix_alpha > 0.0) || P.mix_alpha > 1.0 ||
+      P.n_warmup < 0 || !(P.kT > 0.0) || !(P.mix_alpha >= 0.0) || P.mix_alpha > 1.0 ||
       (P.hxc != DC_HXC_NONE && P.hxc != DC_HXC_HARTREE_X)) {
     dc_set_error("dc_init: invalid parameters");
     return DC_ERR_ARG;

@@ -209,6 +209,7 @@ int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T 
 int launch_bounds(dc_ctx *c, int first, cudaStream_t s);
 template <typename T>
 int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s);
+int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s);
 int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s);
 template <typename T>
 int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s);

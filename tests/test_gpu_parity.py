@@ -75,7 +75,9 @@ def test_ionic_potential_and_starting_density(case):
     ref_r = st.rho_in.reshape(-1)
     assert np.max(np.abs(_np(rho0) - ref_r)) <= 1e-12 * np.max(np.abs(ref_r))
     ref_e = st.veff(st.rho_in).reshape(-1)
-    assert np.max(np.abs(_np(veff) - ref_e)) <= 1e-12 * np.max(np.abs(ref_e))
+    # V_loc and V_H nearly cancel: the FFT rounding scales with the uncancelled terms
+    scale = np.max(np.abs(ref_v)) + np.max(np.abs(model.hartree(st.grid, st.rho_in)))
+    assert np.max(np.abs(_np(veff) - ref_e)) <= 1e-12 * scale
 
 
 def test_starting_orbitals_bit_exact():
@@ -157,7 +159,8 @@ def test_warmup_and_density_fp64(si8_oracle_run):
 
 
 @pytest.mark.parametrize("precision,tol_e,tol_eps,tol_rho", [("fp64", 1e-9, 1e-8, 1e-8),
-                                                             ("fp32", 1e-6, 1e-5, 1e-5)])
+                                                             ("fp32", 1e-6, 1e-5, 1e-5),
+                                                             ("mixed", 1e-6, 1e-5, 1e-5)])
 def test_scf_steps_si8(si8_oracle_run, precision, tol_e, tol_eps, tol_rho):
     """Ten SCF steps of Si8 (10^3 cores + 4-point buffers, 24 orbitals) against the FP64 oracle."""
     cfg, st, _, steps = si8_oracle_run
