@@ -231,6 +231,16 @@ int dc_get_rho_out(dc_ctx *ctx, double *d_rho, void *stream);
 int dc_eb_adjoint(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_occ, const double *d_V,
                   const double *d_D, double *h_Eb, void *d_dpsi, double *d_dV, double *d_dD, void *stream);
 
+/* ---- autotuner ------------------------------------------------------------------------- */
+/* dc_warmup times every useful launch shape (threads per CTA, x-adjacent point pairs per thread) of
+ * the stencil H-apply kernel on the context's own fragments and keeps the fastest, separately for
+ * FP32 and FP64 elements.  With the environment variable DC_TUNE_CACHE=<file> results are looked up
+ * in / appended to that text file (one line per fragment shape, atom and orbital count, type).
+ * h_shape[4] = {fp32 threads, fp32 pairs, fp64 threads, fp64 pairs} (0 = not tuned yet);
+ * h_ms[16] (may be NULL) = best time in ms of each of the 8 candidate shapes, FP32 then FP64
+ * (0 = not tried). */
+int dc_tuning(const dc_ctx *ctx, int *h_shape, float *h_ms);
+
 /* ---- stage profiler -------------------------------------------------------------------- */
 /* Stages of the step, in the order they run. */
 #define DC_STAGE_POTENTIAL 0 /* Poisson + exchange (cuFFT and pointwise kernels) */

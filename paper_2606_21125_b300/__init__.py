@@ -203,8 +203,16 @@ def _profile_methods():
         check("dc_profile_read", self.lib.dc_profile_read(self.ctx, ms, nl, by))
         return {name: dict(ms=ms[i], launches=int(nl[i]), bytes=by[i]) for i, name in enumerate(_lib.STAGES)}
 
+    def tuning(self):
+        shp = (C.c_int * 4)()
+        ms = (C.c_float * 16)()
+        check("dc_tuning", self.lib.dc_tuning(self.ctx, shp, ms))
+        return dict(fp32=dict(threads=shp[0], pairs=shp[1], candidates_ms=list(ms[0:8])),
+                    fp64=dict(threads=shp[2], pairs=shp[3], candidates_ms=list(ms[8:16])))
+
     DCSolver.profile = profile
     DCSolver.profile_read = profile_read
+    DCSolver.tuning = tuning
 
 
 _profile_methods()

@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "dc_internal.h"
@@ -17,6 +19,21 @@ thread_local std::string g_last_error = "";
 }
 
 void dc_set_error(const std::string &msg) { g_last_error = msg; }
+
+cudaError_t dc_set_smem(const void *func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(dev, func);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
+}
 
 int dc_cuda_status(cudaError_t e, const char *what) {
   g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
@@ -63,7 +80,18 @@ void free_ctx(dc_ctx *c) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
-  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  for (auto &g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto &r : g.recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+  for (auto &r : c->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->prof_free) cudaEventDestroy(e);
   if (c->have_plan) cufftDestroy(c->plan_z2z);
   cudaGetLastError();
   delete c;
@@ -92,29 +120,73 @@ int check_flags(dc_ctx *c, cudaStream_t s) {
   return DC_OK;
 }
 
-// Records a CUDA event pair around one stage launch on its stream when the profiler is on.
+cudaEvent_t take_event(dc_ctx *c) {
+  cudaEvent_t e = nullptr;
+  if (!c->prof_free.empty()) {
+    e = c->prof_free.back();
+    c->prof_free.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    e = nullptr;
+  }
+  return e;
+}
+
+// Records a CUDA event pair around one stage launch on its stream when the profiler is on.  The
+// record goes to c->prof_sink: the pending list, or the list of a graph being captured.
 struct StageScope {
   dc_ctx *c;
   cudaStream_t s;
-  int stage, nk, idx = -1;
-  double bytes;
-  StageScope(dc_ctx *c_, int stage_, cudaStream_t s_, double bytes_, int nk_)
-      : c(c_), s(s_), stage(stage_), nk(nk_), bytes(bytes_) {
-    if (c->prof_on && c->prof_used + 2 <= (int)c->prof_pool.size()) {
-      idx = c->prof_used;
-      c->prof_used += 2;
-      cudaEventRecord(c->prof_pool[idx], s);
+  ProfRec r{nullptr, nullptr, 0, 0.0, 0};
+  bool on = false;
+  StageScope(dc_ctx *c_, int stage_, cudaStream_t s_, double bytes_, int nk_) : c(c_), s(s_) {
+    if (c->prof_on && c->prof_sink) {
+      r.a = take_event(c);
+      r.b = take_event(c);
+      r.stage = stage_;
+      r.bytes = bytes_;
+      r.nk = nk_;
+      on = r.a && r.b;
+      if (on) cudaEventRecord(r.a, s);
     }
   }
   ~StageScope() {
-    if (idx >= 0) {
-      cudaEventRecord(c->prof_pool[idx + 1], s);
-      c->prof_stage.push_back(stage);
-      c->prof_bytes.push_back(bytes);
-      c->prof_nk.push_back(nk);
+    if (on) {
+      cudaEventRecord(r.b, s);
+      c->prof_sink->push_back(r);
     }
   }
 };
+
+// Add the elapsed times of completed records to the profiler sums (the device must be idle).
+void prof_collect(dc_ctx *c, std::vector<ProfRec> &recs, bool recycle) {
+  for (auto &r : recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.stage] += t;
+      c->prof_by[r.stage] += r.bytes;
+      c->prof_nl[r.stage] += r.nk;
+    } else {
+      cudaGetLastError();
+    }
+    if (recycle) {
+      c->prof_free.push_back(r.a);
+      c->prof_free.push_back(r.b);
+    }
+  }
+  if (recycle) recs.clear();
+}
+
+void destroy_graphs(dc_ctx *c) {
+  for (auto &g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto &r : g.recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  }
+  c->graphs.clear();
+}
 
 double core_elems(const dc_ctx *c) {
   double s = 0.0;
@@ -219,6 +291,104 @@ int density_stage(dc_ctx *c, double *rho, cudaStream_t s) {
 
 inline cudaStream_t S(void *p) { return reinterpret_cast<cudaStream_t>(p); }
 
+// Autotune the stencil launch shape for element type T on block y (scratch block `out`).  With
+// DC_TUNE_CACHE=<file>, shapes are looked up by fragment shape and atom/orbital counts and new
+// results are appended to the file.
+template <typename T>
+int tune(dc_ctx *c, const T *y, T *out, cudaStream_t s) {
+  const int ti = sizeof(T) == 8 ? 1 : 0;
+  char key[160];
+  snprintf(key, sizeof(key), "hstep %dx%dx%d A%d n%d %s", c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms,
+           c->layout.max_norb, ti ? "f64" : "f32");
+  const char *path = getenv("DC_TUNE_CACHE");
+  if (path && path[0]) {
+    FILE *fp = fopen(path, "r");
+    if (fp) {
+      char line[256];
+      while (fgets(line, sizeof(line), fp)) {
+        const size_t kl = strlen(key);
+        if (strncmp(line, key, kl) == 0 && line[kl] == ' ') {
+          c->hstep_shape[ti] = atoi(line + kl + 1);
+        }
+      }
+      fclose(fp);
+      if (c->hstep_shape[ti] >= 0) return DC_OK;
+    }
+  }
+  DC_TRY(dck::launch_project<T>(c, y, cproj<T>(c, 0), s));
+  DC_TRY(dck::tune_hstep<T>(c, y, out, cproj<T>(c, 0), s));
+  if (path && path[0]) {
+    FILE *fp = fopen(path, "a");
+    if (fp) {
+      fprintf(fp, "%s %d\n", key, c->hstep_shape[ti]);
+      fclose(fp);
+    }
+  }
+  return DC_OK;
+}
+
+// Device part of one SCF step; no host synchronisation, so it can be captured into a graph.  The
+// step's scalars and device flags land in pinned host memory (flags at slot 20) and the flags are
+// cleared for the next call.
+int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
+  const double N8 = 8.0 * (double)c->npts;
+  {
+    StageScope sc(c, DC_STAGE_POTENTIAL, s, 7.0 * N8, 3);
+    DC_TRY(dck::launch_potential(c, rin, s));
+  }
+  {
+    StageScope sc(c, DC_STAGE_GATHER, s, 24.0 * (double)c->layout.frag_points, 1);
+    DC_TRY(dck::launch_gather(c, s));
+  }
+  DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
+  DC_TRY(density_stage(c, c->d_rho_out, s));
+  {
+    StageScope sc(c, DC_STAGE_ENERGY, s, 13.0 * N8, 17);
+    DC_TRY(dck::launch_energy(c, rin, s));
+    DC_TRY(dck::launch_mix(c, rin, s));
+  }
+  DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned, c->d_scalar, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned + 20, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaMemsetAsync(c->d_flags, 0, sizeof(unsigned), s));
+  return DC_OK;
+}
+
+// Capture step_body into a new graph; returns its index, or -1 (graphs then stay off for this
+// context and the step runs eagerly) if capture or instantiation is not possible.
+int capture_step(dc_ctx *c, double *rin, cudaStream_t s) {
+  StepGraph g;
+  g.ib_before = c->ib_psi;
+  g.rho = rin;
+  g.prof = c->prof_on;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graphs_enabled = false;
+    return -1;
+  }
+  std::vector<ProfRec> *sink = c->prof_sink;
+  c->prof_sink = &g.recs;
+  const int ib = c->ib_psi;
+  const int st = step_body(c, rin, s);
+  c->prof_sink = sink;
+  g.ib_after = c->ib_psi;
+  c->ib_psi = ib;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st == DC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st != DC_OK || e != cudaSuccess) {
+    cudaGetLastError();
+    for (auto &r : g.recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    c->graphs_enabled = false;
+    return -1;
+  }
+  c->graphs.push_back(std::move(g));
+  return (int)c->graphs.size() - 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -312,7 +482,13 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   }
   // work lists for the Gram and rotation kernels
   {
+    // points per Gram partial: each chunk's sums are FP32 (tensor memory or SIMT pairs) and the
+    // chunks are added in FP64; DC_GRAM_CHUNK overrides (multiple of 64, 64..65536)
     c->gram_chunk = 2048;
+    if (const char *gc = getenv("DC_GRAM_CHUNK")) {
+      const int v = atoi(gc);
+      if (v >= 64 && v <= 65536 && v % 64 == 0) c->gram_chunk = v;
+    }
     std::vector<int2> gi, ri;
     std::vector<long long> goff(c->nfrag);
     std::vector<int> gn(c->nfrag);
@@ -377,7 +553,11 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   c->n_partials = 4096;
   DC_TRY(dmalloc(&c->d_partials, (size_t)c->n_partials));
   DC_TRY(dmalloc(&c->d_slot_w, (size_t)std::max<long long>(1, Lo.natom_frag)));
-  DC_CUDA(cudaMallocHost((void **)&c->h_scalar_pinned, 16 * sizeof(double)));
+  DC_CUDA(cudaMallocHost((void **)&c->h_scalar_pinned, 32 * sizeof(double)));
+  memset(c->h_scalar_pinned, 0, 32 * sizeof(double));
+  c->prof_sink = &c->prof_pending;
+  const char *graphs_env = getenv("DC_GRAPHS");
+  c->graphs_enabled = !(graphs_env && graphs_env[0] == '0');
   // orbital blocks
   const size_t eb = (size_t)Lo.element_bytes;
   for (int k = 0; k < 3; ++k) {
@@ -555,6 +735,7 @@ int dc_warmup(dc_ctx *c, void *stream) {
   if (c->params.precision == DC_FP64) {
     DC_TRY(dck::launch_init_psi(c, (double *)c->blk[0], s));
     c->ib_psi = 0;
+    if (c->hstep_shape[1] < 0) DC_TRY(tune<double>(c, (double *)c->blk[0], (double *)c->blk[1], s));
     DC_TRY(pass_ctx(c, false, 1, s));
     DC_TRY(check_flags(c, s));
     DC_TRY(pass_ctx(c, true, c->params.n_warmup, s));
@@ -564,6 +745,7 @@ int dc_warmup(dc_ctx *c, void *stream) {
     for (int k = 0; k < 3; ++k) DC_TRY(dmalloc(&c->blk64[k], ne));
     int ib = 0;
     int st = dck::launch_init_psi(c, c->blk64[0], s);
+    if (st == DC_OK && c->hstep_shape[1] < 0) st = tune<double>(c, c->blk64[0], c->blk64[1], s);
     if (st == DC_OK) st = chefsi_pass<double>(c, c->blk64, ib, false, s);
     if (st == DC_OK) st = check_flags(c, s);
     for (int p = 0; st == DC_OK && p < c->params.n_warmup; ++p) st = chefsi_pass<double>(c, c->blk64, ib, true, s);
@@ -575,6 +757,7 @@ int dc_warmup(dc_ctx *c, void *stream) {
     }
     DC_TRY(st);
     c->ib_psi = 0;
+    if (c->hstep_shape[0] < 0) DC_TRY(tune<float>(c, (float *)c->blk[0], (float *)c->blk[1], s));
   }
   DC_TRY(check_flags(c, s));
   c->warmed = true;
@@ -629,25 +812,39 @@ int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, vo
     DC_CUDA(cudaMemcpyAsync(c->d_work, rho, nb, cudaMemcpyHostToDevice, s));
     rin = c->d_work;
   }
-  const double N8 = 8.0 * (double)c->npts;
-  {
-    StageScope sc(c, DC_STAGE_POTENTIAL, s, 7.0 * N8, 3);
-    DC_TRY(dck::launch_potential(c, rin, s));
+  // After one eager step (which also sets every kernel attribute), the device part of the step is
+  // captured once per (state block, rho pointer, profiler on) and replayed as a CUDA graph.
+  int gi = -1;
+  if (c->graphs_enabled && c->steps_done >= 1) {
+    for (size_t k = 0; k < c->graphs.size(); ++k)
+      if (c->graphs[k].ib_before == c->ib_psi && c->graphs[k].rho == rin && c->graphs[k].prof == c->prof_on)
+        gi = (int)k;
+    if (gi < 0) {
+      if (c->graphs.size() >= 12) destroy_graphs(c);
+      gi = capture_step(c, rin, s);
+    }
   }
-  {
-    StageScope sc(c, DC_STAGE_GATHER, s, 24.0 * (double)c->layout.frag_points, 1);
-    DC_TRY(dck::launch_gather(c, s));
-  }
-  DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
-  DC_TRY(density_stage(c, c->d_rho_out, s));
-  {
-    StageScope sc(c, DC_STAGE_ENERGY, s, 13.0 * N8, 17);
-    DC_TRY(dck::launch_energy(c, rin, s));
-    DC_TRY(dck::launch_mix(c, rin, s));
+  if (gi >= 0) {
+    DC_CUDA(cudaGraphLaunch(c->graphs[gi].exec, s));
+    c->ib_psi = c->graphs[gi].ib_after;
+  } else {
+    DC_TRY(step_body(c, rin, s));
   }
   if (rho_on_host) DC_CUDA(cudaMemcpyAsync(rho, c->d_work, nb, cudaMemcpyDeviceToHost, s));
-  DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned, c->d_scalar, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  const int st = check_flags(c, s);
+  DC_CUDA(cudaStreamSynchronize(s));
+  if (gi >= 0 && c->graphs[gi].prof) prof_collect(c, c->graphs[gi].recs, false);
+  int st = DC_OK;
+  const unsigned fl = *reinterpret_cast<const unsigned *>(c->h_scalar_pinned + 20);
+  if (fl & DC_FLAG_TIMEOUT) {
+    dc_set_error("a bounded device wait ran out (grid barrier)");
+    st = DC_ERR_TIMEOUT;
+  } else if (fl & DC_FLAG_NOTSPD) {
+    dc_set_error("Gram matrix not positive definite in at least one fragment");
+    st = DC_ERR_NOCONV;
+  } else if (fl & DC_FLAG_NONFINITE) {
+    dc_set_error("non-finite eigenvalue or chemical potential");
+    st = DC_ERR_NONFINITE;
+  }
   c->steps_done++;
   if (h_stats) {
     const double *v = c->h_scalar_pinned;
@@ -718,39 +915,43 @@ int dc_eb_adjoint(dc_ctx *c, const void *d_psi, int dtype, const double *d_occ, 
   return DC_OK;
 }
 
+int dc_tuning(const dc_ctx *c, int *h_shape, float *h_ms) {
+  if (!c || !h_shape) {
+    dc_set_error("dc_tuning: NULL argument");
+    return DC_ERR_ARG;
+  }
+  for (int t = 0; t < 2; ++t) {
+    h_shape[2 * t] = h_shape[2 * t + 1] = 0;
+    if (c->hstep_shape[t] >= 0) dck::hstep_shape_info(c->hstep_shape[t], &h_shape[2 * t], &h_shape[2 * t + 1]);
+    if (h_ms)
+      for (int k = 0; k < 8; ++k) h_ms[8 * t + k] = c->tune_ms[t][k];
+  }
+  return DC_OK;
+}
+
 int dc_profile(dc_ctx *c, int enable) {
   if (!c) return DC_ERR_ARG;
+  DC_CUDA(cudaDeviceSynchronize());
+  prof_collect(c, c->prof_pending, true);
   if (enable) {
-    if (c->prof_pool.empty()) {
-      c->prof_pool.resize(8192);
-      for (auto &e : c->prof_pool) DC_CUDA(cudaEventCreate(&e));
+    for (int i = 0; i < DC_NSTAGES; ++i) {
+      c->prof_ms[i] = c->prof_by[i] = 0.0;
+      c->prof_nl[i] = 0;
     }
-    c->prof_used = 0;
-    c->prof_stage.clear();
-    c->prof_bytes.clear();
-    c->prof_nk.clear();
   }
   c->prof_on = enable != 0;
+  c->prof_sink = &c->prof_pending;
   return DC_OK;
 }
 
 int dc_profile_read(dc_ctx *c, double *h_ms, int64_t *h_launches, double *h_bytes) {
   if (!c) return DC_ERR_ARG;
   DC_CUDA(cudaDeviceSynchronize());
-  double ms[DC_NSTAGES] = {0}, by[DC_NSTAGES] = {0};
-  int64_t nl[DC_NSTAGES] = {0};
-  for (size_t k = 0; k < c->prof_stage.size(); ++k) {
-    float t = 0.f;
-    DC_CUDA(cudaEventElapsedTime(&t, c->prof_pool[2 * k], c->prof_pool[2 * k + 1]));
-    const int st = c->prof_stage[k];
-    ms[st] += t;
-    by[st] += c->prof_bytes[k];
-    nl[st] += c->prof_nk[k];
-  }
+  prof_collect(c, c->prof_pending, true);
   for (int i = 0; i < DC_NSTAGES; ++i) {
-    if (h_ms) h_ms[i] = ms[i];
-    if (h_bytes) h_bytes[i] = by[i];
-    if (h_launches) h_launches[i] = nl[i];
+    if (h_ms) h_ms[i] = c->prof_ms[i];
+    if (h_bytes) h_bytes[i] = c->prof_by[i];
+    if (h_launches) h_launches[i] = c->prof_nl[i];
   }
   return DC_OK;
 }

@@ -31,6 +31,10 @@ struct FragDesc {
   int pad;
 };
 
+// Row stride of one atom slot's projector factors [gx (Ex) | gy (Ey) | gz (Ez) | pad], kept even so
+// that pairs of x-adjacent factors can be read as one vector.
+__host__ __device__ inline int tab_width(const FragDesc &D) { return (D.E[0] + D.E[1] + D.E[2] + 1) & ~1; }
+
 // Per-(fragment, atom slot) projector data.
 struct ProjSlot {
   int atom;       // global atom index
@@ -49,6 +53,21 @@ struct ProjSlot {
 #define DC_FLAG_NOTSPD 1u
 #define DC_FLAG_TIMEOUT 2u
 #define DC_FLAG_NONFINITE 4u
+
+struct ProfRec {
+  cudaEvent_t a, b;
+  int stage;
+  double bytes;
+  int nk;
+};
+
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  int ib_before = 0, ib_after = 0;
+  const double *rho = nullptr;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+};
 
 struct dc_ctx {
   // configuration
@@ -143,13 +162,22 @@ struct dc_ctx {
   double *d_adj_fd = nullptr;
   double *d_dots = nullptr;
 
-  // stage profiler
+  // stage profiler: event pairs recorded around each stage; eager records wait in prof_pending,
+  // records captured into a CUDA graph belong to that graph and are read after each replay
   bool prof_on = false;
-  std::vector<cudaEvent_t> prof_pool;
-  std::vector<int> prof_stage;       // stage of each recorded (start, end) pair
-  std::vector<double> prof_bytes;    // algorithmic bytes of each pair
-  std::vector<int> prof_nk;          // kernel launches of each pair
-  int prof_used = 0;                 // events used in the pool
+  std::vector<ProfRec> prof_pending;
+  std::vector<ProfRec> *prof_sink = nullptr;  // where new records go (pending or a graph's list)
+  std::vector<cudaEvent_t> prof_free;
+  double prof_ms[DC_NSTAGES] = {0}, prof_by[DC_NSTAGES] = {0};
+  long long prof_nl[DC_NSTAGES] = {0};
+
+  // CUDA graphs of the SCF step, keyed by (state block, rho pointer, profiler on)
+  std::vector<StepGraph> graphs;
+  bool graphs_enabled = true;
+
+  // autotuned launch shape of the stencil kernel per element type ([0] FP32, [1] FP64; -1 = default)
+  int hstep_shape[2] = {-1, -1};
+  float tune_ms[2][8] = {{0}};
 
   int steps_done = 0;
   bool warmed = false;
@@ -170,6 +198,10 @@ void dc_build_cover(const dc_ctx *c, int d, std::vector<int> &beg, std::vector<i
 // ---------------------------------------------------------------------------------------------
 void dc_set_error(const std::string &msg);
 int dc_cuda_status(cudaError_t e, const char *what);
+
+// Raise a kernel's dynamic shared-memory limit on the current device, once per (device, kernel, size):
+// later calls (including those made while a stream is being captured) do no CUDA API work.
+cudaError_t dc_set_smem(const void *func, size_t bytes);
 
 #define DC_CUDA(call)                                          \
   do {                                                         \
@@ -201,6 +233,9 @@ int launch_convert(const float *src, double *dst, long long n, cudaStream_t s);
 // fragment Hamiltonian
 template <typename T>
 int launch_project(dc_ctx *c, const T *psi, T *cout, cudaStream_t s);
+template <typename T>
+int tune_hstep(dc_ctx *c, const T *y, T *out, T *cbuf, cudaStream_t s);
+int hstep_shape_info(int shape, int *threads, int *pairs);
 template <typename T>
 int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T *yout, const T *cin, T *cout,
                  const double *Datom, const double *occ, double *dots, const T *vf, cudaStream_t s);

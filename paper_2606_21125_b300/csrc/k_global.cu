@@ -106,7 +106,7 @@ __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const dou
   if (threadIdx.x == 0) {
     double m = red[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    const int tabw = D.E[0] + D.E[1] + D.E[2];
+    const int tabw = tab_width(D);
     double nl = 0.0;
     for (int k = 0; k < D.natom; ++k) {
       const ProjSlot S = slots[D.at_off + k];

@@ -4,13 +4,23 @@
 // 25-point Laplacian and ghost points that are zero (buffer edge) or wrap within the fragment.
 // The projectors are separable, p_a(j) = C_a gx_a[jx] gy_a[jy] gz_a[jz].
 //
-// One CTA handles one (fragment, orbital) item and streams the fragment along z: every thread
-// owns PPT points of the xy-plane and keeps their 9-deep z column in registers; the current plane
-// sits in shared memory with a 4-point halo (zeros, or wrapped values for the periodic boundary)
-// so the x and y taps need no bounds tests.  The nonlocal term uses the projections of the input
-// (computed beforehand) and per-plane coefficients; the projections of the output, which the next
-// Chebyshev step needs, are accumulated plane by plane in the epilogue by one warp per atom, in a
-// fixed order (deterministic).
+// One CTA handles one (fragment, orbital) item and streams the fragment along z.  Each thread owns
+// pairs of x-adjacent points of the xy-plane and keeps their 9-deep z columns in registers; the
+// current plane sits in shared memory with a 4-point halo (zeros, or wrapped values for the
+// periodic boundary), so the x and y taps are unconditional vector loads shared by the pair, and
+// the pair is updated with paired FP32 instructions (FFMA2/FADD2).
+//
+// The Laplacian is evaluated in difference form, sum_n k_n [(y_{+n} - y) + (y_{-n} - y)], which
+// equals the textbook form because c_0 = -2 sum_n c_n; the differences of neighbouring values are
+// exact in floating point for smooth orbitals, so the large centre and neighbour terms never cancel
+// in rounded arithmetic (100x smaller FP32 error at the same data movement).
+//
+// Nonlocal term: for each plane, warps compact, per row y, the atoms whose projector touches (y, z)
+// into (slot, D_a C_a <p_a|y> gz_a[z] gy_a[y]) records; a point adds u * gx_a[x] over its row's
+// records only.  The projections of the output, which the next Chebyshev step needs, are
+// accumulated one plane behind: one task per (row, atom of that row) forms sum_x gx_a[x] out(x, y)
+// and adds it into a dense [row][atom] array (each slot has one writer per plane, so the order is
+// fixed and the result deterministic); the rows are summed at the end.
 #include "dc_internal.h"
 
 namespace {
@@ -38,9 +48,52 @@ struct HArgs {
   int mode;
   int periodic;
   double dV;
-  T k0;      // -1/2 c0 sum_d 1/h_d^2
   T kx[5], ky[5], kz[5];  // -1/2 c_n / h_d^2
 };
+
+// Arithmetic on the two points of a pair: paired FP32 instructions, scalar pairs for FP64.
+template <typename T>
+struct P2;
+template <>
+struct P2<float> {
+  using V = float2;
+  static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V splat(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+};
+template <>
+struct P2<double> {
+  using V = double2;
+  static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ V splat(double a) { return make_double2(a, a); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+  static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+};
+
+// Row-list record: atom slot and its coefficient for the row and plane.
+template <typename T>
+struct RLE;
+template <>
+struct __align__(8) RLE<float> {
+  int k;
+  float u;
+};
+template <>
+struct __align__(16) RLE<double> {
+  int k;
+  int pad;
+  double u;
+};
+
+template <typename T>
+__device__ __forceinline__ typename P2<T>::V ld2(const T *p) {
+  return *reinterpret_cast<const typename P2<T>::V *>(p);
+}
 
 template <typename T>
 __device__ __forceinline__ T ldz(const T *base, int zz, int Ez, int plane, int t, bool valid, int periodic) {
@@ -66,35 +119,68 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
   return s;  // valid in thread 0
 }
 
-// Projection of one plane (values in `pl`, row pitch Ex) onto every atom of the plane's list;
-// accumulates gz[k][z] * sum_y gy[k][y] sum_x gx[k][x] pl[y][x] into acc[k].  Atom slot k is
-// always handled by warp k % nwarps, so the summation order is fixed.
+// Build the per-row atom lists of plane z: for every row y, the slots k of the plane's z-list whose
+// y factor is non-zero there, with u = sk[k] gz_k[z] gy_k[y] (sk may be null: u = 0).  One warp
+// per row, compaction by ballot; kl (slots only) or rl (slot and u) receives the records.
 template <typename T, int NT>
-__device__ __forceinline__ void project_plane(const T *pl, int z, int Ex, int Ey, const T *stab, int tabw,
-                                              const int *zl_b, const int *zl_i, const int4 *box, T *acc) {
+__device__ __forceinline__ void build_rows(int z, int Ex, int Ey, int A, const T *stab, int tabw, const int *zl_b,
+                                           const int *zl_i, const T *sk, RLE<T> *rl, int *kl, int *rn) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int beg = zl_b[z], end = zl_b[z + 1];
-  for (int e = beg; e < end; ++e) {
-    const int k = zl_i[e];
-    if ((k % (NT / 32)) != warp) continue;
-    const T *gx = stab + k * tabw;
-    const T *gy = gx + Ex;
-    const T *gz = gy + Ey;
-    const int4 bx = box[k];  // x lo, x hi, y lo, y hi
-    T s = T(0);
-    for (int y = bx.z + lane; y < bx.w; y += 32) {
-      T r = T(0);
-      const T *row = pl + y * Ex;
-      for (int x = bx.x; x < bx.y; ++x) r += gx[x] * row[x];
-      s += gy[y] * r;
+  const int zbeg = zl_b[z], zend = zl_b[z + 1];
+  for (int y = warp; y < Ey; y += NT / 32) {
+    int cnt = 0;
+    for (int e0 = zbeg; e0 < zend; e0 += 32) {
+      const int e = e0 + lane;
+      int k = 0;
+      T gzy = T(0);
+      if (e < zend) {
+        k = zl_i[e];
+        const T *g = stab + k * tabw;
+        gzy = g[Ex + Ey + z] * g[Ex + y];
+      }
+      const bool in = gzy != T(0);
+      const unsigned m = __ballot_sync(0xffffffffu, in);
+      if (in) {
+        const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+        if (rl) {
+          RLE<T> r;
+          r.k = k;
+          r.u = sk ? sk[k] * gzy : T(0);
+          rl[y * A + pos] = r;
+        } else {
+          kl[y * A + pos] = k;
+        }
+      }
+      cnt += __popc(m);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) acc[k] += gz[z] * s;
+    if (lane == 0) rn[y] = cnt;
   }
 }
 
-template <typename T, int NT, int PPT>
-__global__ void __launch_bounds__(NT) k_hstep(HArgs<T> a) {
+// Projection tasks of one plane (values pl[y][x], row pitch Ex): for each row y and each listed
+// slot k, pacc[y][k] += gz_k[z] gy_k[y] sum_x gx_k[x] pl[y][x].  Slot (y, k) has one writer.
+template <typename T, int NT>
+__device__ __forceinline__ void project_rows(const T *pl, int z, int Ex, int Ey, int A, const T *stab, int tabw,
+                                             const int4 *box, const RLE<T> *rl, const int *kl, const int *rn,
+                                             T *pacc) {
+  const int nslot = Ey * A;
+  for (int s = threadIdx.x; s < nslot; s += NT) {
+    const int y = s % Ey, e = s / Ey;
+    if (e >= rn[y]) continue;
+    const int k = rl ? rl[y * A + e].k : kl[y * A + e];
+    const T *g = stab + k * tabw;
+    const int4 bx = box[k];
+    const T *row = pl + y * Ex;
+    T w = T(0);
+    for (int x = bx.x; x < bx.y; ++x) w += g[x] * row[x];
+    pacc[y * A + k] += g[Ex + Ey + z] * g[Ex + y] * w;
+  }
+}
+
+template <typename T, int NT, int PP>
+__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
+  using Op = P2<T>;
+  using V = typename Op::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int item = blockIdx.x;
   const int2 fi = a.items[item];
@@ -102,26 +188,30 @@ __global__ void __launch_bounds__(NT) k_hstep(HArgs<T> a) {
   const FragDesc D = a.desc[f];
   const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2];
   const int plane = Ex * Ey;
-  const int pitch = Ex + 8;
+  const int nxp = (Ex + 1) >> 1;
+  const int npairs = nxp * Ey;
+  const int pitch = (Ex + 9) & ~1;  // >= Ex + 8, even
   const int pplane = pitch * (Ey + 8);
   const long long P = (long long)plane * Ez;
   const int A = D.natom;
-  const int tabw = Ex + Ey + Ez;
+  const int tabw = tab_width(D);
+  const bool proj = a.cout != nullptr;
 
-  // shared memory carve-up
-  T *sp = reinterpret_cast<T *>(smem_raw);
-  T *pin = sp;                      // [2][pplane]
-  T *pout = pin + 2 * pplane;       // [2][plane]
-  T *stab = pout + 2 * plane;       // [A][tabw]
-  T *sk = stab + A * tabw;          // [A] apply strengths
-  T *acc = sk + A;                  // [A] output projections
-  T *tz = acc + A;                  // [2][A] per-plane coefficients
-  T *red = tz + 2 * A;              // [NT/32]
-  size_t ioff = (size_t)(2 * pplane + 2 * plane + A * tabw + 4 * A + NT / 32) * sizeof(T);
-  ioff = (ioff + 15) & ~(size_t)15;
-  int *zl_b = reinterpret_cast<int *>(smem_raw + ioff);  // [Ez+1], 16-byte aligned
-  int4 *box = reinterpret_cast<int4 *>(zl_b + ((Ez + 1 + 3) & ~3));  // [A]
-  int *zl_i = reinterpret_cast<int *>(box + A);        // [list]
+  // shared memory: element arrays (vector-read ones first, at even offsets), then 16-byte aligned
+  // records and integers
+  T *pin = reinterpret_cast<T *>(smem_raw);  // [2][pplane]
+  T *stab = pin + 2 * pplane;                // [A][tabw]
+  T *pout = stab + A * tabw;                 // [2][plane]
+  T *pacc = pout + 2 * plane;                // [Ey][A]
+  T *sk = pacc + Ey * A;                     // [A]
+  T *red = sk + A;                           // [NT/32]
+  size_t off = (size_t)(2 * pplane + A * tabw + 2 * plane + Ey * A + A + NT / 32) * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  int4 *box = reinterpret_cast<int4 *>(smem_raw + off);         // [A]
+  RLE<T> *rl = reinterpret_cast<RLE<T> *>(box + A);             // [2][Ey][A]
+  int *rn = reinterpret_cast<int *>(rl + 2 * Ey * A);           // [2][Ey]
+  int *zl_b = rn + 2 * Ey;                                      // [Ez+1]
+  int *zl_i = zl_b + Ez + 1;                                    // [list]
 
   const int zb0 = a.zl_beg[D.zl_off];
   const int nzl = a.zl_beg[D.zl_off + Ez] - zb0;
@@ -132,8 +222,8 @@ __global__ void __launch_bounds__(NT) k_hstep(HArgs<T> a) {
     const ProjSlot S = a.slots[D.at_off + k];
     box[k] = make_int4(S.lo[0], S.hi[0], S.lo[1], S.hi[1]);
     sk[k] = a.cin ? T(a.Datom[S.atom] * S.coef) * a.cin[D.c_off + (long long)i * A + k] : T(0);
-    acc[k] = T(0);
   }
+  for (int t = threadIdx.x; t < Ey * A; t += NT) pacc[t] = T(0);
   for (int t = threadIdx.x; t < 2 * pplane; t += NT) pin[t] = T(0);
 
   T alpha = T(1), beta = T(0), shift = T(0);
@@ -148,18 +238,23 @@ __global__ void __launch_bounds__(NT) k_hstep(HArgs<T> a) {
   const T *ypv = use_prev ? a.yprev + D.psi_off + (long long)i * P : nullptr;
   T *yout = a.yout ? a.yout + D.psi_off + (long long)i * P : nullptr;
   const T *vf = a.vf + D.pt_off;
+  const T occ2 = a.mode == HSTEP_ADJ ? T(2.0 * a.occ[D.st_off + i] * a.dV) : T(0);
 
-  int px[PPT], py[PPT];
-  bool valid[PPT];
-  T q[PPT][9];
+  int px[PP], py[PP];
+  bool valid[PP], v1[PP];
+  V q[PP][9];
 #pragma unroll
-  for (int r = 0; r < PPT; ++r) {
-    const int t = threadIdx.x + r * NT;
-    valid[r] = t < plane;
-    py[r] = valid[r] ? t / Ex : 0;
-    px[r] = valid[r] ? t - py[r] * Ex : 0;
+  for (int r = 0; r < PP; ++r) {
+    const int p = threadIdx.x + r * NT;
+    valid[r] = p < npairs;
+    py[r] = valid[r] ? p / nxp : 0;
+    px[r] = valid[r] ? 2 * (p - py[r] * nxp) : 0;
+    v1[r] = valid[r] && (px[r] + 1 < Ex);
+    const int t0 = px[r] + py[r] * Ex;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) q[r][k] = ldz(yin, k - 4, Ez, plane, t, valid[r], a.periodic);
+    for (int k = 0; k < 9; ++k)
+      q[r][k] = Op::mk(ldz(yin, k - 4, Ez, plane, t0, valid[r], a.periodic),
+                       ldz(yin, k - 4, Ez, plane, t0 + 1, v1[r], a.periodic));
   }
   __syncthreads();
 
@@ -168,78 +263,111 @@ __global__ void __launch_bounds__(NT) k_hstep(HArgs<T> a) {
     const int buf = z & 1;
     T *P0 = pin + buf * pplane;
 #pragma unroll
-    for (int r = 0; r < PPT; ++r) {
-      if (!valid[r]) continue;
-      const int x = px[r], y = py[r];
-      const T v = q[r][4];
-      P0[(y + 4) * pitch + x + 4] = v;
-      if (a.periodic) {
-        if (x < 4) P0[(y + 4) * pitch + x + Ex + 4] = v;
-        if (x >= Ex - 4) P0[(y + 4) * pitch + x - Ex + 4] = v;
-        if (y < 4) P0[(y + Ey + 4) * pitch + x + 4] = v;
-        if (y >= Ey - 4) P0[(y - Ey + 4) * pitch + x + 4] = v;
+    for (int r = 0; r < PP; ++r) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!(h == 0 ? valid[r] : v1[r])) continue;
+        const int x = px[r] + h, y = py[r];
+        const T v = h == 0 ? q[r][4].x : q[r][4].y;
+        P0[(y + 4) * pitch + x + 4] = v;
+        if (a.periodic) {
+          if (x < 4) P0[(y + 4) * pitch + x + Ex + 4] = v;
+          if (x >= Ex - 4) P0[(y + 4) * pitch + x - Ex + 4] = v;
+          if (y < 4) P0[(y + Ey + 4) * pitch + x + 4] = v;
+          if (y >= Ey - 4) P0[(y - Ey + 4) * pitch + x + 4] = v;
+        }
       }
     }
-    const int zbeg = zl_b[z], zend = zl_b[z + 1];
-    T *tzb = tz + buf * A;
-    for (int e = zbeg + threadIdx.x; e < zend; e += NT) {
-      const int k = zl_i[e];
-      tzb[e - zbeg] = sk[k] * stab[k * tabw + Ex + Ey + z];
-    }
+    RLE<T> *RL = rl + buf * Ey * A;
+    int *RN = rn + buf * Ey;
+    build_rows<T, NT>(z, Ex, Ey, A, stab, tabw, zl_b, zl_i, sk, RL, nullptr, RN);
     __syncthreads();
-    if (a.cout && z > 0)
-      project_plane<T, NT>(pout + ((z - 1) & 1) * plane, z - 1, Ex, Ey, stab, tabw, zl_b, zl_i, box, acc);
+    if (proj && z > 0) {
+      const int pb = (z - 1) & 1;
+      project_rows<T, NT>(pout + pb * plane, z - 1, Ex, Ey, A, stab, tabw, box, rl + pb * Ey * A, nullptr,
+                          rn + pb * Ey, pacc);
+    }
 
 #pragma unroll
-    for (int r = 0; r < PPT; ++r) {
+    for (int r = 0; r < PP; ++r) {
       if (!valid[r]) continue;
       const int x = px[r], y = py[r];
-      const int t = x + y * Ex;
       const T *c0 = P0 + (y + 4) * pitch + x + 4;
-      const T cv = q[r][4];
-      T hy = a.k0 * cv;
+      const V cv = q[r][4];
+      V hv = Op::splat(T(0));
+      {
+        // x taps: values at x-4 .. x+5 (five aligned pairs)
+        T xv[10];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const V v = ld2(c0 - 4 + 2 * j);
+          xv[2 * j] = v.x;
+          xv[2 * j + 1] = v.y;
+        }
+#pragma unroll
+        for (int n = 1; n <= 4; ++n) {
+          const V pa = Op::mk(xv[4 + n], xv[5 + n]);
+          const V pb = Op::mk(xv[4 - n], xv[5 - n]);
+          hv = Op::fma(Op::splat(a.kx[n]), Op::add(Op::sub(pa, cv), Op::sub(pb, cv)), hv);
+        }
+      }
 #pragma unroll
       for (int n = 1; n <= 4; ++n) {
-        hy += a.kz[n] * (q[r][4 + n] + q[r][4 - n]);
-        hy += a.ky[n] * (c0[n * pitch] + c0[-n * pitch]);
-        hy += a.kx[n] * (c0[n] + c0[-n]);
+        const V up = ld2(c0 + n * pitch);
+        const V dn = ld2(c0 - n * pitch);
+        hv = Op::fma(Op::splat(a.ky[n]), Op::add(Op::sub(up, cv), Op::sub(dn, cv)), hv);
       }
-      hy += vf[(long long)z * plane + t] * cv;
-      T nl = T(0);
-      for (int e = zbeg; e < zend; ++e) {
-        const int k = zl_i[e];
-        const T *g = stab + k * tabw;
-        nl += tzb[e - zbeg] * (g[Ex + y] * g[x]);
-      }
-      hy += nl;
-      T out;
-      if (a.mode == HSTEP_CHEB) {
-        out = alpha * (hy - shift * cv);
-        if (use_prev) out += beta * ypv[(long long)z * plane + t];
-      } else if (a.mode == HSTEP_ADJ) {
-        dot += cv * hy;
-        out = T(2.0 * a.occ[D.st_off + i] * a.dV) * hy;
-      } else {
-        out = hy;
-      }
-      if (yout) yout[(long long)z * plane + t] = out;
-      if (a.cout) pout[buf * plane + t] = out;
-    }
-    // advance the z column
 #pragma unroll
-    for (int r = 0; r < PPT; ++r) {
+      for (int n = 1; n <= 4; ++n)
+        hv = Op::fma(Op::splat(a.kz[n]), Op::add(Op::sub(q[r][4 + n], cv), Op::sub(q[r][4 - n], cv)), hv);
+      const long long o0 = (long long)z * plane + y * Ex + x;
+      hv = Op::fma(Op::mk(vf[o0], v1[r] ? vf[o0 + 1] : T(0)), cv, hv);
+      const int cnt = RN[y];
+      const RLE<T> *ry = RL + y * A;
+      for (int e = 0; e < cnt; ++e) {
+        const RLE<T> rec = ry[e];
+        hv = Op::fma(Op::splat(rec.u), ld2(stab + rec.k * tabw + x), hv);
+      }
+      V out;
+      if (a.mode == HSTEP_CHEB) {
+        out = Op::mul(Op::splat(alpha), Op::fma(Op::splat(-shift), cv, hv));
+        if (use_prev) out = Op::fma(Op::splat(beta), Op::mk(ypv[o0], v1[r] ? ypv[o0 + 1] : T(0)), out);
+      } else if (a.mode == HSTEP_ADJ) {
+        dot += cv.x * hv.x + (v1[r] ? cv.y * hv.y : T(0));
+        out = Op::mul(Op::splat(occ2), hv);
+      } else {
+        out = hv;
+      }
+      if (yout) {
+        yout[o0] = out.x;
+        if (v1[r]) yout[o0 + 1] = out.y;
+      }
+      if (proj) {
+        pout[buf * plane + y * Ex + x] = out.x;
+        if (v1[r]) pout[buf * plane + y * Ex + x + 1] = out.y;
+      }
+    }
+    // advance the z columns
+#pragma unroll
+    for (int r = 0; r < PP; ++r) {
+      const int t0 = px[r] + py[r] * Ex;
 #pragma unroll
       for (int k = 0; k < 8; ++k) q[r][k] = q[r][k + 1];
-      q[r][8] = ldz(yin, z + 5, Ez, plane, threadIdx.x + r * NT, valid[r], a.periodic);
+      q[r][8] = Op::mk(ldz(yin, z + 5, Ez, plane, t0, valid[r], a.periodic),
+                       ldz(yin, z + 5, Ez, plane, t0 + 1, v1[r], a.periodic));
     }
   }
-  if (a.cout) {
+  if (proj) {
     __syncthreads();
-    project_plane<T, NT>(pout + ((Ez - 1) & 1) * plane, Ez - 1, Ex, Ey, stab, tabw, zl_b, zl_i, box, acc);
+    const int pb = (Ez - 1) & 1;
+    project_rows<T, NT>(pout + pb * plane, Ez - 1, Ex, Ey, A, stab, tabw, box, rl + pb * Ey * A, nullptr,
+                        rn + pb * Ey, pacc);
     __syncthreads();
     for (int k = threadIdx.x; k < A; k += NT) {
+      T s = T(0);
+      for (int y = 0; y < Ey; ++y) s += pacc[y * A + k];
       const ProjSlot S = a.slots[D.at_off + k];
-      a.cout[D.c_off + (long long)i * A + k] = T(S.coef * a.dV) * acc[k];
+      a.cout[D.c_off + (long long)i * A + k] = T(S.coef * a.dV) * s;
     }
   }
   if (a.mode == HSTEP_ADJ) {
@@ -248,7 +376,8 @@ __global__ void __launch_bounds__(NT) k_hstep(HArgs<T> a) {
   }
 }
 
-// Projections c[k] = C_k dV sum_j p_k(j) y(j) of one orbital block (no stencil).
+// Projections c[k] = C_k dV sum_j p_k(j) y(j) of one orbital block (no stencil), with the same
+// row-list tasks as the H-apply epilogue.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_project(HArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -260,16 +389,17 @@ __global__ void __launch_bounds__(NT) k_project(HArgs<T> a) {
   const int plane = Ex * Ey;
   const long long P = (long long)plane * Ez;
   const int A = D.natom;
-  const int tabw = Ex + Ey + Ez;
-  T *sp = reinterpret_cast<T *>(smem_raw);
-  T *pl = sp;                 // [2][plane]
-  T *stab = pl + 2 * plane;   // [A][tabw]
-  T *acc = stab + A * tabw;   // [A]
-  size_t ioff = (size_t)(2 * plane + A * tabw + A) * sizeof(T);
-  ioff = (ioff + 15) & ~(size_t)15;
-  int *zl_b = reinterpret_cast<int *>(smem_raw + ioff);
-  int4 *box = reinterpret_cast<int4 *>(zl_b + ((Ez + 1 + 3) & ~3));
-  int *zl_i = reinterpret_cast<int *>(box + A);
+  const int tabw = tab_width(D);
+  T *pl = reinterpret_cast<T *>(smem_raw);  // [2][plane]
+  T *stab = pl + 2 * plane;                 // [A][tabw]
+  T *pacc = stab + A * tabw;                // [Ey][A]
+  size_t off = (size_t)(2 * plane + A * tabw + Ey * A) * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  int4 *box = reinterpret_cast<int4 *>(smem_raw + off);  // [A]
+  int *kl = reinterpret_cast<int *>(box + A);            // [2][Ey][A]
+  int *rn = kl + 2 * Ey * A;                             // [2][Ey]
+  int *zl_b = rn + 2 * Ey;                               // [Ez+1]
+  int *zl_i = zl_b + Ez + 1;                             // [list]
   const int zb0 = a.zl_beg[D.zl_off];
   const int nzl = a.zl_beg[D.zl_off + Ez] - zb0;
   for (int t = threadIdx.x; t < A * tabw; t += NT) stab[t] = a.tab[D.tab_off + t];
@@ -278,19 +408,24 @@ __global__ void __launch_bounds__(NT) k_project(HArgs<T> a) {
   for (int k = threadIdx.x; k < A; k += NT) {
     const ProjSlot S = a.slots[D.at_off + k];
     box[k] = make_int4(S.lo[0], S.hi[0], S.lo[1], S.hi[1]);
-    acc[k] = T(0);
   }
+  for (int t = threadIdx.x; t < Ey * A; t += NT) pacc[t] = T(0);
+  __syncthreads();
   const T *yin = a.yin + D.psi_off + (long long)i * P;
   for (int z = 0; z < Ez; ++z) {
-    T *cur = pl + (z & 1) * plane;
+    const int buf = z & 1;
+    T *cur = pl + buf * plane;
     for (int t = threadIdx.x; t < plane; t += NT) cur[t] = yin[(long long)z * plane + t];
+    build_rows<T, NT>(z, Ex, Ey, A, stab, tabw, zl_b, zl_i, nullptr, nullptr, kl + buf * Ey * A, rn + buf * Ey);
     __syncthreads();
-    project_plane<T, NT>(cur, z, Ex, Ey, stab, tabw, zl_b, zl_i, box, acc);
+    project_rows<T, NT>(cur, z, Ex, Ey, A, stab, tabw, box, nullptr, kl + buf * Ey * A, rn + buf * Ey, pacc);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < A; k += NT) {
+    T s = T(0);
+    for (int y = 0; y < Ey; ++y) s += pacc[y * A + k];
     const ProjSlot S = a.slots[D.at_off + k];
-    a.cout[D.c_off + (long long)i * A + k] = T(S.coef * a.dV) * acc[k];
+    a.cout[D.c_off + (long long)i * A + k] = T(S.coef * a.dV) * s;
   }
 }
 
@@ -324,47 +459,85 @@ HArgs<T> make_args(dc_ctx *c) {
   a.dV = c->dV;
   // 8th-order central second-derivative weights (exact rationals), scaled by -1/2 h^-2
   const double fd[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
-  double w[3];
-  for (int d = 0; d < 3; ++d) w[d] = 1.0 / (c->h[d] * c->h[d]);
-  a.k0 = T(-0.5 * fd[0] * (w[0] + w[1] + w[2]));
   for (int n = 0; n < 5; ++n) {
-    a.kx[n] = T(-0.5 * fd[n] * w[0]);
-    a.ky[n] = T(-0.5 * fd[n] * w[1]);
-    a.kz[n] = T(-0.5 * fd[n] * w[2]);
+    a.kx[n] = T(-0.5 * fd[n] / (c->h[0] * c->h[0]));
+    a.ky[n] = T(-0.5 * fd[n] / (c->h[1] * c->h[1]));
+    a.kz[n] = T(-0.5 * fd[n] / (c->h[2] * c->h[2]));
   }
   return a;
+}
+
+int max_tabw(const dc_ctx *c) {
+  int w = 0;
+  for (const auto &D : c->h_desc) w = w > tab_width(D) ? w : tab_width(D);
+  return w;
 }
 
 size_t hstep_smem(dc_ctx *c, size_t esz, int NT) {
   const int Ex = c->max_E[0], Ey = c->max_E[1], Ez = c->max_E[2];
   const int A = c->max_atoms;
-  size_t n = 2 * (size_t)(Ex + 8) * (Ey + 8) + 2 * (size_t)Ex * Ey + (size_t)A * (Ex + Ey + Ez) + 4 * (size_t)A + NT / 32;
-  size_t bytes = n * esz;
-  bytes = (bytes + 15) & ~(size_t)15;
-  bytes += sizeof(int) * (size_t)((Ez + 1 + 3) & ~3) + sizeof(int4) * (size_t)A + sizeof(int) * (size_t)c->max_zlist;
+  const int pitch = (Ex + 9) & ~1;
+  size_t n = 2 * (size_t)pitch * (Ey + 8) + (size_t)A * max_tabw(c) + 2 * (size_t)Ex * Ey + (size_t)Ey * A +
+             (size_t)A + NT / 32;
+  size_t bytes = (n * esz + 15) & ~(size_t)15;
+  const size_t rle = esz == 8 ? 16 : 8;
+  bytes += sizeof(int4) * (size_t)A + rle * 2 * (size_t)Ey * A + sizeof(int) * 2 * (size_t)Ey +
+           sizeof(int) * (size_t)(Ez + 1) + sizeof(int) * (size_t)c->max_zlist;
   return bytes + 64;
 }
 
 size_t project_smem(dc_ctx *c, size_t esz) {
   const int Ex = c->max_E[0], Ey = c->max_E[1], Ez = c->max_E[2];
   const int A = c->max_atoms;
-  size_t n = 2 * (size_t)Ex * Ey + (size_t)A * (Ex + Ey + Ez) + (size_t)A;
+  size_t n = 2 * (size_t)Ex * Ey + (size_t)A * max_tabw(c) + (size_t)Ey * A;
   size_t bytes = ((n * esz) + 15) & ~(size_t)15;
-  bytes += sizeof(int) * (size_t)((Ez + 1 + 3) & ~3) + sizeof(int4) * (size_t)A + sizeof(int) * (size_t)c->max_zlist;
+  bytes += sizeof(int4) * (size_t)A + sizeof(int) * 2 * (size_t)Ey * A + sizeof(int) * 2 * (size_t)Ey +
+           sizeof(int) * (size_t)(Ez + 1) + sizeof(int) * (size_t)c->max_zlist;
   return bytes + 64;
 }
 
-template <typename T, int NT, int PPT>
+template <typename T, int NT, int PP>
 int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
   const size_t sm = hstep_smem(c, sizeof(T), NT);
   if (sm > 227 * 1024) {
     dc_set_error("hpsi: fragment tables exceed shared memory");
     return DC_ERR_ARG;
   }
-  DC_CUDA(cudaFuncSetAttribute(k_hstep<T, NT, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_hstep<T, NT, PPT><<<(unsigned)c->layout.nstates, NT, sm, s>>>(a);
+  DC_CUDA(dc_set_smem((const void *)k_hstep<T, NT, PP>, sm));
+  k_hstep<T, NT, PP><<<(unsigned)c->layout.nstates, NT, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
+}
+
+// Launch shapes of the stencil kernel: (threads per CTA, x-pairs per thread).
+constexpr int kShapes[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {512, 1}, {512, 2}, {512, 4}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <typename T>
+int run_shape(dc_ctx *c, int shape, HArgs<T> a, cudaStream_t s) {
+  switch (shape) {
+    case 0: return run_hstep<T, 128, 1>(c, a, s);
+    case 1: return run_hstep<T, 128, 2>(c, a, s);
+    case 2: return run_hstep<T, 256, 1>(c, a, s);
+    case 3: return run_hstep<T, 256, 2>(c, a, s);
+    case 4: return run_hstep<T, 512, 1>(c, a, s);
+    case 5: return run_hstep<T, 512, 2>(c, a, s);
+    default: return run_hstep<T, 512, 4>(c, a, s);
+  }
+}
+
+// A shape is valid when one CTA covers every x-pair of the largest plane, and useful when it does
+// not leave more than three quarters of its threads idle.
+bool shape_ok(const dc_ctx *c, int shape) {
+  const int pairs = ((c->max_E[0] + 1) / 2) * c->max_E[1];
+  const int cover = kShapes[shape][0] * kShapes[shape][1];
+  return cover >= pairs && (cover <= 4 * pairs || kShapes[shape][0] == 128);
+}
+
+int default_shape(const dc_ctx *c) {
+  for (int k : {0, 2, 3, 5, 6})
+    if (shape_ok(c, k)) return k;
+  return 6;
 }
 
 }  // namespace
@@ -386,11 +559,57 @@ int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T 
   if (Datom) a.Datom = Datom;
   a.occ = occ;
   a.dots = dots;
-  const int plane = c->max_E[0] * c->max_E[1];
-  if (plane <= 256) return run_hstep<T, 128, 2>(c, a, s);
-  if (plane <= 512) return run_hstep<T, 256, 2>(c, a, s);
-  if (plane <= 1024) return run_hstep<T, 512, 2>(c, a, s);
-  return run_hstep<T, 512, 8>(c, a, s);
+  int shape = c->hstep_shape[sizeof(T) == 8 ? 1 : 0];
+  if (shape < 0 || !shape_ok(c, shape)) shape = default_shape(c);
+  return run_shape<T>(c, shape, a, s);
+}
+
+// Time every useful launch shape on the context's fragments (H applied to `y`, written to `out`,
+// projections in `cbuf`), best of three repetitions each, and keep the fastest for this element type.
+template <typename T>
+int tune_hstep(dc_ctx *c, const T *y, T *out, T *cbuf, cudaStream_t s) {
+  HArgs<T> a = make_args<T>(c);
+  a.mode = HSTEP_HPSI;
+  a.yin = y;
+  a.yout = out;
+  a.cin = cbuf;
+  cudaEvent_t e0, e1;
+  DC_CUDA(cudaEventCreate(&e0));
+  DC_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_shape = default_shape(c);
+  int st = DC_OK;
+  for (int k = 0; k < kNumShapes && st == DC_OK; ++k) {
+    if (!shape_ok(c, k)) continue;
+    st = run_shape<T>(c, k, a, s);  // warm-up and attribute set
+    float tk = 1e30f;
+    for (int r = 0; r < 3 && st == DC_OK; ++r) {
+      cudaEventRecord(e0, s);
+      st = run_shape<T>(c, k, a, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = DC_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      tk = t < tk ? t : tk;
+    }
+    c->tune_ms[sizeof(T) == 8 ? 1 : 0][k] = tk;
+    if (st == DC_OK && tk < best) {
+      best = tk;
+      best_shape = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DC_OK) return st;
+  c->hstep_shape[sizeof(T) == 8 ? 1 : 0] = best_shape;
+  return DC_OK;
+}
+
+int hstep_shape_info(int shape, int *threads, int *pairs) {
+  if (shape < 0 || shape >= kNumShapes) return DC_ERR_ARG;
+  *threads = kShapes[shape][0];
+  *pairs = kShapes[shape][1];
+  return DC_OK;
 }
 
 template <typename T>
@@ -399,12 +618,14 @@ int launch_project(dc_ctx *c, const T *psi, T *cout, cudaStream_t s) {
   a.yin = psi;
   a.cout = cout;
   const size_t sm = project_smem(c, sizeof(T));
-  DC_CUDA(cudaFuncSetAttribute(k_project<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DC_CUDA(dc_set_smem((const void *)k_project<T, 256>, sm));
   k_project<T, 256><<<(unsigned)c->layout.nstates, 256, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
 
+template int tune_hstep<double>(dc_ctx *, const double *, double *, double *, cudaStream_t);
+template int tune_hstep<float>(dc_ctx *, const float *, float *, float *, cudaStream_t);
 template int launch_hstep<double>(dc_ctx *, int, int, const double *, const double *, double *, const double *,
                                   double *, const double *, const double *, double *, const double *, cudaStream_t);
 template int launch_hstep<float>(dc_ctx *, int, int, const float *, const float *, float *, const float *, float *,

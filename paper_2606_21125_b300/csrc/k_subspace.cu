@@ -457,7 +457,7 @@ int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s) {
 int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
   const int np = c->layout.max_norb + (c->layout.max_norb & 1);
   const size_t sm = 4 * (size_t)np * (np + 1) * sizeof(double);
-  DC_CUDA(cudaFuncSetAttribute(k_subspace, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DC_CUDA(dc_set_smem((const void *)k_subspace, sm));
   k_subspace<<<c->nfrag, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, c->d_eps,
                                        c->d_C64, precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags);
   DC_CUDA(cudaGetLastError());
@@ -467,7 +467,7 @@ int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
 template <typename T>
 int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s) {
   const size_t sm = ((size_t)DC_MAX_NORB * RPAD + (size_t)DC_MAX_NORB * DC_MAX_NORB) * sizeof(T);
-  DC_CUDA(cudaFuncSetAttribute(k_rotate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  DC_CUDA(dc_set_smem((const void *)k_rotate<T>, sm));
   const T *C = nullptr;
   if (sizeof(T) == 8) C = reinterpret_cast<const T *>(c->d_C64);
   else C = reinterpret_cast<const T *>(c->d_C32);

@@ -229,6 +229,7 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
         S.hi[d] = hi;
         for (int j = 0; j < D.E[d]; ++j) tab.push_back(fx[d].val[j]);
       }
+      for (int p = D.E[0] + D.E[1] + D.E[2]; p < tab_width(D); ++p) tab.push_back(0.0);
       slots.push_back(S);
       c->h_atoms.push_back(a);
       zsup.push_back(fx[2].sup);
@@ -254,7 +255,7 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
     pt_off += P;
     st_off += D.norb;
     at_off += A;
-    tab_off += (long long)A * (D.E[0] + D.E[1] + D.E[2]);
+    tab_off += (long long)A * tab_width(D);
     c_off += (long long)A * D.norb;
     sub_off += (long long)D.norb * D.norb;
   }

@@ -27,6 +27,17 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
+def _synthetic_potential(grid, seed):
+    """Seeded smooth periodic potential (a few random Fourier modes, Ha) used as an H-apply input."""
+    r = np.random.default_rng(seed)
+    z, y, x = np.meshgrid(*[np.arange(grid.n[d]) / grid.n[d] for d in (2, 1, 0)], indexing="ij")
+    V = -0.5 + np.zeros(grid.shape())
+    for _ in range(6):
+        m = r.integers(-3, 4, size=3)
+        V += 0.3 * r.standard_normal() * np.cos(2 * np.pi * (m[0] * x + m[1] * y + m[2] * z) + r.uniform(0, 6.3))
+    return V
+
+
 CASES = {
     "si8": lambda **kw: workloads.make_config("si8", **kw),
     "periodic": lambda **kw: workloads.small_config(n=(12, 12, 12), L=(7.2, 7.2, 7.2), bc="periodic", natom=4,
@@ -75,9 +86,14 @@ def test_ionic_potential_and_starting_density(case):
     ref_r = st.rho_in.reshape(-1)
     assert np.max(np.abs(_np(rho0) - ref_r)) <= 1e-12 * np.max(np.abs(ref_r))
     ref_e = st.veff(st.rho_in).reshape(-1)
-    # V_loc and V_H nearly cancel: the FFT rounding scales with the uncancelled terms
+    # V_loc and V_H nearly cancel: the FFT rounding scales with the uncancelled terms.  Where the
+    # starting density is FFT noise around zero, v_x = -(3 rho/pi)^(1/3) turns that noise into
+    # cbrt-sized differences; those points are compared against that bound instead.
     scale = np.max(np.abs(ref_v)) + np.max(np.abs(model.hartree(st.grid, st.rho_in)))
-    assert np.max(np.abs(_np(veff) - ref_e)) <= 1e-12 * scale
+    dense = ref_r > 1e-9 * np.max(ref_r)
+    diff = np.abs(_np(veff) - ref_e)
+    assert np.max(diff[dense]) <= 1e-12 * scale
+    assert np.max(diff, initial=0.0) <= 1e-12 * scale + 2.0 * np.cbrt(3.0 * 1e-9 * np.max(ref_r) / np.pi)
 
 
 def test_starting_orbitals_bit_exact():
@@ -94,11 +110,10 @@ def test_starting_orbitals_bit_exact():
 def test_hpsi(case, dtype):
     cfg = CASES[case](precision=dtype)
     st = oracle_state(cfg)
-    V = st.veff(st.rho_in)
+    V = _synthetic_potential(st.grid, seed=17)
     r = np.random.default_rng(11)
     with _solver(cfg) as s:
-        _, rho0 = s.initial()
-        s.potential(rho0)
+        s.set_potential(torch.tensor(V.reshape(-1), dtype=torch.float64, device="cuda"))
         x = r.standard_normal(s.layout.psi_elems)
         tdt = torch.float64 if dtype == "fp64" else torch.float32
         psi = torch.tensor(x, dtype=tdt, device="cuda")
@@ -182,6 +197,20 @@ def test_scf_steps_si8(si8_oracle_run, precision, tol_e, tol_eps, tol_rho):
     assert np.max(np.abs(_np(eps) - ref_eps)) < tol_eps
     ref_rho = steps[-1]["rho_out"].reshape(-1)
     assert np.sum(np.abs(rho_out - ref_rho)) / np.sum(np.abs(ref_rho)) < tol_rho
+
+
+def test_mixed_gram_matches_fp32_gram():
+    """From the same warmed-up state, one CheFSI pass with the tensor-core split-BF16 Gram gives the Ritz
+    values of the FP32 SIMT Gram within the eigenvalue budget; the filter is identical in both, so the
+    difference isolates the tensor-core contraction."""
+    res = []
+    for prec in ("fp32", "mixed"):
+        with _solver(CASES["si8"](precision=prec)) as s:
+            s.warmup()
+            s.chefsi(1)
+            res.append(_np(s.get_state()[1]))
+    d = float(np.max(np.abs(res[0] - res[1])))
+    assert d < 1e-5, f"max |eps_mixed - eps_fp32| = {d:.3e} Ha"
 
 
 def test_scf_step_host_buffers_match_device_buffers():
@@ -286,11 +315,10 @@ def test_full_size_hpsi_sampled_si512():
     cfg = workloads.make_config("si512", precision="fp32")
     sample = [0, 137, 511]
     st = oracle_state(cfg, subset=sample)
-    V = st.veff(st.rho_in)
+    V = _synthetic_potential(st.grid, seed=23)
     r = np.random.default_rng(2)
     with _solver(cfg) as s:
-        _, rho0 = s.initial()
-        s.potential(rho0)
+        s.set_potential(torch.tensor(V.reshape(-1), dtype=torch.float64, device="cuda"))
         psi = torch.tensor(r.standard_normal(s.layout.psi_elems), dtype=torch.float32, device="cuda")
         out = s.hpsi(psi)
         offs = {}
