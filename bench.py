@@ -31,6 +31,10 @@ WORKLOAD_TEXT = {
              "8^3 fragments of 10^3 core + 6-point buffer (22^3), 48 orbitals each",
     "si64": "Si64 (2^3 supercell), 40^3 grid, 4^3 fragments of 10^3 core + 5 (20^3), 32 orbitals",
     "si8": "Si8 diamond cell, 20^3 grid, 2^3 fragments of 10^3 core + 4 (18^3), 24 orbitals",
+    "si_weak64": "Si64 weak-scaling cell (2^3 supercell, N(0,0.3)), 40^3 grid, 4^3 fragments of 10^3 core + 6 "
+                 "(22^3), 48 orbitals",
+    "si_weak4096": "Si4096 weak-scaling cell (8^3 supercell, N(0,0.3)), 160^3 grid, 16^3 fragments of 10^3 core + 6 "
+                   "(22^3), 48 orbitals",
 }
 
 

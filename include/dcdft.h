@@ -102,7 +102,9 @@ typedef struct {
  * m (>= 1).  n_pass: CheFSI passes per SCF step.  n_warmup: passes in the starting potential before
  * the first step (run in FP64 for every precision).  hxc: DC_HXC_*.  kT: electronic temperature
  * (Ha, > 0).  mix_alpha: linear mixing weight in [0, 1]; 0 keeps rho_in fixed (the paper's fixed-density
- * DC, Sec. 2.5 use case 3).  seed: initial-orbital seed. */
+ * DC, Sec. 2.5 use case 3).  seed: initial-orbital seed.  kerker_q0 (bohr^-1, >= 0): 0 gives plain
+ * linear mixing; > 0 weights every Fourier component of the density residual by
+ * mix_alpha G^2/(G^2 + q0^2) (Kerker preconditioning against long-wavelength charge sloshing). */
 typedef struct {
   int precision;
   int cheb_degree;
@@ -112,6 +114,7 @@ typedef struct {
   double kT;
   double mix_alpha;
   uint64_t seed;
+  double kerker_q0;
 } dc_params_t;
 
 /* Sizes of everything a caller allocates for the calls below. */

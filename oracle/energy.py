@@ -36,5 +36,12 @@ def residual(grid, rho_out, rho_in, ne):
     return grid.dV * float(np.sum(np.abs(rho_out - rho_in))) / ne
 
 
-def mix(rho_in, rho_out, alpha):
-    return rho_in + alpha * (rho_out - rho_in)
+def mix(rho_in, rho_out, alpha, grid=None, q0=0.0):
+    """Next input density.  q0 = 0: plain linear mixing rho_in + alpha (rho_out - rho_in).  q0 > 0:
+    Kerker-preconditioned linear mixing, each Fourier component of the residual weighted by
+    alpha G^2/(G^2 + q0^2) (long wavelengths damped; G = 0 carries no charge change)."""
+    if q0 <= 0.0:
+        return rho_in + alpha * (rho_out - rho_in)
+    g2 = grid.g2()
+    w = alpha * g2 / (g2 + q0 * q0)
+    return rho_in + np.real(np.fft.ifftn(w * np.fft.fftn(rho_out - rho_in)))

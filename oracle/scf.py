@@ -105,7 +105,7 @@ class DCState:
         stats = dict(E=E, F=E - self.kT * S, eband=eband, mu=mu, drho=drho, natom=len(self.pos),
                      rho_out=rho_out, rho_in=self.rho_in.copy(), q=q, occ=occ,
                      eps={f: self.eps[f].copy() for f in self.active})
-        self.rho_in = energy.mix(self.rho_in, rho_out, self.alpha)
+        self.rho_in = energy.mix(self.rho_in, rho_out, self.alpha, self.grid, float(self.cfg.get("kerker_q0", 0.0)))
         self.step_index += 1
         return stats
 

@@ -417,7 +417,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   c->params = *params;
   const dc_params_t &P = c->params;
   if (P.precision < DC_FP64 || P.precision > DC_MIXED || P.cheb_degree < 1 || P.cheb_degree > 64 || P.n_pass < 1 ||
-      P.n_warmup < 0 || !(P.kT > 0.0) || !(P.mix_alpha >= 0.0) || P.mix_alpha > 1.0 ||
+      P.n_warmup < 0 || !(P.kT > 0.0) || !(P.mix_alpha >= 0.0) || P.mix_alpha > 1.0 || !(P.kerker_q0 >= 0.0) ||
       (P.hxc != DC_HXC_NONE && P.hxc != DC_HXC_HARTREE_X)) {
     dc_set_error("dc_init: invalid parameters");
     return DC_ERR_ARG;
@@ -483,8 +483,10 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   // work lists for the Gram and rotation kernels
   {
     // points per Gram partial: each chunk's sums are FP32 (tensor memory or SIMT pairs) and the
-    // chunks are added in FP64; DC_GRAM_CHUNK overrides (multiple of 64, 64..65536)
-    c->gram_chunk = 2048;
+    // chunks are added in FP64; DC_GRAM_CHUNK overrides (multiple of 64, 64..65536).  Tensor-memory
+    // FP32 accumulation carries an error that grows linearly with the chunk length (measured on
+    // B300), so the mixed path uses short chunks.
+    c->gram_chunk = c->params.precision == DC_MIXED ? 256 : 2048;
     if (const char *gc = getenv("DC_GRAM_CHUNK")) {
       const int v = atoi(gc);
       if (v >= 64 && v <= 65536 && v % 64 == 0) c->gram_chunk = v;

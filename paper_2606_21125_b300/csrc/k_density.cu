@@ -114,29 +114,58 @@ __global__ void __launch_bounds__(QNT) k_fermi(const double *eps, const double *
   }
   lo -= 40.0 * kT;
   hi += 40.0 * kT;
-  double *pacc = partials + 2 * nb;  // [2][nb]
+  // Safeguarded Newton: every iteration evaluates N(mu) and dN/dmu in one pass, shrinks the bracket
+  // by the sign of N - N_e, and takes the Newton step when it stays inside the bracket (bisection
+  // otherwise).  Starts from the previous mu when that lies in the bracket.  Converged when the
+  // Newton correction is below 1e-14 Ha or the bracket below 1e-13 Ha.
+  double *pacc = partials + 2 * nb;  // [2][2 nb]
+  const double guess = __ldcg(mu_out);
+  double mu = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
   for (int itn = 0; itn < 200; ++itn) {
-    if (hi - lo < 1e-13) break;
-    const double mid = 0.5 * (lo + hi);
-    double s = 0.0;
-    for (int p = base; p < nst; p += stride) s += 2.0 * fermi_occ(eps[p], mid, kT) * q[p];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    double s = 0.0, ds = 0.0;
+    for (int p = base; p < nst; p += stride) {
+      const double fo = fermi_occ(eps[p], mu, kT);
+      s += 2.0 * fo * q[p];
+      ds += 2.0 * q[p] * fo * (1.0 - fo) / kT;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      ds += __shfl_xor_sync(0xffffffffu, ds, o);
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    if ((threadIdx.x & 31) == 0) {
+      red[threadIdx.x >> 5] = s;
+      red2[threadIdx.x >> 5] = ds;
+    }
     __syncthreads();
-    double *pa = pacc + (itn & 1) * nb;
+    double *pa = pacc + (itn & 1) * 2 * nb;
     if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < QNT / 32; ++w) t += red[w];
-      pa[blockIdx.x] = t;
+      double t = 0.0, dt = 0.0;
+      for (int w = 0; w < QNT / 32; ++w) {
+        t += red[w];
+        dt += red2[w];
+      }
+      pa[2 * blockIdx.x] = t;
+      pa[2 * blockIdx.x + 1] = dt;
     }
     if (!grid_sync(bar, bar + 1, nb, flags)) return;
-    double tot = 0.0;
-    for (int b = 0; b < nb; ++b) tot += __ldcg(&pa[b]);
-    if (tot < ne) lo = mid;
-    else hi = mid;
+    double tot = 0.0, dtot = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      tot += __ldcg(&pa[2 * b]);
+      dtot += __ldcg(&pa[2 * b + 1]);
+    }
+    const double r = tot - ne;
+    if (r < 0.0) lo = mu;
+    else hi = mu;
+    const double step = dtot > 0.0 ? r / dtot : 0.0;
+    double nm = mu - step;
+    const bool newton_ok = dtot > 0.0 && nm > lo && nm < hi;
+    if (r == 0.0 || (newton_ok && fabs(step) < 1e-14) || hi - lo < 1e-13) {
+      if (newton_ok) mu = nm;
+      break;
+    }
+    mu = newton_ok ? nm : 0.5 * (lo + hi);
   }
-  const double mu = 0.5 * (lo + hi);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     mu_out[0] = mu;
     if (!isfinite(mu)) atomicOr(flags, DC_FLAG_NONFINITE);

@@ -258,6 +258,28 @@ __global__ void k_mix(long long n, double *rho_in, const double *rho_out, double
   if (i < n) rho_in[i] = rho_in[i] + alpha * (rho_out[i] - rho_in[i]);
 }
 
+__global__ void k_residual_cplx(long long n, const double *rho_out, const double *rho_in, double2 *out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(rho_out[i] - rho_in[i], 0.0);
+}
+
+// Kerker weight alpha G^2/(G^2+q0^2), divided by N for the unnormalised inverse transform
+__global__ void k_kerker(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
+                         double q0sq, double2 *c) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npts) return;
+  double gx, gy, gz;
+  const double g2 = gsq(idx, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
+  const double w = alpha * g2 / (g2 + q0sq) / (double)npts;
+  const double2 v = c[idx];
+  c[idx] = make_double2(w * v.x, w * v.y);
+}
+
+__global__ void k_add_real(long long n, double *rho_in, const double2 *d) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) rho_in[i] += d[i].x;
+}
+
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 int fft(dc_ctx *c, double2 *data, int dir) {
@@ -356,7 +378,21 @@ int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s) {
 }
 
 int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s) {
-  k_mix<<<nblk(c->npts), 256, 0, s>>>(c->npts, rho_in, c->d_rho_out, c->params.mix_alpha);
+  const long long N = c->npts;
+  const double q0 = c->params.kerker_q0;
+  if (!(q0 > 0.0)) {
+    k_mix<<<nblk(N), 256, 0, s>>>(N, rho_in, c->d_rho_out, c->params.mix_alpha);
+    DC_CUDA(cudaGetLastError());
+    return DC_OK;
+  }
+  const int *n = c->grid.n;
+  const double *L = c->grid.L;
+  DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
+  k_residual_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, rho_in, c->d_cplx);
+  DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
+  k_kerker<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->params.mix_alpha, q0 * q0, c->d_cplx);
+  DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
+  k_add_real<<<nblk(N), 256, 0, s>>>(N, rho_in, c->d_cplx);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

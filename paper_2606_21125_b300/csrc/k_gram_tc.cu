@@ -252,8 +252,7 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     return DC_ERR_ARG;
   }
   const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
-  // 64 KB of slack past the two stages keeps every descriptor reading inside the allocation
-  const size_t sm = 2 * stage + 65536;
+  const size_t sm = 2 * stage;
   DC_CUDA(dc_set_smem((const void *)k_gram_tc, sm));
   k_gram_tc<<<c->n_gram_items, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->d_gram_off, c->gram_chunk, Y, HY,
                                             c->d_gram, c->d_flags);

@@ -213,6 +213,24 @@ def test_mixed_gram_matches_fp32_gram():
     assert d < 1e-5, f"max |eps_mixed - eps_fp32| = {d:.3e} Ha"
 
 
+def test_scf_kerker_mixing_fp64():
+    """SCF steps with Kerker-preconditioned mixing (FFT-weighted residual) against the oracle."""
+    cfg = CASES["uneven"](precision="fp64", n_warmup=3, kerker_q0=0.8)
+    st = oracle_state(cfg)
+    st.warmup()
+    refs = [st.scf_step() for _ in range(3)]
+    natom = len(cfg["pos"])
+    with _solver(cfg) as s:
+        s.warmup()
+        _, rho = s.initial()
+        rho = rho.clone()
+        for ref in refs:
+            got = s.scf_step(rho)
+            assert abs(got["E"] - ref["E"]) / natom < 1e-9
+        rin = _np(rho)
+    assert np.max(np.abs(rin - st.rho_in.reshape(-1))) < 1e-9 * np.max(np.abs(st.rho_in))
+
+
 def test_scf_step_host_buffers_match_device_buffers():
     cfg = CASES["uneven"](precision="fp32", n_warmup=3)
     res = []

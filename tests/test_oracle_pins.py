@@ -16,7 +16,7 @@ from scipy.optimize import brentq
 from scipy.special import erf
 
 import workloads
-from oracle import adjoint, chefsi, density, fermi, maps, model, rng, scf
+from oracle import adjoint, chefsi, density, energy, fermi, maps, model, rng, scf
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -321,6 +321,22 @@ def test_initial_density_is_band_limited_ion_charge():
     assert abs(grid.dV * rho.sum() - 4.0) < 1e-12
     ref = _sampled_gaussian(grid, R[0], sig, 4.0)
     assert np.max(np.abs(rho - ref)) < 1e-6 * np.max(ref)
+
+
+def test_kerker_mixing_plane_wave_and_charge():
+    """Kerker mixing scales a plane-wave residual by alpha G^2/(G^2+q0^2) and keeps the charge; q0=0 is linear."""
+    grid = model.Grid((12, 10, 8), (6.0, 5.0, 4.0))
+    z, y, x = np.meshgrid(*[np.arange(grid.n[d]) * grid.h[d] for d in (2, 1, 0)], indexing="ij")
+    G = np.array([2 * np.pi * 2 / 6.0, 2 * np.pi * 1 / 5.0, 0.0])
+    res = 0.05 * np.cos(G[0] * x + G[1] * y)
+    rho_in = np.full(grid.shape(), 0.1)
+    alpha, q0 = 0.3, 0.8
+    out = energy.mix(rho_in, rho_in + res, alpha, grid, q0)
+    g2 = float(G @ G)
+    np.testing.assert_allclose(out - rho_in, alpha * g2 / (g2 + q0 * q0) * res, atol=1e-14)
+    r = np.random.default_rng(3).uniform(0.0, 0.2, grid.shape())
+    assert abs(energy.mix(rho_in, r, alpha, grid, q0).sum() - rho_in.sum()) < 1e-12
+    np.testing.assert_allclose(energy.mix(rho_in, r, alpha, grid, 0.0), rho_in + alpha * (r - rho_in))
 
 
 def test_exchange_uniform_gas():

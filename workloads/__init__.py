@@ -133,6 +133,7 @@ DEFAULT_PARAMS = dict(
     hxc="hartree_x",  # hartree_x | none
     kT=0.01,
     mix_alpha=0.3,
+    kerker_q0=0.0,  # 0: plain linear mixing; > 0: Kerker-preconditioned (bohr^-1)
     seed=20260603,
     bc="zero",  # zero | periodic
 )
@@ -168,6 +169,9 @@ def make_config(name: str, **overrides):
         cfg["L"] = (a, a, a)
     cfg.pop("cells", None)
     cfg.update(copy.deepcopy(DEFAULT_PARAMS))
+    # Si8 is specified with plain linear mixing; the larger cells slosh charge under it (the oracle
+    # diverges on Si64 after three steps), so they use Kerker-preconditioned linear mixing.
+    cfg["kerker_q0"] = 0.0 if name == "si8" else 1.0
     cfg.update(pos=pos, species=spc, spec=sp, name=name)
     cfg.update(overrides)
     return cfg
