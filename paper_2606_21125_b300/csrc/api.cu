@@ -75,6 +75,7 @@ void free_ctx(dc_ctx *c) {
                   c->blk64[1], c->blk64[2], c->d_hy64, c->d_c64[0], c->d_c64[1], c->d_c32[0], c->d_c32[1],
                   c->d_eps, c->d_q, c->d_occ, c->d_bounds, c->d_gram, c->d_gram_off, c->d_gram_nchunk, c->d_C64,
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
+                  c->d_items2,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
                   c->d_dots};
   for (void *p : ptrs)
@@ -440,6 +441,13 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   // maps and tables
   DC_TRY(upload(&c->d_desc, c->h_desc));
   DC_TRY(upload(&c->d_items, c->h_items));
+  {
+    std::vector<int2> it2;
+    for (int f = 0; f < c->nfrag; ++f)
+      for (int i = 0; i < c->h_desc[f].norb; i += 2) it2.push_back(make_int2(f, i));
+    c->n_items2 = (int)it2.size();
+    DC_TRY(upload(&c->d_items2, it2));
+  }
   DC_TRY(upload(&c->d_idx_map, c->h_idx_map));
   DC_TRY(upload(&c->d_owner, c->h_owner));
   DC_TRY(upload(&c->d_core_local, c->h_core_local));

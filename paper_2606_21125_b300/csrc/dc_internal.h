@@ -149,6 +149,8 @@ struct dc_ctx {
   double *h_scalar_pinned = nullptr;
 
   // work lists
+  int2 *d_items2 = nullptr;      // (fragment, first orbital) of orbital pairs (two-orbital stencil)
+  int n_items2 = 0;
   int2 *d_gram_items = nullptr;  // (fragment, chunk) of the Gram kernel
   int n_gram_items = 0;
   int2 *d_rot_items = nullptr;   // (fragment, 128-point chunk) of the rotation kernel

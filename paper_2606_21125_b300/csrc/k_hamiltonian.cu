@@ -4,11 +4,13 @@
 // 25-point Laplacian and ghost points that are zero (buffer edge) or wrap within the fragment.
 // The projectors are separable, p_a(j) = C_a gx_a[jx] gy_a[jy] gz_a[jz].
 //
-// One CTA handles one (fragment, orbital) item and streams the fragment along z.  Each thread owns
-// pairs of x-adjacent points of the xy-plane and keeps their 9-deep z columns in registers; the
-// current plane sits in shared memory with a 4-point halo (zeros, or wrapped values for the
-// periodic boundary), so the x and y taps are unconditional vector loads shared by the pair, and
-// the pair is updated with paired FP32 instructions (FFMA2/FADD2).
+// One CTA handles NO orbitals of one fragment (NO = 2 in FP32) and streams the fragment along z.
+// Each thread owns pairs of x-adjacent points of the xy-plane, for every one of the CTA's
+// orbitals, and keeps their 9-deep z columns in registers; the current planes sit in shared memory
+// with a 4-point halo (zeros, or wrapped values for the periodic boundary), so the x and y taps
+// are unconditional vector loads, and each pair is updated with paired FP32 instructions
+// (FFMA2/FADD2).  Addressing, the per-plane atom lists and all loop control are shared by the
+// orbitals of a thread, which is where most of the instructions of this kernel go.
 //
 // The Laplacian is evaluated in difference form, sum_n k_n [(y_{+n} - y) + (y_{-n} - y)], which
 // equals the textbook form because c_0 = -2 sum_n c_n; the differences of neighbouring values are
@@ -16,11 +18,11 @@
 // in rounded arithmetic (100x smaller FP32 error at the same data movement).
 //
 // Nonlocal term: for each plane, warps compact, per row y, the atoms whose projector touches (y, z)
-// into (slot, D_a C_a <p_a|y> gz_a[z] gy_a[y]) records; a point adds u * gx_a[x] over its row's
-// records only.  The projections of the output, which the next Chebyshev step needs, are
-// accumulated one plane behind: one task per (row, atom of that row) forms sum_x gx_a[x] out(x, y)
-// and adds it into a dense [row][atom] array (each slot has one writer per plane, so the order is
-// fixed and the result deterministic); the rows are summed at the end.
+// into records (slot, D_a C_a <p_a|psi_o> gz_a[z] gy_a[y] for each orbital o); a point adds
+// u_o * gx_a[x] over its row's records only.  The projections of the output, which the next
+// Chebyshev step needs, are accumulated one plane behind: one task per (row, atom of that row)
+// forms sum_x gx_a[x] out_o(x, y) and adds it into a dense [orbital][row][atom] array (each slot has
+// one writer per plane, so the order is fixed and the result deterministic); rows are summed last.
 #include "dc_internal.h"
 
 namespace {
@@ -75,34 +77,15 @@ struct P2<double> {
   static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
 };
 
-// Row-list record: atom slot and its coefficient for the row and plane.
-template <typename T>
-struct RLE;
-template <>
-struct __align__(8) RLE<float> {
-  int k;
-  float u;
-};
-template <>
-struct __align__(16) RLE<double> {
-  int k;
-  int pad;
-  double u;
+// Per-row record coefficients of the NO orbitals, each splatted over the two points of a pair.
+template <typename T, int NO>
+struct RU {
+  typename P2<T>::V u[NO];
 };
 
 template <typename T>
 __device__ __forceinline__ typename P2<T>::V ld2(const T *p) {
   return *reinterpret_cast<const typename P2<T>::V *>(p);
-}
-
-template <typename T>
-__device__ __forceinline__ T ldz(const T *base, int zz, int Ez, int plane, int t, bool valid, int periodic) {
-  if (!valid) return T(0);
-  if (zz < 0 || zz >= Ez) {
-    if (!periodic) return T(0);
-    zz = zz < 0 ? zz + Ez : zz - Ez;
-  }
-  return base[(long long)zz * plane + t];
 }
 
 template <typename T, int NT>
@@ -119,12 +102,13 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
   return s;  // valid in thread 0
 }
 
-// Build the per-row atom lists of plane z: for every row y, the slots k of the plane's z-list whose
-// y factor is non-zero there, with u = sk[k] gz_k[z] gy_k[y] (sk may be null: u = 0).  One warp
-// per row, compaction by ballot; kl (slots only) or rl (slot and u) receives the records.
-template <typename T, int NT>
+// Per-row atom lists of plane z: for every row y, the slots k of the plane's z-list whose y factor
+// is non-zero there.  One warp per row, compaction by ballot.  With ru != nullptr the records also
+// get u_o = sk[o][k] gz_k[z] gy_k[y] for the NO orbitals.
+template <typename T, int NT, int NO>
 __device__ __forceinline__ void build_rows(int z, int Ex, int Ey, int A, const T *stab, int tabw, const int *zl_b,
-                                           const int *zl_i, const T *sk, RLE<T> *rl, int *kl, int *rn) {
+                                           const int *zl_i, const T *sk, RU<T, NO> *ru, int *rk, int *rn) {
+  using Op = P2<T>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int zbeg = zl_b[z], zend = zl_b[z + 1];
   for (int y = warp; y < Ey; y += NT / 32) {
@@ -142,13 +126,12 @@ __device__ __forceinline__ void build_rows(int z, int Ex, int Ey, int A, const T
       const unsigned m = __ballot_sync(0xffffffffu, in);
       if (in) {
         const int pos = cnt + __popc(m & ((1u << lane) - 1u));
-        if (rl) {
-          RLE<T> r;
-          r.k = k;
-          r.u = sk ? sk[k] * gzy : T(0);
-          rl[y * A + pos] = r;
-        } else {
-          kl[y * A + pos] = k;
+        rk[y * A + pos] = k;
+        if (ru) {
+          RU<T, NO> r;
+#pragma unroll
+          for (int o = 0; o < NO; ++o) r.u[o] = Op::splat(sk[o * A + k] * gzy);
+          ru[y * A + pos] = r;
         }
       }
       cnt += __popc(m);
@@ -157,35 +140,45 @@ __device__ __forceinline__ void build_rows(int z, int Ex, int Ey, int A, const T
   }
 }
 
-// Projection tasks of one plane (values pl[y][x], row pitch Ex): for each row y and each listed
-// slot k, pacc[y][k] += gz_k[z] gy_k[y] sum_x gx_k[x] pl[y][x].  Slot (y, k) has one writer.
-template <typename T, int NT>
-__device__ __forceinline__ void project_rows(const T *pl, int z, int Ex, int Ey, int A, const T *stab, int tabw,
-                                             const int4 *box, const RLE<T> *rl, const int *kl, const int *rn,
-                                             T *pacc) {
+// Projection tasks of one plane (values pl[o][y][x], plane stride `ps`, row pitch Ex): for each
+// row y and listed slot k, pacc[o][y][k] += gz_k[z] gy_k[y] sum_x gx_k[x] pl[o][y][x].  Slot (o, y, k)
+// has one writer per plane.
+template <typename T, int NT, int NO>
+__device__ __forceinline__ void project_rows(const T *pl, int ps, int z, int Ex, int Ey, int A, const T *stab,
+                                             int tabw, const int4 *box, const int *rk, const int *rn, T *pacc,
+                                             int nvalid) {
   const int nslot = Ey * A;
   for (int s = threadIdx.x; s < nslot; s += NT) {
     const int y = s % Ey, e = s / Ey;
     if (e >= rn[y]) continue;
-    const int k = rl ? rl[y * A + e].k : kl[y * A + e];
+    const int k = rk[y * A + e];
     const T *g = stab + k * tabw;
     const int4 bx = box[k];
-    const T *row = pl + y * Ex;
-    T w = T(0);
-    for (int x = bx.x; x < bx.y; ++x) w += g[x] * row[x];
-    pacc[y * A + k] += g[Ex + Ey + z] * g[Ex + y] * w;
+    const T gzy = g[Ex + Ey + z] * g[Ex + y];
+    T w[NO];
+#pragma unroll
+    for (int o = 0; o < NO; ++o) w[o] = T(0);
+    for (int x = bx.x; x < bx.y; ++x) {
+      const T gv = g[x];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) w[o] += gv * pl[o * ps + y * Ex + x];
+    }
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      if (o < nvalid) pacc[(o * Ey + y) * A + k] += gzy * w[o];
   }
 }
 
-template <typename T, int NT, int PP>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
+template <typename T, int NT, int PP, int NO>
+__global__ void __launch_bounds__(NT, NT <= 256 ? (NO == 2 ? 2 : 3) : 1) k_hstep(HArgs<T> a) {
   using Op = P2<T>;
   using V = typename Op::V;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int item = blockIdx.x;
   const int2 fi = a.items[item];
-  const int f = fi.x, i = fi.y;
+  const int f = fi.x, i0 = fi.y;
   const FragDesc D = a.desc[f];
+  const int nvalid = min(NO, D.norb - i0);  // orbitals i0 .. i0+nvalid-1 of fragment f
   const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2];
   const int plane = Ex * Ey;
   const int nxp = (Ex + 1) >> 1;
@@ -199,17 +192,18 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
 
   // shared memory: element arrays (vector-read ones first, at even offsets), then 16-byte aligned
   // records and integers
-  T *pin = reinterpret_cast<T *>(smem_raw);  // [2][pplane]
-  T *stab = pin + 2 * pplane;                // [A][tabw]
-  T *pout = stab + A * tabw;                 // [2][plane]
-  T *pacc = pout + 2 * plane;                // [Ey][A]
-  T *sk = pacc + Ey * A;                     // [A]
-  T *red = sk + A;                           // [NT/32]
-  size_t off = (size_t)(2 * pplane + A * tabw + 2 * plane + Ey * A + A + NT / 32) * sizeof(T);
+  T *pin = reinterpret_cast<T *>(smem_raw);  // [2 buf][NO][pplane]
+  T *stab = pin + 2 * NO * pplane;           // [A][tabw]
+  T *pout = stab + A * tabw;                 // [2 buf][NO][plane]
+  T *pacc = pout + 2 * NO * plane;           // [NO][Ey][A]
+  T *sk = pacc + NO * Ey * A;                // [NO][A]
+  T *red = sk + NO * A;                      // [NT/32]
+  size_t off = (size_t)(2 * NO * pplane + A * tabw + 2 * NO * plane + NO * Ey * A + NO * A + NT / 32) * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   int4 *box = reinterpret_cast<int4 *>(smem_raw + off);         // [A]
-  RLE<T> *rl = reinterpret_cast<RLE<T> *>(box + A);             // [2][Ey][A]
-  int *rn = reinterpret_cast<int *>(rl + 2 * Ey * A);           // [2][Ey]
+  RU<T, NO> *ru = reinterpret_cast<RU<T, NO> *>(box + A);       // [2 buf][Ey][A]
+  int *rk = reinterpret_cast<int *>(ru + 2 * Ey * A);           // [2 buf][Ey][A]
+  int *rn = rk + 2 * Ey * A;                                    // [2 buf][Ey]
   int *zl_b = rn + 2 * Ey;                                      // [Ez+1]
   int *zl_i = zl_b + Ez + 1;                                    // [list]
 
@@ -221,10 +215,13 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
   for (int k = threadIdx.x; k < A; k += NT) {
     const ProjSlot S = a.slots[D.at_off + k];
     box[k] = make_int4(S.lo[0], S.hi[0], S.lo[1], S.hi[1]);
-    sk[k] = a.cin ? T(a.Datom[S.atom] * S.coef) * a.cin[D.c_off + (long long)i * A + k] : T(0);
+    const T ds = T(a.Datom[S.atom] * S.coef);
+#pragma unroll
+    for (int o = 0; o < NO; ++o)
+      sk[o * A + k] = (a.cin && o < nvalid) ? ds * a.cin[D.c_off + (long long)(i0 + o) * A + k] : T(0);
   }
-  for (int t = threadIdx.x; t < Ey * A; t += NT) pacc[t] = T(0);
-  for (int t = threadIdx.x; t < 2 * pplane; t += NT) pin[t] = T(0);
+  for (int t = threadIdx.x; t < NO * Ey * A; t += NT) pacc[t] = T(0);
+  for (int t = threadIdx.x; t < 2 * NO * pplane; t += NT) pin[t] = T(0);
 
   T alpha = T(1), beta = T(0), shift = T(0);
   if (a.mode == HSTEP_CHEB) {
@@ -234,15 +231,18 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
     beta = T(bd[5 + 2 * a.step]);
   }
   const bool use_prev = (a.mode == HSTEP_CHEB) && a.yprev != nullptr && a.step > 0;
-  const T *yin = a.yin + D.psi_off + (long long)i * P;
-  const T *ypv = use_prev ? a.yprev + D.psi_off + (long long)i * P : nullptr;
-  T *yout = a.yout ? a.yout + D.psi_off + (long long)i * P : nullptr;
+  // orbital o of the item lives at element offset base + o * P (invalid orbitals read orbital 0)
+  const long long base = D.psi_off + (long long)i0 * P;
+  const long long ostride = P;
   const T *vf = a.vf + D.pt_off;
-  const T occ2 = a.mode == HSTEP_ADJ ? T(2.0 * a.occ[D.st_off + i] * a.dV) : T(0);
+  T occ2[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o)
+    occ2[o] = (a.mode == HSTEP_ADJ && o < nvalid) ? T(2.0 * a.occ[D.st_off + i0 + o] * a.dV) : T(0);
 
   int px[PP], py[PP];
   bool valid[PP], v1[PP];
-  V q[PP][9];
+  V q[PP][NO][9];
 #pragma unroll
   for (int r = 0; r < PP; ++r) {
     const int p = threadIdx.x + r * NT;
@@ -252,55 +252,97 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
     v1[r] = valid[r] && (px[r] + 1 < Ex);
     const int t0 = px[r] + py[r] * Ex;
 #pragma unroll
-    for (int k = 0; k < 9; ++k)
-      q[r][k] = Op::mk(ldz(yin, k - 4, Ez, plane, t0, valid[r], a.periodic),
-                       ldz(yin, k - 4, Ez, plane, t0 + 1, v1[r], a.periodic));
+    for (int o = 0; o < NO; ++o) {
+      const T *col = a.yin + base + (o < nvalid ? o : 0) * ostride + t0;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        int zz = k - 4;
+        bool in = zz >= 0 && zz < Ez;
+        if (!in && a.periodic) {
+          zz = zz < 0 ? zz + Ez : zz - Ez;
+          in = true;
+        }
+        const T *pz = col + (long long)zz * plane;
+        q[r][o][k] = Op::mk((in && valid[r]) ? pz[0] : T(0), (in && v1[r]) ? pz[1] : T(0));
+      }
+    }
   }
   __syncthreads();
 
-  T dot = T(0);
+  T dot[NO];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) dot[o] = T(0);
   for (int z = 0; z < Ez; ++z) {
     const int buf = z & 1;
-    T *P0 = pin + buf * pplane;
-#pragma unroll
-    for (int r = 0; r < PP; ++r) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!(h == 0 ? valid[r] : v1[r])) continue;
-        const int x = px[r] + h, y = py[r];
-        const T v = h == 0 ? q[r][4].x : q[r][4].y;
-        P0[(y + 4) * pitch + x + 4] = v;
-        if (a.periodic) {
-          if (x < 4) P0[(y + 4) * pitch + x + Ex + 4] = v;
-          if (x >= Ex - 4) P0[(y + 4) * pitch + x - Ex + 4] = v;
-          if (y < 4) P0[(y + Ey + 4) * pitch + x + 4] = v;
-          if (y >= Ey - 4) P0[(y - Ey + 4) * pitch + x + 4] = v;
-        }
-      }
-    }
-    RLE<T> *RL = rl + buf * Ey * A;
-    int *RN = rn + buf * Ey;
-    build_rows<T, NT>(z, Ex, Ey, A, stab, tabw, zl_b, zl_i, sk, RL, nullptr, RN);
-    __syncthreads();
-    if (proj && z > 0) {
-      const int pb = (z - 1) & 1;
-      project_rows<T, NT>(pout + pb * plane, z - 1, Ex, Ey, A, stab, tabw, box, rl + pb * Ey * A, nullptr,
-                          rn + pb * Ey, pacc);
-    }
-
+    T *P0 = pin + buf * NO * pplane;
 #pragma unroll
     for (int r = 0; r < PP; ++r) {
       if (!valid[r]) continue;
       const int x = px[r], y = py[r];
+      const int c = (y + 4) * pitch + x + 4;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        T *Po = P0 + o * pplane;
+        const V v = q[r][o][4];
+        Po[c] = v.x;
+        if (v1[r]) Po[c + 1] = v.y;
+        if (a.periodic) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !v1[r]) continue;
+            const int xx = x + h;
+            const T vv = h == 0 ? v.x : v.y;
+            if (xx < 4) Po[c + h + Ex] = vv;
+            if (xx >= Ex - 4) Po[c + h - Ex] = vv;
+            if (y < 4) Po[c + h + Ey * pitch] = vv;
+            if (y >= Ey - 4) Po[c + h - Ey * pitch] = vv;
+          }
+        }
+      }
+    }
+    RU<T, NO> *RUb = ru + buf * Ey * A;
+    int *RK = rk + buf * Ey * A;
+    int *RN = rn + buf * Ey;
+    build_rows<T, NT, NO>(z, Ex, Ey, A, stab, tabw, zl_b, zl_i, sk, RUb, RK, RN);
+    __syncthreads();
+    if (proj && z > 0) {
+      const int pb = (z - 1) & 1;
+      project_rows<T, NT, NO>(pout + pb * NO * plane, plane, z - 1, Ex, Ey, A, stab, tabw, box, rk + pb * Ey * A,
+                              rn + pb * Ey, pacc, nvalid);
+    }
+
+    // next planes' global values: issue the loads early
+    int zn = z + 5;
+    bool zin = zn < Ez;
+    if (!zin && a.periodic) {
+      zn -= Ez;
+      zin = true;
+    }
+    const long long zoff = (long long)zn * plane;
+    const long long o_here = (long long)z * plane;
+#pragma unroll
+    for (int r = 0; r < PP; ++r) {
+      if (!valid[r]) continue;
+      const int x = px[r], y = py[r];
+      const int t0 = y * Ex + x;
       const T *c0 = P0 + (y + 4) * pitch + x + 4;
-      const V cv = q[r][4];
-      V hv = Op::splat(T(0));
-      {
-        // x taps: values at x-4 .. x+5 (five aligned pairs)
+      V nxt[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        const T *pz = a.yin + base + (o < nvalid ? o : 0) * ostride + zoff + t0;
+        nxt[o] = Op::mk(zin ? pz[0] : T(0), (zin && v1[r]) ? pz[1] : T(0));
+      }
+      const V vv = Op::mk(vf[o_here + t0], v1[r] ? vf[o_here + t0 + 1] : T(0));
+      V hxy[NO], hz[NO], hn[NO];
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        const T *co = c0 + o * pplane;
+        const V cv = q[r][o][4];
+        V h1 = Op::splat(T(0)), h2 = Op::splat(T(0));
         T xv[10];
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
-          const V v = ld2(c0 - 4 + 2 * j);
+          const V v = ld2(co - 4 + 2 * j);
           xv[2 * j] = v.x;
           xv[2 * j + 1] = v.y;
         }
@@ -308,71 +350,87 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_hstep(HArgs<T> a) {
         for (int n = 1; n <= 4; ++n) {
           const V pa = Op::mk(xv[4 + n], xv[5 + n]);
           const V pb = Op::mk(xv[4 - n], xv[5 - n]);
-          hv = Op::fma(Op::splat(a.kx[n]), Op::add(Op::sub(pa, cv), Op::sub(pb, cv)), hv);
+          h1 = Op::fma(Op::splat(a.kx[n]), Op::add(Op::sub(pa, cv), Op::sub(pb, cv)), h1);
+          const V up = ld2(co + n * pitch);
+          const V dn = ld2(co - n * pitch);
+          h2 = Op::fma(Op::splat(a.ky[n]), Op::add(Op::sub(up, cv), Op::sub(dn, cv)), h2);
+        }
+        V h3 = Op::mul(vv, cv);
+#pragma unroll
+        for (int n = 1; n <= 4; ++n)
+          h3 = Op::fma(Op::splat(a.kz[n]), Op::add(Op::sub(q[r][o][4 + n], cv), Op::sub(q[r][o][4 - n], cv)), h3);
+        hxy[o] = Op::add(h1, h2);
+        hz[o] = h3;
+        hn[o] = Op::splat(T(0));
+      }
+      const int cnt = RN[y];
+      const RU<T, NO> *ry = RUb + y * A;
+      const int *rky = RK + y * A;
+      for (int e = 0; e < cnt; ++e) {
+        const V g = ld2(stab + rky[e] * tabw + x);
+        const RU<T, NO> rec = ry[e];
+#pragma unroll
+        for (int o = 0; o < NO; ++o) hn[o] = Op::fma(rec.u[o], g, hn[o]);
+      }
+      const long long o0 = o_here + t0;
+#pragma unroll
+      for (int o = 0; o < NO; ++o) {
+        if (o >= nvalid) continue;
+        const V cv = q[r][o][4];
+        const V hv = Op::add(Op::add(hxy[o], hz[o]), hn[o]);
+        V out;
+        if (a.mode == HSTEP_CHEB) {
+          out = Op::mul(Op::splat(alpha), Op::fma(Op::splat(-shift), cv, hv));
+          if (use_prev) {
+            const T *pv = a.yprev + base + o * ostride + o0;
+            out = Op::fma(Op::splat(beta), Op::mk(pv[0], v1[r] ? pv[1] : T(0)), out);
+          }
+        } else if (a.mode == HSTEP_ADJ) {
+          dot[o] += cv.x * hv.x + (v1[r] ? cv.y * hv.y : T(0));
+          out = Op::mul(Op::splat(occ2[o]), hv);
+        } else {
+          out = hv;
+        }
+        if (a.yout) {
+          T *po = a.yout + base + o * ostride + o0;
+          po[0] = out.x;
+          if (v1[r]) po[1] = out.y;
+        }
+        if (proj) {
+          T *pp = pout + (buf * NO + o) * plane + t0;
+          pp[0] = out.x;
+          if (v1[r]) pp[1] = out.y;
         }
       }
+      // advance the z columns
 #pragma unroll
-      for (int n = 1; n <= 4; ++n) {
-        const V up = ld2(c0 + n * pitch);
-        const V dn = ld2(c0 - n * pitch);
-        hv = Op::fma(Op::splat(a.ky[n]), Op::add(Op::sub(up, cv), Op::sub(dn, cv)), hv);
-      }
+      for (int o = 0; o < NO; ++o) {
 #pragma unroll
-      for (int n = 1; n <= 4; ++n)
-        hv = Op::fma(Op::splat(a.kz[n]), Op::add(Op::sub(q[r][4 + n], cv), Op::sub(q[r][4 - n], cv)), hv);
-      const long long o0 = (long long)z * plane + y * Ex + x;
-      hv = Op::fma(Op::mk(vf[o0], v1[r] ? vf[o0 + 1] : T(0)), cv, hv);
-      const int cnt = RN[y];
-      const RLE<T> *ry = RL + y * A;
-      for (int e = 0; e < cnt; ++e) {
-        const RLE<T> rec = ry[e];
-        hv = Op::fma(Op::splat(rec.u), ld2(stab + rec.k * tabw + x), hv);
+        for (int k = 0; k < 8; ++k) q[r][o][k] = q[r][o][k + 1];
+        q[r][o][8] = nxt[o];
       }
-      V out;
-      if (a.mode == HSTEP_CHEB) {
-        out = Op::mul(Op::splat(alpha), Op::fma(Op::splat(-shift), cv, hv));
-        if (use_prev) out = Op::fma(Op::splat(beta), Op::mk(ypv[o0], v1[r] ? ypv[o0 + 1] : T(0)), out);
-      } else if (a.mode == HSTEP_ADJ) {
-        dot += cv.x * hv.x + (v1[r] ? cv.y * hv.y : T(0));
-        out = Op::mul(Op::splat(occ2), hv);
-      } else {
-        out = hv;
-      }
-      if (yout) {
-        yout[o0] = out.x;
-        if (v1[r]) yout[o0 + 1] = out.y;
-      }
-      if (proj) {
-        pout[buf * plane + y * Ex + x] = out.x;
-        if (v1[r]) pout[buf * plane + y * Ex + x + 1] = out.y;
-      }
-    }
-    // advance the z columns
-#pragma unroll
-    for (int r = 0; r < PP; ++r) {
-      const int t0 = px[r] + py[r] * Ex;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) q[r][k] = q[r][k + 1];
-      q[r][8] = Op::mk(ldz(yin, z + 5, Ez, plane, t0, valid[r], a.periodic),
-                       ldz(yin, z + 5, Ez, plane, t0 + 1, v1[r], a.periodic));
     }
   }
   if (proj) {
     __syncthreads();
     const int pb = (Ez - 1) & 1;
-    project_rows<T, NT>(pout + pb * plane, Ez - 1, Ex, Ey, A, stab, tabw, box, rl + pb * Ey * A, nullptr,
-                        rn + pb * Ey, pacc);
+    project_rows<T, NT, NO>(pout + pb * NO * plane, plane, Ez - 1, Ex, Ey, A, stab, tabw, box, rk + pb * Ey * A,
+                            rn + pb * Ey, pacc, nvalid);
     __syncthreads();
-    for (int k = threadIdx.x; k < A; k += NT) {
+    for (int t = threadIdx.x; t < nvalid * A; t += NT) {
+      const int o = t / A, k = t - o * A;
       T s = T(0);
-      for (int y = 0; y < Ey; ++y) s += pacc[y * A + k];
+      for (int y = 0; y < Ey; ++y) s += pacc[(o * Ey + y) * A + k];
       const ProjSlot S = a.slots[D.at_off + k];
-      a.cout[D.c_off + (long long)i * A + k] = T(S.coef * a.dV) * s;
+      a.cout[D.c_off + (long long)(i0 + o) * A + k] = T(S.coef * a.dV) * s;
     }
   }
   if (a.mode == HSTEP_ADJ) {
-    const T s = block_sum<T, NT>(dot, red);
-    if (threadIdx.x == 0) a.dots[item] = a.occ[D.st_off + i] * a.dV * (double)s;
+#pragma unroll
+    for (int o = 0; o < NO; ++o) {
+      const T s = block_sum<T, NT>(dot[o], red);
+      if (threadIdx.x == 0 && o < nvalid) a.dots[D.st_off + i0 + o] = a.occ[D.st_off + i0 + o] * a.dV * (double)s;
+    }
   }
 }
 
@@ -416,9 +474,9 @@ __global__ void __launch_bounds__(NT) k_project(HArgs<T> a) {
     const int buf = z & 1;
     T *cur = pl + buf * plane;
     for (int t = threadIdx.x; t < plane; t += NT) cur[t] = yin[(long long)z * plane + t];
-    build_rows<T, NT>(z, Ex, Ey, A, stab, tabw, zl_b, zl_i, nullptr, nullptr, kl + buf * Ey * A, rn + buf * Ey);
+    build_rows<T, NT, 1>(z, Ex, Ey, A, stab, tabw, zl_b, zl_i, nullptr, nullptr, kl + buf * Ey * A, rn + buf * Ey);
     __syncthreads();
-    project_rows<T, NT>(cur, z, Ex, Ey, A, stab, tabw, box, nullptr, kl + buf * Ey * A, rn + buf * Ey, pacc);
+    project_rows<T, NT, 1>(cur, plane, z, Ex, Ey, A, stab, tabw, box, kl + buf * Ey * A, rn + buf * Ey, pacc, 1);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < A; k += NT) {
@@ -473,16 +531,16 @@ int max_tabw(const dc_ctx *c) {
   return w;
 }
 
-size_t hstep_smem(dc_ctx *c, size_t esz, int NT) {
+size_t hstep_smem(dc_ctx *c, size_t esz, int NT, int NO) {
   const int Ex = c->max_E[0], Ey = c->max_E[1], Ez = c->max_E[2];
   const int A = c->max_atoms;
   const int pitch = (Ex + 9) & ~1;
-  size_t n = 2 * (size_t)pitch * (Ey + 8) + (size_t)A * max_tabw(c) + 2 * (size_t)Ex * Ey + (size_t)Ey * A +
-             (size_t)A + NT / 32;
+  size_t n = 2 * (size_t)NO * pitch * (Ey + 8) + (size_t)A * max_tabw(c) + 2 * (size_t)NO * Ex * Ey +
+             (size_t)NO * Ey * A + (size_t)NO * A + NT / 32;
   size_t bytes = (n * esz + 15) & ~(size_t)15;
-  const size_t rle = esz == 8 ? 16 : 8;
-  bytes += sizeof(int4) * (size_t)A + rle * 2 * (size_t)Ey * A + sizeof(int) * 2 * (size_t)Ey +
-           sizeof(int) * (size_t)(Ez + 1) + sizeof(int) * (size_t)c->max_zlist;
+  const size_t rue = 2 * esz * NO;  // one record: NO splatted pairs
+  bytes += sizeof(int4) * (size_t)A + rue * 2 * (size_t)Ey * A + sizeof(int) * 2 * (size_t)Ey * A +
+           sizeof(int) * 2 * (size_t)Ey + sizeof(int) * (size_t)(Ez + 1) + sizeof(int) * (size_t)c->max_zlist;
   return bytes + 64;
 }
 
@@ -496,15 +554,17 @@ size_t project_smem(dc_ctx *c, size_t esz) {
   return bytes + 64;
 }
 
-template <typename T, int NT, int PP>
+template <typename T, int NT, int PP, int NO>
 int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
-  const size_t sm = hstep_smem(c, sizeof(T), NT);
+  const size_t sm = hstep_smem(c, sizeof(T), NT, NO);
   if (sm > 227 * 1024) {
     dc_set_error("hpsi: fragment tables exceed shared memory");
     return DC_ERR_ARG;
   }
-  DC_CUDA(dc_set_smem((const void *)k_hstep<T, NT, PP>, sm));
-  k_hstep<T, NT, PP><<<(unsigned)c->layout.nstates, NT, sm, s>>>(a);
+  DC_CUDA(dc_set_smem((const void *)k_hstep<T, NT, PP, NO>, sm));
+  if (NO == 2) a.items = c->d_items2;
+  const unsigned grid = NO == 2 ? (unsigned)c->n_items2 : (unsigned)c->layout.nstates;
+  k_hstep<T, NT, PP, NO><<<grid, NT, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -513,16 +573,18 @@ int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
 constexpr int kShapes[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {512, 1}, {512, 2}, {512, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
+// FP32 runs two orbitals per thread; FP64 one (its pairs of doubles would not fit in registers twice)
 template <typename T>
 int run_shape(dc_ctx *c, int shape, HArgs<T> a, cudaStream_t s) {
+  constexpr int NO = sizeof(T) == 4 ? 2 : 1;
   switch (shape) {
-    case 0: return run_hstep<T, 128, 1>(c, a, s);
-    case 1: return run_hstep<T, 128, 2>(c, a, s);
-    case 2: return run_hstep<T, 256, 1>(c, a, s);
-    case 3: return run_hstep<T, 256, 2>(c, a, s);
-    case 4: return run_hstep<T, 512, 1>(c, a, s);
-    case 5: return run_hstep<T, 512, 2>(c, a, s);
-    default: return run_hstep<T, 512, 4>(c, a, s);
+    case 0: return run_hstep<T, 128, 1, NO>(c, a, s);
+    case 1: return run_hstep<T, 128, 2, NO>(c, a, s);
+    case 2: return run_hstep<T, 256, 1, NO>(c, a, s);
+    case 3: return run_hstep<T, 256, 2, NO>(c, a, s);
+    case 4: return run_hstep<T, 512, 1, NO>(c, a, s);
+    case 5: return run_hstep<T, 512, 2, NO>(c, a, s);
+    default: return run_hstep<T, 512, 4, NO>(c, a, s);
   }
 }
 

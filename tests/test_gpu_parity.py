@@ -90,7 +90,7 @@ def test_ionic_potential_and_starting_density(case):
     # starting density is FFT noise around zero, v_x = -(3 rho/pi)^(1/3) turns that noise into
     # cbrt-sized differences; those points are compared against that bound instead.
     scale = np.max(np.abs(ref_v)) + np.max(np.abs(model.hartree(st.grid, st.rho_in)))
-    dense = ref_r > 1e-9 * np.max(ref_r)
+    dense = ref_r > 1e-6 * np.max(ref_r)  # d(rho^(1/3))/drho stays below ~1e4 here
     diff = np.abs(_np(veff) - ref_e)
     assert np.max(diff[dense]) <= 1e-12 * scale
     assert np.max(diff, initial=0.0) <= 1e-12 * scale + 2.0 * np.cbrt(3.0 * 1e-9 * np.max(ref_r) / np.pi)
