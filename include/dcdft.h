@@ -212,6 +212,26 @@ int dc_set_state(dc_ctx *ctx, const void *d_psi, const double *d_eps, void *stre
  * Outputs (device, FP64): d_rho[npts]; d_q[nstates] and d_mu[1] may be NULL. */
 int dc_density(dc_ctx *ctx, double *d_rho, double *d_q, double *d_mu, void *stream);
 
+/* Allocation-free chemical potential.  The paper has no counterpart: this is a library variant of
+ * the Fermi-level solve inside dc_density (same kernel, same stopping rule), for callers that may
+ * not allocate device memory where they need mu (a caller-owned pool or arena holding the device,
+ * or work interleaved with other streams where cudaFree would synchronise the device).  It needs
+ * no context and makes no cudaMalloc/cudaFree or other allocating call: its scratch is a fixed
+ * 12,352-byte array in the library's static device memory (FP64 partials for at most 256 blocks,
+ * plus barrier and error words that the call zeroes on the stream before each launch).
+ * Inputs (device, FP64): d_eps[nstates] eigenvalues, d_q[nstates] core weights; n_elec >= 0
+ * electrons; kT > 0 (Ha).  Solves sum_i 2 f((eps_i - mu)/kT) q_i = n_elec and writes d_mu[1]
+ * and d_occ[nstates] = f_i (device).  *d_mu on entry serves as the starting guess when it lies in
+ * the bracket; any value is accepted.  Synchronises the stream before returning.
+ * Setup: the first call on each device looks up the scratch address (cudaGetSymbolAddress), the SM
+ * count and the kernel's residency; a call with nstates = 0 does only that, so do it before any
+ * stream capture begins.  Calls on one device share the scratch: calls that overlap in time
+ * (several host threads, or streams not ordered with each other) race and must be serialised by
+ * the caller.  Errors: DC_ERR_ARG (nstates outside [0, 2^31 - 1], NULL pointer, bad kT or n_elec),
+ * DC_ERR_TIMEOUT, DC_ERR_NONFINITE, DC_ERR_CUDA. */
+int dc_fermi_level_noalloc(const double *d_eps, const double *d_q, int64_t nstates, double n_elec, double kT,
+                           double *d_mu, double *d_occ, void *stream);
+
 /* ---- SCF step ------------------------------------------------------------------------- */
 /* One DC-DFT SCF iteration (Sec. 2.2): V_eff[rho_in], n_pass CheFSI passes, q, mu, rho_out,
  * energies, and linear mixing written back: rho_in <- rho_in + alpha (rho_out - rho_in).

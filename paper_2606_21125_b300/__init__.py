@@ -14,7 +14,7 @@ from . import _lib
 from ._lib import (DC_BC_PERIODIC, DC_BC_ZERO, DC_FP32, DC_FP64, DC_HXC_HARTREE_X, DC_HXC_NONE, DC_MIXED,
                    DCError, check, load)
 
-__all__ = ["DCSolver", "Eb", "DCError", "load", "DC_FP64", "DC_FP32", "DC_MIXED"]
+__all__ = ["DCSolver", "Eb", "DCError", "load", "fermi_level_noalloc", "DC_FP64", "DC_FP32", "DC_MIXED"]
 
 PRECISIONS = {"fp64": DC_FP64, "fp32": DC_FP32, "mixed": DC_MIXED}
 BCS = {"zero": DC_BC_ZERO, "periodic": DC_BC_PERIODIC}
@@ -190,6 +190,15 @@ class DCSolver:
                                                       C.byref(Eb), _ptr(dpsi), _ptr(dV), _ptr(dD),
                                                       _stream(stream)))
         return Eb.value, dpsi, dV, dD
+
+
+def fermi_level_noalloc(eps, q, n_elec, kT, mu, occ, stream=None):
+    """``dc_fermi_level_noalloc``: mu and occupations from eigenvalues ``eps`` and core weights ``q``
+    (CUDA float64 tensors of one length) into the caller's tensors ``mu`` (1 element, read as the
+    starting guess) and ``occ``.  The library allocates nothing; this wrapper creates no tensors."""
+    lib = load()
+    check("dc_fermi_level_noalloc", lib.dc_fermi_level_noalloc(_ptr(eps), _ptr(q), int(eps.numel()), float(n_elec),
+                                                               float(kT), _ptr(mu), _ptr(occ), _stream(stream)))
 
 
 def _profile_methods():

@@ -1,5 +1,9 @@
 // Density stage (Sec. 2.2, Eqs. 2-4): core weights, global chemical potential, occupations and the
 // core-projected density rho_tot(g) = sum_i 2 f_i^f psi_i^f(j)^2 with f = owner(g).
+#include <climits>
+#include <cmath>
+#include <mutex>
+
 #include "dc_internal.h"
 
 namespace {
@@ -240,3 +244,116 @@ template int launch_density<double>(dc_ctx *, const double *, double *, cudaStre
 template int launch_density<float>(dc_ctx *, const float *, double *, cudaStream_t);
 
 }  // namespace dck
+
+// ---- allocation-free Fermi level ---------------------------------------------------------------
+// dc_fermi_level_noalloc runs the k_fermi solve above without a context: its scratch is a fixed
+// array in this module's static device memory instead of context buffers.  It exists for callers
+// that may not allocate device memory at the point where they need mu: code working inside a
+// caller-owned memory pool or arena that holds the whole device (no cudaMalloc can succeed
+// there), and code interleaved with work on other streams, where a cudaFree would synchronise
+// the device.  Layout of the array: bytes [0, 64) are unsigned words (0: error flags,
+// 1: barrier arrival count, 2: barrier generation), zeroed on the stream before every launch;
+// from byte 64 on, 6 FP64 partials per block (a min/max pair, then two double-buffered pairs of
+// sums), written before they are read inside each launch, so they need no clearing.
+constexpr int kFermiNoallocBlocks = 256;
+constexpr size_t kFermiNoallocHeader = 64;
+constexpr size_t kFermiNoallocBytes = kFermiNoallocHeader + 6 * sizeof(double) * kFermiNoallocBlocks;  // 12,352
+
+static __device__ __align__(256) unsigned char g_fermi_scratch[kFermiNoallocBytes];
+
+namespace {
+
+constexpr int kFermiNoallocMaxDevices = 64;
+
+struct FermiNoallocDevice {
+  bool ready = false;
+  unsigned char *scratch = nullptr;  // device address of g_fermi_scratch on this device
+  int sm_count = 0;
+};
+
+std::mutex g_fermi_noalloc_mutex;
+FermiNoallocDevice g_fermi_noalloc_dev[kFermiNoallocMaxDevices];
+
+// Looks up the scratch address, the SM count and the co-residency of k_fermi once per device.
+int fermi_noalloc_setup(FermiNoallocDevice **out) {
+  int dev = -1;
+  DC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kFermiNoallocMaxDevices) {
+    dc_set_error("dc_fermi_level_noalloc: device ordinal above 63");
+    return DC_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_fermi_noalloc_mutex);
+  FermiNoallocDevice &d = g_fermi_noalloc_dev[dev];
+  if (!d.ready) {
+    void *addr = nullptr;
+    DC_CUDA(cudaGetSymbolAddress(&addr, g_fermi_scratch));
+    int sms = 0, resident = 0;
+    DC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_fermi, QNT, 0));
+    if (sms < 1 || resident < 1) {
+      dc_set_error("dc_fermi_level_noalloc: k_fermi cannot be resident on this device");
+      return DC_ERR_CUDA;
+    }
+    d.scratch = static_cast<unsigned char *>(addr);
+    d.sm_count = sms;
+    d.ready = true;
+  }
+  *out = &d;
+  return DC_OK;
+}
+
+}  // namespace
+
+extern "C" int dc_fermi_level_noalloc(const double *d_eps, const double *d_q, int64_t nstates, double n_elec,
+                                      double kT, double *d_mu, double *d_occ, void *stream) {
+  if (nstates < 0 || nstates > (int64_t)INT_MAX) {
+    dc_set_error("dc_fermi_level_noalloc: nstates outside [0, 2^31 - 1] (the kernel indexes states with int)");
+    return DC_ERR_ARG;
+  }
+  FermiNoallocDevice *dev = nullptr;
+  DC_TRY(fermi_noalloc_setup(&dev));
+  if (nstates == 0) return DC_OK;  // setup only
+  if (!d_eps || !d_q || !d_mu || !d_occ) {
+    dc_set_error("dc_fermi_level_noalloc: NULL device pointer");
+    return DC_ERR_ARG;
+  }
+  if (!(kT > 0.0) || !std::isfinite(kT) || !(n_elec >= 0.0) || !std::isfinite(n_elec)) {
+    dc_set_error("dc_fermi_level_noalloc: kT must be finite and > 0, n_elec finite and >= 0");
+    return DC_ERR_ARG;
+  }
+  // one block per SM (all co-resident), no more blocks than states need or the scratch holds
+  int grid = dev->sm_count;
+  const int need = (int)((nstates + QNT - 1) / QNT);
+  if (grid > need) grid = need;
+  if (grid > kFermiNoallocBlocks) grid = kFermiNoallocBlocks;
+  if (kFermiNoallocHeader + 6 * sizeof(double) * (size_t)grid > kFermiNoallocBytes) {
+    dc_set_error("dc_fermi_level_noalloc: partials exceed the 12,352-byte static scratch");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned *words = reinterpret_cast<unsigned *>(dev->scratch);
+  DC_CUDA(cudaMemsetAsync(words, 0, kFermiNoallocHeader, s));
+  const double *eps = d_eps;
+  const double *q = d_q;
+  int nst = (int)nstates;
+  double ne = n_elec, t = kT;
+  double *partials = reinterpret_cast<double *>(dev->scratch + kFermiNoallocHeader);
+  unsigned *bar = words + 1;
+  unsigned *flags = words;
+  double *mu = d_mu;
+  double *occ = d_occ;
+  void *args[] = {&eps, &q, &nst, &ne, &t, &partials, &bar, &flags, &mu, &occ};
+  DC_CUDA(cudaLaunchCooperativeKernel((const void *)k_fermi, dim3(grid), dim3(QNT), args, 0, s));
+  unsigned fl = 0;
+  DC_CUDA(cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  DC_CUDA(cudaStreamSynchronize(s));
+  if (fl & DC_FLAG_TIMEOUT) {
+    dc_set_error("dc_fermi_level_noalloc: a bounded device wait ran out (grid barrier)");
+    return DC_ERR_TIMEOUT;
+  }
+  if (fl & DC_FLAG_NONFINITE) {
+    dc_set_error("dc_fermi_level_noalloc: non-finite chemical potential");
+    return DC_ERR_NONFINITE;
+  }
+  return DC_OK;
+}
