@@ -255,14 +255,21 @@ int dc_eb_adjoint(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_occ
                   const double *d_D, double *h_Eb, void *d_dpsi, double *d_dV, double *d_dD, void *stream);
 
 /* ---- autotuner ------------------------------------------------------------------------- */
-/* dc_warmup times every useful launch shape (threads per CTA, x-adjacent point pairs per thread) of
- * the stencil H-apply kernel on the context's own fragments and keeps the fastest, separately for
- * FP32 and FP64 elements.  With the environment variable DC_TUNE_CACHE=<file> results are looked up
- * in / appended to that text file (one line per fragment shape, atom and orbital count, type).
- * h_shape[4] = {fp32 threads, fp32 pairs, fp64 threads, fp64 pairs} (0 = not tuned yet);
- * h_ms[16] (may be NULL) = best time in ms of each of the 8 candidate shapes, FP32 then FP64
+/* dc_warmup times every useful launch shape of the stencil H-apply kernels on the context's own
+ * fragments and keeps the fastest, separately for FP32 and FP64 elements.  A shape is (kind, threads
+ * per CTA, point pairs per thread); kind 0 pairs x-adjacent points of one orbital (FP32: two
+ * orbitals per CTA), kind 1 (FP32 only) interleaves two orbitals at every point.  With the
+ * environment variable DC_TUNE_CACHE=<file> results are looked up in / appended to that text file
+ * (one line per fragment shape, atom and orbital count, type).
+ * h_shape[6] = {fp32 kind, threads, pairs, fp64 kind, threads, pairs} (threads 0 = not tuned yet);
+ * h_ms[32] (may be NULL) = best time in ms of each of the 16 candidate slots, FP32 then FP64
  * (0 = not tried). */
 int dc_tuning(const dc_ctx *ctx, int *h_shape, float *h_ms);
+
+/* Pin the stencil launch shape (kind, threads, pairs as in dc_tuning) for element type dtype
+ * (DC_FP64 or DC_FP32); dc_warmup then keeps it instead of tuning.  Errors: DC_ERR_ARG when the
+ * shape does not exist or cannot cover / fit this context's largest fragment. */
+int dc_set_tuning(dc_ctx *ctx, int dtype, int kind, int threads, int pairs);
 
 /* ---- stage profiler -------------------------------------------------------------------- */
 /* Stages of the step, in the order they run. */

@@ -214,13 +214,23 @@ def _profile_methods():
         return {name: dict(ms=ms[i], launches=int(nl[i]), bytes=by[i]) for i, name in enumerate(_lib.STAGES)}
 
     def tuning(self):
-        shp = (C.c_int * 4)()
-        ms = (C.c_float * 16)()
+        shp = (C.c_int * 6)()
+        ms = (C.c_float * 32)()
         check("dc_tuning", self.lib.dc_tuning(self.ctx, shp, ms))
-        return dict(fp32=dict(threads=shp[0], pairs=shp[1], candidates_ms=list(ms[0:8])),
-                    fp64=dict(threads=shp[2], pairs=shp[3], candidates_ms=list(ms[8:16])))
+        return dict(fp32=dict(kind=shp[0], threads=shp[1], pairs=shp[2], candidates_ms=list(ms[0:16])),
+                    fp64=dict(kind=shp[3], threads=shp[4], pairs=shp[5], candidates_ms=list(ms[16:32])))
+
+    def set_tuning(self, dtype, kind, threads, pairs):
+        """Pin the stencil launch shape for ``dtype`` ("fp64" or "fp32"); False if it does not fit."""
+        st = self.lib.dc_set_tuning(self.ctx, PRECISIONS[dtype], int(kind), int(threads), int(pairs))
+        if st == _lib.DC_OK:
+            return True
+        if st == -1:
+            return False
+        check("dc_set_tuning", st)
 
     DCSolver.profile = profile
+    DCSolver.set_tuning = set_tuning
     DCSolver.profile_read = profile_read
     DCSolver.tuning = tuning
 

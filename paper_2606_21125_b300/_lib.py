@@ -84,6 +84,7 @@ PROTOTYPES = {
     "dc_get_rho_out": (C.c_int, [VP, VP, VP]),
     "dc_eb_adjoint": (C.c_int, [VP, VP, C.c_int, VP, VP, VP, PD, VP, VP, VP, VP]),
     "dc_tuning": (C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "dc_set_tuning": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, C.c_int]),
     "dc_profile": (C.c_int, [VP, C.c_int]),
     "dc_profile_read": (C.c_int, [VP, PD, C.POINTER(C.c_int64), PD]),
 }

@@ -75,7 +75,7 @@ void free_ctx(dc_ctx *c) {
                   c->blk64[1], c->blk64[2], c->d_hy64, c->d_c64[0], c->d_c64[1], c->d_c32[0], c->d_c32[1],
                   c->d_eps, c->d_q, c->d_occ, c->d_bounds, c->d_gram, c->d_gram_off, c->d_gram_nchunk, c->d_C64,
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
-                  c->d_items2,
+                  c->d_items2, c->d_row_beg, c->d_row_ent,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
                   c->d_dots};
   for (void *p : ptrs)
@@ -457,6 +457,8 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(upload(&c->d_tab32, tab32));
   DC_TRY(upload(&c->d_zl_beg, ht.zl_beg));
   DC_TRY(upload(&c->d_zl_items, ht.zl_items));
+  DC_TRY(upload(&c->d_row_beg, ht.row_beg));
+  DC_TRY(upload(&c->d_row_ent, ht.row_ent));
   std::vector<double> Datom(c->natom), posv(c->h_pos);
   for (int a = 0; a < c->natom; ++a) Datom[a] = c->h_Ds[c->h_species[a]];
   DC_TRY(upload(&c->d_atom_D, Datom));
@@ -931,11 +933,27 @@ int dc_tuning(const dc_ctx *c, int *h_shape, float *h_ms) {
     return DC_ERR_ARG;
   }
   for (int t = 0; t < 2; ++t) {
-    h_shape[2 * t] = h_shape[2 * t + 1] = 0;
-    if (c->hstep_shape[t] >= 0) dck::hstep_shape_info(c->hstep_shape[t], &h_shape[2 * t], &h_shape[2 * t + 1]);
+    int *sh = h_shape + 3 * t;
+    sh[0] = sh[1] = sh[2] = 0;
+    if (c->hstep_shape[t] >= 0) dck::hstep_shape_info(c->hstep_shape[t], &sh[0], &sh[1], &sh[2]);
     if (h_ms)
-      for (int k = 0; k < 8; ++k) h_ms[8 * t + k] = c->tune_ms[t][k];
+      for (int k = 0; k < DC_TUNE_SLOTS; ++k) h_ms[DC_TUNE_SLOTS * t + k] = c->tune_ms[t][k];
   }
+  return DC_OK;
+}
+
+int dc_set_tuning(dc_ctx *c, int dtype, int kind, int threads, int pairs) {
+  if (!c || (dtype != DC_FP64 && dtype != DC_FP32)) {
+    dc_set_error("dc_set_tuning: invalid argument");
+    return DC_ERR_ARG;
+  }
+  const size_t esz = dtype == DC_FP64 ? sizeof(double) : sizeof(float);
+  const int k = dck::hstep_shape_find(c, esz, kind, threads, pairs);
+  if (k < 0) {
+    dc_set_error("dc_set_tuning: no such launch shape, or it does not fit this context's fragments");
+    return DC_ERR_ARG;
+  }
+  c->hstep_shape[dtype == DC_FP64 ? 1 : 0] = k;
   return DC_OK;
 }
 

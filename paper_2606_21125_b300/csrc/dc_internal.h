@@ -28,7 +28,7 @@ struct FragDesc {
   long long c_off;    // offset of the fragment's projections (n_f * A_f values, orbital-major)
   long long sub_off;  // offset of the fragment's n_f x n_f matrices
   int zl_off;         // offset into the per-plane atom list starts (Ez + 1 entries)
-  int pad;
+  int row_off;        // offset into the per-row projector list starts (Ez * Ey + 1 entries)
 };
 
 // Row stride of one atom slot's projector factors [gx (Ex) | gy (Ey) | gz (Ez) | pad], kept even so
@@ -43,6 +43,7 @@ struct ProjSlot {
   double coef;    // (pi sigma^2)^(-3/4)
 };
 
+#define DC_TUNE_SLOTS 16   // candidate launch shapes of the stencil kernels (per element type)
 #define DC_MAX_NORB 64     // subspace kernels hold n x n FP64 matrices in shared memory
 #define DC_MAX_EXTENT 64   // stencil kernels hold padded planes of (E+8)^2 points
 
@@ -82,6 +83,7 @@ struct dc_ctx {
   int max_E[3];
   int max_atoms;      // max |A_f|
   int max_zlist;      // max over f of total per-plane list length
+  int max_plane_ent;  // max over f and z of the row-list entries of one plane
 
   // host copies of maps (for dc_get_maps and launch planning)
   std::vector<FragDesc> h_desc;
@@ -99,6 +101,8 @@ struct dc_ctx {
   float *d_tab32 = nullptr;    // same in FP32
   int *d_zl_beg = nullptr;     // per-plane atom list starts
   int *d_zl_items = nullptr;   // per-plane atom slots
+  int *d_row_beg = nullptr;    // per-row (z, y) list starts into d_row_ent
+  int2 *d_row_ent = nullptr;   // (slot | y << 16, FP32 bits of gz(z) gy(y))
   double *d_atom_D = nullptr;  // D per atom (global index)
   double *d_atom_pos = nullptr;
   int *d_atom_species = nullptr;
@@ -179,7 +183,7 @@ struct dc_ctx {
 
   // autotuned launch shape of the stencil kernel per element type ([0] FP32, [1] FP64; -1 = default)
   int hstep_shape[2] = {-1, -1};
-  float tune_ms[2][8] = {{0}};
+  float tune_ms[2][DC_TUNE_SLOTS] = {{0}};
 
   int steps_done = 0;
   bool warmed = false;
@@ -191,6 +195,8 @@ struct HostTables {
   std::vector<ProjSlot> slots;
   std::vector<double> tab;
   std::vector<int> zl_beg, zl_items;
+  std::vector<int> row_beg;
+  std::vector<int2> row_ent;
 };
 int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out);
 void dc_build_cover(const dc_ctx *c, int d, std::vector<int> &beg, std::vector<int2> &items);
@@ -237,7 +243,8 @@ template <typename T>
 int launch_project(dc_ctx *c, const T *psi, T *cout, cudaStream_t s);
 template <typename T>
 int tune_hstep(dc_ctx *c, const T *y, T *out, T *cbuf, cudaStream_t s);
-int hstep_shape_info(int shape, int *threads, int *pairs);
+int hstep_shape_info(int shape, int *kind, int *threads, int *pairs);
+int hstep_shape_find(const dc_ctx *c, size_t esz, int kind, int threads, int pairs);
 template <typename T>
 int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T *yout, const T *cin, T *cout,
                  const double *Datom, const double *occ, double *dots, const T *vf, cudaStream_t s);

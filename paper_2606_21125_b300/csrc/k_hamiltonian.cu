@@ -23,6 +23,9 @@
 // Chebyshev step needs, are accumulated one plane behind: one task per (row, atom of that row)
 // forms sum_x gx_a[x] out_o(x, y) and adds it into a dense [orbital][row][atom] array (each slot has
 // one writer per plane, so the order is fixed and the result deterministic); rows are summed last.
+#include <algorithm>
+#include <type_traits>
+
 #include "dc_internal.h"
 
 namespace {
@@ -35,6 +38,9 @@ struct HArgs {
   const T *tab;
   const int *zl_beg;
   const int *zl_items;
+  const int *row_beg;
+  const int2 *row_ent;
+  int maxent;
   const T *vf;
   const T *yin;
   const T *yprev;
@@ -487,6 +493,503 @@ __global__ void __launch_bounds__(NT) k_project(HArgs<T> a) {
   }
 }
 
+// ---- orbital-pair kernel (FP32) -----------------------------------------------------------------
+// Two orbitals of one fragment are interleaved at every point: a float2 holds (y_i, y_i+1) at one
+// grid point, so each tap, the potential product and each nonlocal update of both orbitals is one
+// paired instruction on operands that need no lane rearrangement, and every stencil read is an
+// aligned 16-byte shared load covering two x-adjacent points.  A thread owns PP such point pairs of
+// the plane and keeps their 9-deep z columns in registers (float4 = 2 points x 2 orbitals).
+// The taps n = 1, 2 are taken in difference form, (y+n - y) + (y-n - y), the small outer taps
+// n = 3, 4 as sums y+n + y-n with the centre term -2 (k3 + k4) y added once: their coefficients are
+// 60x below k1, so their rounding stays under that of the V y product.  The Chebyshev scaling is
+// folded into the coefficients: out = alpha L y + alpha (V - shift) y + alpha NL + beta y_prev.
+// The per-row projector lists come precomputed from the host (one entry per (row, slot), in z-list
+// order); each plane's entries are turned into records (u_i, u_i+1, slot|row, gz gy) once per CTA.
+// One barrier per plane: point planes and output planes are double-buffered, records triple-buffered.
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// Stencil coefficients, splatted over the orbital pair.  ISO: one set for all three axes.
+template <bool ISO>
+struct PairK {
+  float2 k1[ISO ? 1 : 3], k2[ISO ? 1 : 3], k3[ISO ? 1 : 3], k4[ISO ? 1 : 3];
+  float2 kc;  // -2 sum over axes of (k3 + k4)
+};
+
+// alpha (-1/2 L8) y at one point (centre c) from its 24 neighbours, plus h.
+template <bool ISO>
+__device__ __forceinline__ float2 lap_pair(const PairK<ISO> &K, float2 c, const float2 (&xm)[4],
+                                           const float2 (&xp)[4], const float2 (&ym)[4], const float2 (&yp)[4],
+                                           const float2 (&zm)[4], const float2 (&zp)[4], float2 h) {
+  if (ISO) {
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      float2 d = add2(sub2(xp[n], c), sub2(xm[n], c));
+      d = add2(d, add2(sub2(yp[n], c), sub2(ym[n], c)));
+      d = add2(d, add2(sub2(zp[n], c), sub2(zm[n], c)));
+      h = fma2(n == 0 ? K.k1[0] : K.k2[0], d, h);
+    }
+#pragma unroll
+    for (int n = 2; n < 4; ++n) {
+      const float2 t = add2(add2(add2(xp[n], xm[n]), add2(yp[n], ym[n])), add2(zp[n], zm[n]));
+      h = fma2(n == 2 ? K.k3[0] : K.k4[0], t, h);
+    }
+  } else {
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      const float2 *kk = n == 0 ? K.k1 : K.k2;
+      h = fma2(kk[0], add2(sub2(xp[n], c), sub2(xm[n], c)), h);
+      h = fma2(kk[1], add2(sub2(yp[n], c), sub2(ym[n], c)), h);
+      h = fma2(kk[2], add2(sub2(zp[n], c), sub2(zm[n], c)), h);
+    }
+#pragma unroll
+    for (int n = 2; n < 4; ++n) {
+      const float2 *kk = n == 2 ? K.k3 : K.k4;
+      h = fma2(kk[0], add2(xp[n], xm[n]), h);
+      h = fma2(kk[1], add2(yp[n], ym[n]), h);
+      h = fma2(kk[2], add2(zp[n], zm[n]), h);
+    }
+  }
+  return fma2(K.kc, c, h);
+}
+
+// Shared-memory carve of the orbital-pair kernels (sizes in the fragment's own extents).
+struct PairSmem {
+  float2 *pin, *pout, *gx2, *pacc, *sk2;
+  float4 *rec;
+  int2 *box;
+  int *rb;
+  float *red;
+};
+
+__device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int Ey, int Ez, int A, int maxent,
+                                               int nrec, bool halo) {
+  const int pitch = (Ex + 9) & ~1, pitch2 = (Ex + 1) & ~1;
+  PairSmem m;
+  m.pin = reinterpret_cast<float2 *>(raw);
+  m.pout = m.pin + (halo ? 2 * (Ey + 8) * pitch : 0);
+  m.gx2 = m.pout + 2 * Ey * pitch2;
+  m.pacc = m.gx2 + A * pitch2;
+  m.sk2 = m.pacc + Ey * A;
+  size_t off = (size_t)(reinterpret_cast<unsigned char *>(m.sk2 + A) - raw);
+  off = (off + 15) & ~(size_t)15;
+  m.rec = reinterpret_cast<float4 *>(raw + off);
+  m.box = reinterpret_cast<int2 *>(m.rec + nrec * maxent);
+  m.rb = reinterpret_cast<int *>(m.box + A);
+  m.red = reinterpret_cast<float *>(m.rb + Ez * Ey + 1);
+  return m;
+}
+
+size_t pair_smem_bytes(int Ex, int Ey, int Ez, int A, int maxent, int nrec, bool halo, int NT) {
+  const int pitch = (Ex + 9) & ~1, pitch2 = (Ex + 1) & ~1;
+  size_t n2 = (halo ? 2 * (size_t)(Ey + 8) * pitch : 0) + 2 * (size_t)Ey * pitch2 + (size_t)A * pitch2 +
+              (size_t)Ey * A + A;
+  size_t b = (n2 * sizeof(float2) + 15) & ~(size_t)15;
+  b += (size_t)nrec * maxent * sizeof(float4) + (size_t)A * sizeof(int2) + (size_t)(Ez * Ey + 1) * sizeof(int) +
+       2 * (size_t)(NT / 32) * sizeof(float);
+  return b + 64;
+}
+
+// Common CTA setup: x factors splatted over the pair (zero on the padded column), x supports rounded
+// out to even bounds, row starts relative to the fragment's first entry, zeroed accumulators.
+template <int NT>
+__device__ __forceinline__ void pair_setup(const HArgs<float> &a, const FragDesc &D, const PairSmem &m, int i0,
+                                           int nvalid, float alpha) {
+  const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2], A = D.natom, tabw = tab_width(D);
+  const int pitch2 = (Ex + 1) & ~1;
+  for (int t = threadIdx.x; t < A * pitch2; t += NT) {
+    const int k = t / pitch2, x = t - k * pitch2;
+    const float g = x < Ex ? a.tab[D.tab_off + (long long)k * tabw + x] : 0.f;
+    m.gx2[t] = f2(g, g);
+  }
+  for (int k = threadIdx.x; k < A; k += NT) {
+    const ProjSlot S = a.slots[D.at_off + k];
+    m.box[k] = make_int2(S.lo[0] & ~1, min((S.hi[0] + 1) & ~1, pitch2));
+    const float ds = alpha * float(a.Datom[S.atom] * S.coef);
+    float u0 = 0.f, u1 = 0.f;
+    if (a.cin) {
+      u0 = ds * a.cin[D.c_off + (long long)i0 * A + k];
+      if (nvalid > 1) u1 = ds * a.cin[D.c_off + (long long)(i0 + 1) * A + k];
+    }
+    m.sk2[k] = f2(u0, u1);
+  }
+  const int r0 = a.row_beg[D.row_off];
+  for (int t = threadIdx.x; t <= Ez * Ey; t += NT) m.rb[t] = a.row_beg[D.row_off + t] - r0;
+  for (int t = threadIdx.x; t < Ey * A; t += NT) m.pacc[t] = f2(0.f, 0.f);
+  for (int t = threadIdx.x; t < 2 * Ey * pitch2; t += NT) m.pout[t] = f2(0.f, 0.f);
+}
+
+// Projection tasks of one plane: one task per row-list entry (row y, slot k) forms
+// gz gy sum_x gx_k[x] out(x, y) for both orbitals and adds it to pacc[y][k] (one writer per plane).
+template <int NT>
+__device__ __forceinline__ void pair_project(const float2 *pl, const float4 *rc, int ne, const PairSmem &m,
+                                             int pitch2, int A) {
+  for (int t = threadIdx.x; t < ne; t += NT) {
+    const float4 r = rc[t];
+    const int kb = __float_as_int(r.z);
+    const int k = kb & 0xffff, y = kb >> 16;
+    const int2 bx = m.box[k];
+    const float4 *o4 = reinterpret_cast<const float4 *>(pl + y * pitch2);
+    const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2 + k * pitch2);
+    float2 s0 = f2(0.f, 0.f), s1 = f2(0.f, 0.f);
+    for (int x = bx.x; x < bx.y; x += 2) {
+      const float4 o = o4[x >> 1];
+      const float4 g = g4[x >> 1];
+      s0 = fma2(lo2(o), lo2(g), s0);
+      s1 = fma2(hi2(o), hi2(g), s1);
+    }
+    float2 &pa = m.pacc[y * A + k];
+    pa = fma2(f2(r.w, r.w), add2(s0, s1), pa);
+  }
+}
+
+// Final projections c[i][k] = C_k dV sum_y pacc[y][k] of the pair.
+template <int NT>
+__device__ __forceinline__ void pair_finish(const HArgs<float> &a, const FragDesc &D, const PairSmem &m, int i0,
+                                            int nvalid) {
+  const int Ey = D.E[1], A = D.natom;
+  for (int t = threadIdx.x; t < nvalid * A; t += NT) {
+    const int o = t / A, k = t - o * A;
+    float s = 0.f;
+    for (int y = 0; y < Ey; ++y) {
+      const float2 v = m.pacc[y * A + k];
+      s += o == 0 ? v.x : v.y;
+    }
+    const ProjSlot S = a.slots[D.at_off + k];
+    a.cout[D.c_off + (long long)(i0 + o) * A + k] = float(S.coef * a.dV) * s;
+  }
+}
+
+// Records of plane z: (u_i, u_i+1, slot|row, gz gy) with u = alpha D C <p|y> gz gy.  The first 2 NT
+// entries come from registers (loaded one plane ahead), any further ones straight from global memory.
+template <int NT>
+__device__ __forceinline__ void pair_records(const int2 *ent, int ne, const int2 (&pre)[2], const float2 *sk2,
+                                             float4 *rc) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int t = threadIdx.x + j * NT;
+    if (t < ne) {
+      const int2 e = pre[j];
+      const float w = __int_as_float(e.y);
+      const float2 u = sk2[e.x & 0xffff];
+      rc[t] = make_float4(u.x * w, u.y * w, __int_as_float(e.x), w);
+    }
+  }
+  for (int t = threadIdx.x + 2 * NT; t < ne; t += NT) {
+    const int2 e = ent[t];
+    const float w = __int_as_float(e.y);
+    const float2 u = sk2[e.x & 0xffff];
+    rc[t] = make_float4(u.x * w, u.y * w, __int_as_float(e.x), w);
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ void pair_prefetch(const int2 *ent, int ne, int2 (&pre)[2]) {
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int t = threadIdx.x + j * NT;
+    pre[j] = t < ne ? ent[t] : make_int2(0, 0);
+  }
+}
+
+template <int NT, int PP, bool ISO>
+__global__ void __launch_bounds__(NT, (PP == 1 && NT <= 256) ? 512 / NT : 1) k_hpair(HArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 fi = a.items[blockIdx.x];
+  const int f = fi.x, i0 = fi.y;
+  const FragDesc D = a.desc[f];
+  const int nvalid = min(2, D.norb - i0);
+  const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2];
+  const int plane = Ex * Ey;
+  const int nxp = (Ex + 1) >> 1;
+  const int npairs = nxp * Ey;
+  const int pitch = (Ex + 9) & ~1;
+  const int pitch2 = (Ex + 1) & ~1;
+  const int pplane = pitch * (Ey + 8);
+  const int A = D.natom;
+  const long long P = (long long)plane * Ez;
+  const bool proj = a.cout != nullptr;
+  const PairSmem m = pair_carve(smem_raw, Ex, Ey, Ez, A, a.maxent, 3, true);
+
+  float alpha = 1.f, beta = 0.f, shift = 0.f;
+  if (a.mode == HSTEP_CHEB) {
+    const double *bd = a.bounds + (long long)f * a.bstride;
+    shift = float(bd[3]);
+    alpha = float(bd[4 + 2 * a.step]);
+    beta = float(bd[5 + 2 * a.step]);
+  }
+  const bool use_prev = (a.mode == HSTEP_CHEB) && a.yprev != nullptr && a.step > 0;
+  pair_setup<NT>(a, D, m, i0, nvalid, alpha);
+  for (int t = threadIdx.x; t < 2 * pplane; t += NT) m.pin[t] = f2(0.f, 0.f);
+
+  PairK<ISO> K;
+  {
+    float s34 = 0.f;
+#pragma unroll
+    for (int d = 0; d < (ISO ? 1 : 3); ++d) {
+      float kd[5];
+#pragma unroll
+      for (int n = 1; n < 5; ++n) kd[n] = alpha * (d == 0 ? a.kx[n] : (d == 1 ? a.ky[n] : a.kz[n]));
+      K.k1[d] = f2(kd[1], kd[1]);
+      K.k2[d] = f2(kd[2], kd[2]);
+      K.k3[d] = f2(kd[3], kd[3]);
+      K.k4[d] = f2(kd[4], kd[4]);
+      s34 += (ISO ? 3.f : 1.f) * (kd[3] + kd[4]);
+    }
+    K.kc = f2(-2.f * s34, -2.f * s34);
+  }
+  const float2 bb = f2(beta, beta);
+  const float vsh = -alpha * shift;
+  float2 occ2 = f2(0.f, 0.f);
+  if (a.mode == HSTEP_ADJ) {
+    occ2.x = float(2.0 * a.occ[D.st_off + i0] * a.dV);
+    if (nvalid > 1) occ2.y = float(2.0 * a.occ[D.st_off + i0 + 1] * a.dV);
+  }
+  // orbital i0 at element offset base, i0+1 at base + P (an invalid second orbital reads the first)
+  const long long base = D.psi_off + (long long)i0 * P;
+  const long long o1off = nvalid > 1 ? P : 0;
+  const float *vf = a.vf + D.pt_off;
+  const int2 *ent = a.row_ent + a.row_beg[D.row_off];
+
+  int px[PP], py[PP];
+  bool valid[PP], v1[PP];
+  float4 q[PP][9];
+#pragma unroll
+  for (int r = 0; r < PP; ++r) {
+    const int p = threadIdx.x + r * NT;
+    valid[r] = p < npairs;
+    py[r] = valid[r] ? p / nxp : 0;
+    px[r] = valid[r] ? 2 * (p - py[r] * nxp) : 0;
+    v1[r] = valid[r] && (px[r] + 1 < Ex);
+    const float *col = a.yin + base + px[r] + py[r] * Ex;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      int zz = k - 4;
+      bool in = zz >= 0 && zz < Ez;
+      if (!in && a.periodic) {
+        zz = zz < 0 ? zz + Ez : zz - Ez;
+        in = true;
+      }
+      const float *pz = col + (long long)zz * plane;
+      const bool i0k = in && valid[r], i1k = in && v1[r];
+      q[r][k] = make_float4(i0k ? pz[0] : 0.f, i0k ? pz[o1off] : 0.f, i1k ? pz[1] : 0.f, i1k ? pz[o1off + 1] : 0.f);
+    }
+  }
+  __syncthreads();
+  int2 pre[2];
+  pair_prefetch<NT>(ent, m.rb[Ey], pre);
+
+  float2 dot = f2(0.f, 0.f);
+  int b3 = 0;
+  for (int z = 0; z < Ez; ++z) {
+    float2 *P0 = m.pin + (z & 1) * pplane;
+    // centre values of plane z (and the periodic halo)
+#pragma unroll
+    for (int r = 0; r < PP; ++r) {
+      if (!valid[r]) continue;
+      const int x = px[r], y = py[r];
+      const int c = (y + 4) * pitch + x + 4;
+      if (v1[r]) *reinterpret_cast<float4 *>(P0 + c) = q[r][4];
+      else P0[c] = lo2(q[r][4]);
+      if (a.periodic) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !v1[r]) continue;
+          const int xx = x + h;
+          const float2 vv = h == 0 ? lo2(q[r][4]) : hi2(q[r][4]);
+          if (xx < 4) P0[c + h + Ex] = vv;
+          if (xx >= Ex - 4) P0[c + h - Ex] = vv;
+          if (y < 4) P0[c + h + Ey * pitch] = vv;
+          if (y >= Ey - 4) P0[c + h - Ey * pitch] = vv;
+        }
+      }
+    }
+    const int e0 = m.rb[z * Ey];
+    const int nez = m.rb[(z + 1) * Ey] - e0;
+    float4 *RC = m.rec + b3 * a.maxent;
+    pair_records<NT>(ent + e0, nez, pre, m.sk2, RC);
+    if (z + 1 < Ez) pair_prefetch<NT>(ent + m.rb[(z + 1) * Ey], m.rb[(z + 2) * Ey] - m.rb[(z + 1) * Ey], pre);
+    __syncthreads();
+    if (proj && z > 0) {
+      const int zp = z - 1;
+      const int bp = b3 == 0 ? 2 : b3 - 1;
+      pair_project<NT>(m.pout + (zp & 1) * Ey * pitch2, m.rec + bp * a.maxent,
+                       m.rb[(zp + 1) * Ey] - m.rb[zp * Ey], m, pitch2, A);
+    }
+
+    int zn = z + 5;
+    bool zin = zn < Ez;
+    if (!zin && a.periodic) {
+      zn -= Ez;
+      zin = true;
+    }
+    const long long zoff = (long long)zn * plane;
+    const long long o_here = (long long)z * plane;
+#pragma unroll
+    for (int r = 0; r < PP; ++r) {
+      if (!valid[r]) continue;
+      const int x = px[r], y = py[r];
+      const int t0 = y * Ex + x;
+      const float *pn = a.yin + base + zoff + t0;
+      const float4 nxt = make_float4(zin ? pn[0] : 0.f, zin ? pn[o1off] : 0.f, (zin && v1[r]) ? pn[1] : 0.f,
+                                     (zin && v1[r]) ? pn[o1off + 1] : 0.f);
+      const float va = fmaf(alpha, vf[o_here + t0], vsh);
+      const float vb = v1[r] ? fmaf(alpha, vf[o_here + t0 + 1], vsh) : 0.f;
+      float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (use_prev) {
+        const float *pp = a.yprev + base + o_here + t0;
+        pv = make_float4(pp[0], pp[o1off], v1[r] ? pp[1] : 0.f, v1[r] ? pp[o1off + 1] : 0.f);
+      }
+      const float2 *co = P0 + (y + 4) * pitch + x + 4;
+      float4 X[5];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) X[j] = *reinterpret_cast<const float4 *>(co - 4 + 2 * j);
+      // point m of the row (m = -4 .. 5 relative to x): X[(m + 4) / 2], low half for even m
+      float2 row[10];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        row[2 * j] = lo2(X[j]);
+        row[2 * j + 1] = hi2(X[j]);
+      }
+      float2 ym0[4], yp0[4], ym1[4], yp1[4], zm0[4], zp0[4], zm1[4], zp1[4], xm0[4], xp0[4], xm1[4], xp1[4];
+#pragma unroll
+      for (int n = 1; n <= 4; ++n) {
+        const float4 u = *reinterpret_cast<const float4 *>(co + n * pitch);
+        const float4 d = *reinterpret_cast<const float4 *>(co - n * pitch);
+        yp0[n - 1] = lo2(u);
+        yp1[n - 1] = hi2(u);
+        ym0[n - 1] = lo2(d);
+        ym1[n - 1] = hi2(d);
+        zp0[n - 1] = lo2(q[r][4 + n]);
+        zp1[n - 1] = hi2(q[r][4 + n]);
+        zm0[n - 1] = lo2(q[r][4 - n]);
+        zm1[n - 1] = hi2(q[r][4 - n]);
+        xp0[n - 1] = row[4 + n];
+        xm0[n - 1] = row[4 - n];
+        xp1[n - 1] = row[5 + n];
+        xm1[n - 1] = row[5 - n];
+      }
+      const float2 c0 = lo2(q[r][4]), c1 = hi2(q[r][4]);
+      float2 h0 = fma2(f2(va, va), c0, mul2(bb, lo2(pv)));
+      float2 h1 = fma2(f2(vb, vb), c1, mul2(bb, hi2(pv)));
+      h0 = lap_pair<ISO>(K, c0, xm0, xp0, ym0, yp0, zm0, zp0, h0);
+      h1 = lap_pair<ISO>(K, c1, xm1, xp1, ym1, yp1, zm1, zp1, h1);
+      // nonlocal term over the row's records
+      {
+        const int eb = m.rb[z * Ey + y] - e0, ee = m.rb[z * Ey + y + 1] - e0;
+        const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2 + x);
+        for (int e = eb; e < ee; ++e) {
+          const float4 rr = RC[e];
+          const int k = __float_as_int(rr.z) & 0xffff;
+          const float4 g = g4[(k * pitch2) >> 1];
+          const float2 u = lo2(rr);
+          h0 = fma2(u, lo2(g), h0);
+          h1 = fma2(u, hi2(g), h1);
+        }
+      }
+      float2 out0 = h0, out1 = h1;
+      if (a.mode == HSTEP_ADJ) {
+        dot = fma2(c0, h0, dot);
+        if (v1[r]) dot = fma2(c1, h1, dot);
+        out0 = mul2(occ2, h0);
+        out1 = mul2(occ2, h1);
+      }
+      if (a.yout) {
+        float *po = a.yout + base + o_here + t0;
+        po[0] = out0.x;
+        if (v1[r]) po[1] = out1.x;
+        if (nvalid > 1) {
+          po[P] = out0.y;
+          if (v1[r]) po[P + 1] = out1.y;
+        }
+      }
+      if (proj) {
+        float2 *pp = m.pout + (z & 1) * Ey * pitch2 + y * pitch2 + x;
+        *reinterpret_cast<float4 *>(pp) = make_float4(out0.x, out0.y, v1[r] ? out1.x : 0.f, v1[r] ? out1.y : 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) q[r][k] = q[r][k + 1];
+      q[r][8] = nxt;
+    }
+    b3 = b3 == 2 ? 0 : b3 + 1;
+  }
+  if (proj) {
+    __syncthreads();
+    const int zp = Ez - 1;
+    const int bp = b3 == 0 ? 2 : b3 - 1;
+    pair_project<NT>(m.pout + (zp & 1) * Ey * pitch2, m.rec + bp * a.maxent, m.rb[(zp + 1) * Ey] - m.rb[zp * Ey], m,
+                     pitch2, A);
+    __syncthreads();
+    pair_finish<NT>(a, D, m, i0, nvalid);
+  }
+  if (a.mode == HSTEP_ADJ) {
+    for (int o = 16; o > 0; o >>= 1) {
+      dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
+      dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) {
+      m.red[w] = dot.x;
+      m.red[NT / 32 + w] = dot.y;
+    }
+    __syncthreads();
+    if (threadIdx.x < nvalid) {
+      float s = 0.f;
+      for (int i = 0; i < NT / 32; ++i) s += m.red[threadIdx.x * (NT / 32) + i];
+      const int st = D.st_off + i0 + threadIdx.x;
+      a.dots[st] = a.occ[st] * a.dV * (double)s;
+    }
+  }
+}
+
+// Projections of an orbital block (no stencil), orbital pairs interleaved like k_hpair: plane z of
+// both orbitals is staged in shared memory while the row-list tasks of plane z-1 run.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_project_pair(HArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 fi = a.items[blockIdx.x];
+  const int f = fi.x, i0 = fi.y;
+  const FragDesc D = a.desc[f];
+  const int nvalid = min(2, D.norb - i0);
+  const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2];
+  const int plane = Ex * Ey;
+  const int pitch2 = (Ex + 1) & ~1;
+  const int A = D.natom;
+  const long long P = (long long)plane * Ez;
+  const PairSmem m = pair_carve(smem_raw, Ex, Ey, Ez, A, a.maxent, 2, false);
+  pair_setup<NT>(a, D, m, i0, nvalid, 1.f);
+  const long long base = D.psi_off + (long long)i0 * P;
+  const long long o1off = nvalid > 1 ? P : 0;
+  const int2 *ent = a.row_ent + a.row_beg[D.row_off];
+  const float *y0 = a.yin + base;
+  // sk2 is zero here (no input projections): only the (slot|row, weight) part of a record is used
+  __syncthreads();
+  int2 pre[2];
+  pair_prefetch<NT>(ent, m.rb[Ey], pre);
+  for (int z = 0; z < Ez; ++z) {
+    float2 *pl = m.pout + (z & 1) * Ey * pitch2;
+    for (int t = threadIdx.x; t < plane; t += NT) {
+      const int y = t / Ex, x = t - y * Ex;
+      const float *p = y0 + (long long)z * plane + t;
+      pl[y * pitch2 + x] = f2(p[0], p[o1off]);
+    }
+    const int e0 = m.rb[z * Ey];
+    pair_records<NT>(ent + e0, m.rb[(z + 1) * Ey] - e0, pre, m.sk2, m.rec + (z & 1) * a.maxent);
+    if (z + 1 < Ez) pair_prefetch<NT>(ent + m.rb[(z + 1) * Ey], m.rb[(z + 2) * Ey] - m.rb[(z + 1) * Ey], pre);
+    __syncthreads();
+    pair_project<NT>(pl, m.rec + (z & 1) * a.maxent, m.rb[(z + 1) * Ey] - e0, m, pitch2, A);
+  }
+  __syncthreads();
+  pair_finish<NT>(a, D, m, i0, nvalid);
+}
+
 template <typename T>
 const T *tab_of(dc_ctx *c);
 template <>
@@ -509,6 +1012,9 @@ HArgs<T> make_args(dc_ctx *c) {
   a.tab = tab_of<T>(c);
   a.zl_beg = c->d_zl_beg;
   a.zl_items = c->d_zl_items;
+  a.row_beg = c->d_row_beg;
+  a.row_ent = c->d_row_ent;
+  a.maxent = c->max_plane_ent;
   a.vf = vf_of<T>(c);
   a.Datom = c->d_atom_D;
   a.bounds = c->d_bounds;
@@ -569,36 +1075,106 @@ int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
   return DC_OK;
 }
 
-// Launch shapes of the stencil kernel: (threads per CTA, x-pairs per thread).
-constexpr int kShapes[][2] = {{128, 1}, {128, 2}, {256, 1}, {256, 2}, {512, 1}, {512, 2}, {512, 4}};
+// Launch shapes of the stencil kernels: kind 0 = x-adjacent point pairs of one orbital (NO orbitals
+// per CTA), kind 1 = orbital-pair kernel (FP32 only); threads per CTA; point pairs per thread.
+struct Shape {
+  int kind, nt, pp;
+};
+constexpr Shape kShapes[] = {{0, 128, 1}, {0, 128, 2}, {0, 256, 1}, {0, 256, 2}, {0, 512, 1},
+                             {0, 512, 2}, {0, 512, 4}, {1, 128, 1}, {1, 256, 1}, {1, 512, 1},
+                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+static_assert(kNumShapes <= DC_TUNE_SLOTS, "tuning slots");
 
-// FP32 runs two orbitals per thread; FP64 one (its pairs of doubles would not fit in registers twice)
+size_t hpair_smem(const dc_ctx *c, int NT) {
+  return pair_smem_bytes(c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms, std::max(1, c->max_plane_ent), 3,
+                         true, NT);
+}
+size_t project_pair_smem(const dc_ctx *c) {
+  return pair_smem_bytes(c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms, std::max(1, c->max_plane_ent), 2,
+                         false, 256);
+}
+
+// The three axes share one set of coefficients when their FP32 values agree (cubic spacing).
+bool iso_coeffs(const HArgs<float> &a) {
+  for (int n = 1; n < 5; ++n)
+    if (a.kx[n] != a.ky[n] || a.kx[n] != a.kz[n]) return false;
+  return true;
+}
+
+template <int NT, int PP>
+int run_hpair(dc_ctx *c, HArgs<float> a, cudaStream_t s) {
+  const size_t sm = hpair_smem(c, NT);
+  if (sm > 227 * 1024) {
+    dc_set_error("hpsi: fragment tables exceed shared memory (orbital-pair kernel)");
+    return DC_ERR_ARG;
+  }
+  a.items = c->d_items2;
+  a.maxent = std::max(1, c->max_plane_ent);
+  if (iso_coeffs(a)) {
+    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, true>, sm));
+    k_hpair<NT, PP, true><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
+  } else {
+    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, false>, sm));
+    k_hpair<NT, PP, false><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
+  }
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+// FP32 row-pair kernels run two orbitals per CTA; FP64 one (its pairs of doubles would not fit in
+// registers twice).  The orbital-pair kernel exists for FP32 only.
 template <typename T>
-int run_shape(dc_ctx *c, int shape, HArgs<T> a, cudaStream_t s) {
-  constexpr int NO = sizeof(T) == 4 ? 2 : 1;
+int run_shape(dc_ctx *c, int shape, HArgs<T> a, cudaStream_t s);
+template <>
+int run_shape<double>(dc_ctx *c, int shape, HArgs<double> a, cudaStream_t s) {
   switch (shape) {
-    case 0: return run_hstep<T, 128, 1, NO>(c, a, s);
-    case 1: return run_hstep<T, 128, 2, NO>(c, a, s);
-    case 2: return run_hstep<T, 256, 1, NO>(c, a, s);
-    case 3: return run_hstep<T, 256, 2, NO>(c, a, s);
-    case 4: return run_hstep<T, 512, 1, NO>(c, a, s);
-    case 5: return run_hstep<T, 512, 2, NO>(c, a, s);
-    default: return run_hstep<T, 512, 4, NO>(c, a, s);
+    case 0: return run_hstep<double, 128, 1, 1>(c, a, s);
+    case 1: return run_hstep<double, 128, 2, 1>(c, a, s);
+    case 2: return run_hstep<double, 256, 1, 1>(c, a, s);
+    case 3: return run_hstep<double, 256, 2, 1>(c, a, s);
+    case 4: return run_hstep<double, 512, 1, 1>(c, a, s);
+    case 5: return run_hstep<double, 512, 2, 1>(c, a, s);
+    case 6: return run_hstep<double, 512, 4, 1>(c, a, s);
+    default: dc_set_error("hpsi: no such FP64 launch shape"); return DC_ERR_ARG;
+  }
+}
+template <>
+int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
+  switch (shape) {
+    case 0: return run_hstep<float, 128, 1, 2>(c, a, s);
+    case 1: return run_hstep<float, 128, 2, 2>(c, a, s);
+    case 2: return run_hstep<float, 256, 1, 2>(c, a, s);
+    case 3: return run_hstep<float, 256, 2, 2>(c, a, s);
+    case 4: return run_hstep<float, 512, 1, 2>(c, a, s);
+    case 5: return run_hstep<float, 512, 2, 2>(c, a, s);
+    case 6: return run_hstep<float, 512, 4, 2>(c, a, s);
+    case 7: return run_hpair<128, 1>(c, a, s);
+    case 8: return run_hpair<256, 1>(c, a, s);
+    case 9: return run_hpair<512, 1>(c, a, s);
+    case 10: return run_hpair<1024, 1>(c, a, s);
+    case 11: return run_hpair<256, 2>(c, a, s);
+    default: return run_hpair<512, 2>(c, a, s);
   }
 }
 
-// A shape is valid when one CTA covers every x-pair of the largest plane, and useful when it does
-// not leave more than three quarters of its threads idle.
-bool shape_ok(const dc_ctx *c, int shape) {
+// A shape is valid when one CTA covers every x-pair of the largest plane and its shared memory
+// fits, and useful when it does not leave more than three quarters of its threads idle.
+bool shape_ok(const dc_ctx *c, int shape, size_t esz) {
+  if (shape < 0 || shape >= kNumShapes) return false;
+  const Shape S = kShapes[shape];
+  if (S.kind == 1 && (esz != sizeof(float) || hpair_smem(c, S.nt) > 227 * 1024)) return false;
   const int pairs = ((c->max_E[0] + 1) / 2) * c->max_E[1];
-  const int cover = kShapes[shape][0] * kShapes[shape][1];
-  return cover >= pairs && (cover <= 4 * pairs || kShapes[shape][0] == 128);
+  const int cover = S.nt * S.pp;
+  return cover >= pairs && (cover <= 4 * pairs || S.nt == 128);
 }
 
-int default_shape(const dc_ctx *c) {
+int default_shape(const dc_ctx *c, size_t esz) {
+  if (esz == sizeof(float))
+    for (int k : {7, 8, 11, 9, 12, 10})
+      if (shape_ok(c, k, esz)) return k;
   for (int k : {0, 2, 3, 5, 6})
-    if (shape_ok(c, k)) return k;
+    if (shape_ok(c, k, esz)) return k;
   return 6;
 }
 
@@ -622,7 +1198,7 @@ int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T 
   a.occ = occ;
   a.dots = dots;
   int shape = c->hstep_shape[sizeof(T) == 8 ? 1 : 0];
-  if (shape < 0 || !shape_ok(c, shape)) shape = default_shape(c);
+  if (!shape_ok(c, shape, sizeof(T))) shape = default_shape(c, sizeof(T));
   return run_shape<T>(c, shape, a, s);
 }
 
@@ -639,10 +1215,10 @@ int tune_hstep(dc_ctx *c, const T *y, T *out, T *cbuf, cudaStream_t s) {
   DC_CUDA(cudaEventCreate(&e0));
   DC_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_shape = default_shape(c);
+  int best_shape = default_shape(c, sizeof(T));
   int st = DC_OK;
   for (int k = 0; k < kNumShapes && st == DC_OK; ++k) {
-    if (!shape_ok(c, k)) continue;
+    if (!shape_ok(c, k, sizeof(T))) continue;
     st = run_shape<T>(c, k, a, s);  // warm-up and attribute set
     float tk = 1e30f;
     for (int r = 0; r < 3 && st == DC_OK; ++r) {
@@ -667,10 +1243,18 @@ int tune_hstep(dc_ctx *c, const T *y, T *out, T *cbuf, cudaStream_t s) {
   return DC_OK;
 }
 
-int hstep_shape_info(int shape, int *threads, int *pairs) {
+int hstep_shape_find(const dc_ctx *c, size_t esz, int kind, int threads, int pairs) {
+  for (int k = 0; k < kNumShapes; ++k)
+    if (kShapes[k].kind == kind && kShapes[k].nt == threads && kShapes[k].pp == pairs)
+      return shape_ok(c, k, esz) ? k : -1;
+  return -1;
+}
+
+int hstep_shape_info(int shape, int *kind, int *threads, int *pairs) {
   if (shape < 0 || shape >= kNumShapes) return DC_ERR_ARG;
-  *threads = kShapes[shape][0];
-  *pairs = kShapes[shape][1];
+  *kind = kShapes[shape].kind;
+  *threads = kShapes[shape].nt;
+  *pairs = kShapes[shape].pp;
   return DC_OK;
 }
 
@@ -679,6 +1263,17 @@ int launch_project(dc_ctx *c, const T *psi, T *cout, cudaStream_t s) {
   HArgs<T> a = make_args<T>(c);
   a.yin = psi;
   a.cout = cout;
+  if constexpr (std::is_same<T, float>::value) {
+    if (project_pair_smem(c) <= 227 * 1024) {
+      a.items = c->d_items2;
+      a.maxent = std::max(1, c->max_plane_ent);
+      const size_t sm = project_pair_smem(c);
+      DC_CUDA(dc_set_smem((const void *)k_project_pair<256>, sm));
+      k_project_pair<256><<<(unsigned)c->n_items2, 256, sm, s>>>(a);
+      DC_CUDA(cudaGetLastError());
+      return DC_OK;
+    }
+  }
   const size_t sm = project_smem(c, sizeof(T));
   DC_CUDA(dc_set_smem((const void *)k_project<T, 256>, sm));
   k_project<T, 256><<<(unsigned)c->layout.nstates, 256, sm, s>>>(a);

@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <stdexcept>
 
 #include "dc_internal.h"
@@ -176,8 +177,11 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   std::vector<ProjSlot> slots;
   std::vector<double> tab;
   std::vector<int> zl_beg, zl_items;
+  std::vector<int> row_beg;
+  std::vector<int2> row_ent;
   c->max_atoms = 0;
   c->max_zlist = 0;
+  c->max_plane_ent = 0;
   for (int d = 0; d < 3; ++d) c->max_E[d] = 0;
   int max_norb = 0;
   for (int f = 0; f < c->nfrag; ++f) {
@@ -249,6 +253,35 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
     }
     zl_beg.push_back((int)zl_items.size());
     c->max_zlist = std::max(c->max_zlist, total);
+    // Row lists of the orbital-pair stencil kernel: for every row (z, y), in z-list order, the slots
+    // whose FP32 product gz(z) gy(y) is non-zero, as (k | y << 16, bits of that product).
+    {
+      const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2], tw = tab_width(D);
+      const int zl0 = (int)zl_beg.size() - (Ez + 1);
+      D.row_off = (int)row_beg.size();
+      for (int z = 0; z < Ez; ++z) {
+        const size_t plane_start = row_ent.size();
+        for (int y = 0; y < Ey; ++y) {
+          row_beg.push_back((int)row_ent.size());
+          for (int e = zl_beg[zl0 + z]; e < zl_beg[zl0 + z + 1]; ++e) {
+            const int k = zl_items[e];
+            const double *g = &tab[tab_off + (long long)k * tw];
+            const float w = (float)g[Ex + Ey + z] * (float)g[Ex + y];
+            if (w != 0.f) {
+              int wb;
+              std::memcpy(&wb, &w, sizeof(int));
+              row_ent.push_back(make_int2(k | (y << 16), wb));
+            }
+          }
+        }
+        c->max_plane_ent = std::max(c->max_plane_ent, (int)(row_ent.size() - plane_start));
+      }
+      row_beg.push_back((int)row_ent.size());
+      if (row_ent.size() > (size_t)INT32_MAX / 2) {
+        dc_set_error("dc_init: projector row lists too long");
+        return DC_ERR_ARG;
+      }
+    }
     zl_off += D.E[2] + 1;
     D.c_off = c_off;
     psi_off += (long long)D.norb * P;
@@ -302,6 +335,8 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   out.tab.swap(tab);
   out.zl_beg.swap(zl_beg);
   out.zl_items.swap(zl_items);
+  out.row_beg.swap(row_beg);
+  out.row_ent.swap(row_ent);
   return DC_OK;
 }
 

@@ -24,6 +24,7 @@ def main():
     p.add_argument("--dtype", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--reps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--all-shapes", action="store_true", help="one line per launch shape that fits")
     args = p.parse_args()
 
     import numpy as np
@@ -43,22 +44,29 @@ def main():
     psi = torch.tensor(g.standard_normal(s.layout.psi_elems), dtype=dt, device="cuda")
     out = torch.empty_like(psi)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
-    for _ in range(args.warmup):
-        s.hpsi(psi, out)
-    torch.cuda.synchronize()
-    s.profile(True)
-    for _ in range(args.reps):
-        flush.fill_(1.0)
-        s.hpsi(psi, out)
-    torch.cuda.synchronize()
-    prof = s.profile_read()
-    s.profile(False)
-    h, pj = prof["hpsi"], prof["project"]
-    res = dict(workload=args.workload, dtype=args.dtype, reps=args.reps,
-               point_orbitals=int(s.layout.psi_elems), hpsi_ms=h["ms"] / args.reps,
-               hpsi_gbs=h["bytes"] / (h["ms"] * 1e-3) / 1e9, project_ms=pj["ms"] / args.reps,
-               total_gbs=(h["bytes"] + pj["bytes"]) / ((h["ms"] + pj["ms"]) * 1e-3) / 1e9)
-    print(json.dumps(res), flush=True)
+    shapes = [None]
+    if args.all_shapes:
+        shapes = [(0, 128, 1), (0, 128, 2), (0, 256, 1), (0, 256, 2), (0, 512, 1), (0, 512, 2), (0, 512, 4),
+                  (1, 128, 1), (1, 256, 1), (1, 512, 1), (1, 1024, 1), (1, 256, 2), (1, 512, 2)]
+    for shape in shapes:
+        if shape is not None and not s.set_tuning(args.dtype, *shape):
+            continue
+        for _ in range(args.warmup):
+            s.hpsi(psi, out)
+        torch.cuda.synchronize()
+        s.profile(True)
+        for _ in range(args.reps):
+            flush.fill_(1.0)
+            s.hpsi(psi, out)
+        torch.cuda.synchronize()
+        prof = s.profile_read()
+        s.profile(False)
+        h, pj = prof["hpsi"], prof["project"]
+        res = dict(workload=args.workload, dtype=args.dtype, reps=args.reps, shape=shape,
+                   point_orbitals=int(s.layout.psi_elems), hpsi_ms=h["ms"] / args.reps,
+                   hpsi_gbs=h["bytes"] / (h["ms"] * 1e-3) / 1e9, project_ms=pj["ms"] / args.reps,
+                   total_gbs=(h["bytes"] + pj["bytes"]) / ((h["ms"] + pj["ms"]) * 1e-3) / 1e9)
+        print(json.dumps(res), flush=True)
     s.close()
 
 

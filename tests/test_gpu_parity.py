@@ -105,24 +105,53 @@ def test_starting_orbitals_bit_exact():
     assert np.array_equal(got, pack(st, st.psi))
 
 
-@pytest.mark.parametrize("case", list(CASES))
-@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
-def test_hpsi(case, dtype):
+def _hpsi_against_oracle(case, dtype, shapes=(None,)):
+    """H psi of a seeded random block under each launch shape (None = default), against the oracle."""
     cfg = CASES[case](precision=dtype)
     st = oracle_state(cfg)
     V = _synthetic_potential(st.grid, seed=17)
     r = np.random.default_rng(11)
+    tol = 1e-12 if dtype == "fp64" else 2e-6
+    ran = []
     with _solver(cfg) as s:
         s.set_potential(torch.tensor(V.reshape(-1), dtype=torch.float64, device="cuda"))
         x = r.standard_normal(s.layout.psi_elems)
         tdt = torch.float64 if dtype == "fp64" else torch.float32
         psi = torch.tensor(x, dtype=tdt, device="cuda")
-        out = _np(s.hpsi(psi))
         xin = _np(psi).astype(np.float64)
-    blocks = unpack(st, xin)
-    ref = pack(st, {f: st.hamiltonian(f, V).apply(blocks[f]) for f in range(st.frags.nfrag)})
-    tol = 1e-12 if dtype == "fp64" else 2e-6
-    assert np.max(np.abs(out - ref)) <= tol * np.max(np.abs(ref))
+        blocks = unpack(st, xin)
+        ref = pack(st, {f: st.hamiltonian(f, V).apply(blocks[f]) for f in range(st.frags.nfrag)})
+        for shape in shapes:
+            if shape is not None and not s.set_tuning(dtype, *shape):
+                continue
+            out = _np(s.hpsi(psi))
+            err = np.max(np.abs(out - ref)) / np.max(np.abs(ref))
+            assert err <= tol, (shape, err)
+            ran.append(shape)
+    return ran
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_hpsi(case, dtype):
+    _hpsi_against_oracle(case, dtype)
+
+
+# (kind, threads per CTA, point pairs per thread) of the stencil kernels
+SHAPES = [(0, 128, 1), (0, 128, 2), (0, 256, 1), (0, 256, 2), (0, 512, 1), (0, 512, 2), (0, 512, 4),
+          (1, 128, 1), (1, 256, 1), (1, 512, 1), (1, 1024, 1), (1, 256, 2), (1, 512, 2)]
+
+
+@pytest.mark.parametrize("case", ["si8", "uneven", "periodic", "wide", "water_auto"])
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_hpsi_every_launch_shape(case, dtype):
+    """Every launch shape that fits the case (both kernel kinds in FP32) gives the oracle's H psi."""
+    ran = _hpsi_against_oracle(case, dtype, SHAPES)
+    assert any(k == 0 for k, _, _ in ran)
+    if dtype == "fp32":
+        assert any(k == 1 for k, _, _ in ran)
+    else:
+        assert all(k == 0 for k, _, _ in ran)
 
 
 @pytest.mark.parametrize("case", ["si8", "periodic", "uneven", "water_auto"])
@@ -145,6 +174,27 @@ def test_subspace_and_one_chefsi_pass_fp64(case):
         e1 = _np(e1)
     assert np.max(np.abs(e0 - eps_rr)) < 1e-10 * max(1.0, np.max(np.abs(eps_rr)))
     assert np.max(np.abs(e1 - eps_1)) < 1e-9 * max(1.0, np.max(np.abs(eps_1)))
+
+
+@pytest.mark.parametrize("case", ["periodic", "uneven", "water_auto"])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_subspace_and_one_chefsi_pass_fp32(case, kind):
+    """FP32 filter steps (with their in-kernel projections) under both stencil kernel kinds."""
+    cfg = CASES[case](precision="fp32")
+    st = oracle_state(cfg)
+    V = st.veff(st.rho_in)
+    st.initial_rr(V)
+    st.solve(V, 1)
+    eps_1 = pack(st, st.eps)
+    with _solver(cfg) as s:
+        shape = next(sh for sh in SHAPES if sh[0] == kind and s.set_tuning("fp32", *sh))
+        _, rho0 = s.initial()
+        s.potential(rho0)
+        s.subspace()
+        s.chefsi(1)
+        _, e1 = s.get_state()
+        e1 = _np(e1)
+    assert np.max(np.abs(e1 - eps_1)) < 2e-5 * max(1.0, np.max(np.abs(eps_1))), shape
 
 
 @pytest.fixture(scope="module")
