@@ -496,7 +496,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
     // chunks are added in FP64; DC_GRAM_CHUNK overrides (multiple of 64, 64..65536).  Tensor-memory
     // FP32 accumulation carries an error that grows linearly with the chunk length (measured on
     // B300), so the mixed path uses short chunks.
-    c->gram_chunk = c->params.precision == DC_MIXED ? 256 : 2048;
+    c->gram_chunk = 2048;
     if (const char *gc = getenv("DC_GRAM_CHUNK")) {
       const int v = atoi(gc);
       if (v >= 64 && v <= 65536 && v % 64 == 0) c->gram_chunk = v;

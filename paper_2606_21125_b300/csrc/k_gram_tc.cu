@@ -6,22 +6,28 @@
 // FP32 accuracy are accumulated in FP32 in tensor memory:
 //   S = hh + hm + mh + hl + lh + mm            (lh = (hl)^T by symmetry)
 //   A = h.zh + h.zm + m.zh + h.zl + l.zh + m.zm (z = HY split the same way)
-// One CTA (4 warps) handles one (fragment, 2048-point chunk).  Per 64-point K-tile the CTA splits
-// Y and HY into BF16 rows in shared memory (K-major, no-swizzle canonical layout), and one thread
-// issues three MMAs per 16-point K-step:
+// Persistent CTAs (one per SM, 8 warps) walk the (fragment, 2048-point item) list.  Per 64-point
+// K-tile the CTA splits Y and HY into BF16 rows in shared memory (K-major, no-swizzle canonical
+// layout), and one thread issues three MMAs per 16-point K-step:
 //   D_S[128 x 3nb] = [Yh;Ym;Yl..] x [Yh|Ym|Yl]^T,  D_A[128 x 3nb] = [Yh;Ym;..] x [Zh|Zm|Zl]^T,
 //   D_L[128 x nb]  = [Yl;0] x [Zh]^T                                   (nb = n rounded up to 16)
-// with two K-tile stages in flight (mbarrier per stage).  The chunk's partial S and A leave in FP64
-// and the FP64 subspace kernel adds the chunks in a fixed order.  Every wait is bounded; on a
-// timeout the kernel sets DC_FLAG_TIMEOUT, frees its tensor memory and returns.
+// with two K-tile stages in flight (mbarrier per stage) and the FP32 tiles of the next two K-tiles
+// already loading into registers (16-byte loads).  The FP32 accumulators in tensor memory are
+// drained every 256 points into FP32 sums in shared memory (the rounding of a tensor-memory sum
+// grows with its length), and each item leaves as one FP64 partial of S and A that the FP64
+// subspace kernel adds in a fixed order.  Every wait is bounded; on a timeout the kernel sets
+// DC_FLAG_TIMEOUT, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "dc_internal.h"
 
 namespace {
 
 constexpr int TKT = 64;   // points per K-tile
-constexpr int TNT = 128;  // threads per CTA
+constexpr int TNT = 256;  // threads per CTA
+constexpr int TDR = 4;    // K-tiles per tensor-memory drain (256 points)
 constexpr int TMEM_COLS = 512;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -80,31 +86,134 @@ __device__ __forceinline__ void split3(float y, __nv_bfloat16 &h, __nv_bfloat16 
   l = __float2bfloat16_rn(r2);
 }
 
-__global__ void __launch_bounds__(TNT) k_gram_tc(const FragDesc *desc, const int2 *gitems, const long long *goff,
-                                                 int chunk, const float *Y, const float *HY, double *out,
-                                                 unsigned *flags) {
+// Loads of one K-tile: rows i < n, points pb..pb+63, as 16 float4 per row (slots idx = tid + j*TNT).
+__device__ __forceinline__ float4 ld4g(const float *row, long long p, long long p1, bool vec) {
+  if (vec && p + 3 < p1) return *reinterpret_cast<const float4 *>(row + p);
+  float4 v;
+  v.x = p < p1 ? row[p] : 0.f;
+  v.y = p + 1 < p1 ? row[p + 1] : 0.f;
+  v.z = p + 2 < p1 ? row[p + 2] : 0.f;
+  v.w = p + 3 < p1 ? row[p + 3] : 0.f;
+  return v;
+}
+
+constexpr int TSL = 4;  // float4 slots per thread per array: 64 rows x 16 float4 / 256 threads
+
+struct TileRegs {
+  float4 y[TSL], z[TSL];
+};
+
+__device__ __forceinline__ void load_tile(TileRegs &r, const float *Yf, const float *Zf, long long P, int n,
+                                          long long pb, long long p1, bool vec) {
+#pragma unroll
+  for (int j = 0; j < TSL; ++j) {
+    const int idx = threadIdx.x + j * TNT;
+    if (idx < n * 16) {
+      const int i = idx >> 4;
+      const long long p = pb + 4 * (idx & 15);
+      r.y[j] = ld4g(Yf + (long long)i * P, p, p1, vec);
+      r.z[j] = ld4g(Zf + (long long)i * P, p, p1, vec);
+    }
+  }
+}
+
+__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d) {
+  const __nv_bfloat162 lo = __halves2bfloat162(a, b), hi = __halves2bfloat162(c, d);
+  return make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
+}
+
+// Split 4 consecutive-point values of row i into h/m/l rows (base row offsets 0, nb, 2 nb).
+__device__ __forceinline__ void store_split(unsigned char *st, int i, int k, int ks, int nb, float4 v) {
+  __nv_bfloat16 h[4], m[4], l[4];
+  split3(v.x, h[0], m[0], l[0]);
+  split3(v.y, h[1], m[1], l[1]);
+  split3(v.z, h[2], m[2], l[2]);
+  split3(v.w, h[3], m[3], l[3]);
+  *reinterpret_cast<uint2 *>(st + toff(i, k, ks)) = pack4(h[0], h[1], h[2], h[3]);
+  *reinterpret_cast<uint2 *>(st + toff(nb + i, k, ks)) = pack4(m[0], m[1], m[2], m[3]);
+  *reinterpret_cast<uint2 *>(st + toff(2 * nb + i, k, ks)) = pack4(l[0], l[1], l[2], l[3]);
+}
+
+__device__ __forceinline__ void convert_tile(const TileRegs &r, unsigned char *ys, unsigned char *zs, int n, int nb,
+                                             int ksY, int ksZ) {
+#pragma unroll
+  for (int j = 0; j < TSL; ++j) {
+    const int idx = threadIdx.x + j * TNT;
+    if (idx < n * 16) {
+      const int i = idx >> 4, k = 4 * (idx & 15);
+      store_split(ys, i, k, ksY, nb, r.y[j]);
+      store_split(zs, i, k, ksZ, nb, r.z[j]);
+    }
+  }
+}
+
+struct GramPipe {
+  uint32_t phase[2];
+  int commits[2], waits[2];
+};
+
+// Wait until every committed MMA group has completed.
+__device__ __forceinline__ bool wait_all(GramPipe &g, uint64_t *mbar) {
+  bool ok = true;
+  for (int s = 0; s < 2; ++s) {
+    while (g.commits[s] > g.waits[s]) {
+      if (!mbar_wait(&mbar[s], g.phase[s])) ok = false;
+      g.phase[s] ^= 1u;
+      ++g.waits[s];
+    }
+  }
+  return ok;
+}
+
+// Adds the tensor-memory accumulators into the FP32 sums: rows r < n (h rows) give
+// P1S += hh + hm + hl, HL += hl, P1A += h.zh + h.zm + h.zl + l.zh; rows nb <= r < nb + n (m rows)
+// give P2S += mh + mm, P2A += m.zh + m.zm.  Warp w reads lanes 32 (w % 4) .. +31, warps 0-3 the
+// even 8-column groups and warps 4-7 the odd ones.
+__device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int n, int nb, float *acc) {
+  float *P1S = acc, *HL = acc + n * n, *P1A = HL + n * n, *P2S = P1A + n * n, *P2A = P2S + n * n;
+  const int warp = threadIdx.x >> 5;
+  const int r = 32 * (warp & 3) + (threadIdx.x & 31);
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const bool own = r < n, mrow = (r >= nb && r < nb + n);
+  const int i = own ? r : r - nb;
+  for (int cg = 8 * (warp >> 2); cg < nb; cg += 16) {
+    float sh[8], sm_[8], sl[8], ah[8], am[8], al[8], ll[8];
+    tmem_ld8(tS + lane_base + cg, sh);
+    tmem_ld8(tS + lane_base + nb + cg, sm_);
+    tmem_ld8(tS + lane_base + 2 * nb + cg, sl);
+    tmem_ld8(tA + lane_base + cg, ah);
+    tmem_ld8(tA + lane_base + nb + cg, am);
+    tmem_ld8(tA + lane_base + 2 * nb + cg, al);
+    tmem_ld8(tL + lane_base + cg, ll);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = cg + e;
+      if (j < n) {
+        if (own) {
+          P1S[i * n + j] += sh[e] + sm_[e] + sl[e];
+          HL[i * n + j] += sl[e];
+          P1A[i * n + j] += ah[e] + am[e] + al[e] + ll[e];
+        } else if (mrow) {
+          P2S[i * n + j] += sh[e] + sm_[e];
+          P2A[i * n + j] += ah[e] + am[e];
+        }
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const int2 *gitems, int n_items,
+                                                    const long long *goff, int chunk, int nmax, const float *Y,
+                                                    const float *HY, double *out, unsigned *flags) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tslot;
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ int timed_out;
   const int tid = threadIdx.x;
-  const int2 it = gitems[blockIdx.x];
-  const int f = it.x, ch = it.y;
-  const FragDesc D = desc[f];
-  const int n = D.norb;
-  const int nb = (n + 15) & ~15;
-  const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
-  const long long p0 = (long long)ch * chunk;
-  const long long p1 = min(P, p0 + chunk);
-  const int Ry = 2 * nb + 128, Rz = 3 * nb;
-  const int ksY = (Ry / 8) * 128, ksZ = (Rz / 8) * 128;  // K-direction strides (8 K-columns apart)
-  const int ybytes = Ry * TKT * 2, zbytes = Rz * TKT * 2;
-  const int stage_bytes = ybytes + zbytes;
-  const float *Yf = Y + D.psi_off;
-  const float *Zf = HY + D.psi_off;
+  const int nbmax = (nmax + 15) & ~15;
+  const int stage_max = (2 * nbmax + 128) * TKT * 2 + 3 * nbmax * TKT * 2;
+  float *acc = reinterpret_cast<float *>(sm + 2 * stage_max);  // [5][n][n]
 
-  // zero both stages: padding rows stay zero for the whole kernel
-  for (int t = tid; t < 2 * stage_bytes / 16; t += TNT) reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
                  "r"(TMEM_COLS));
@@ -120,121 +229,106 @@ __global__ void __launch_bounds__(TNT) k_gram_tc(const FragDesc *desc, const int
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tslot;
-  const uint32_t tS = tbase, tA = tbase + 3 * nb, tL = tbase + 6 * nb;
-  const uint32_t iS = idesc_bf16(128, 3 * nb), iL = idesc_bf16(128, nb);
+  GramPipe g{{0u, 0u}, {0, 0}, {0, 0}};
+  int gt = 0;         // K-tiles issued by this CTA (selects the stage)
+  int prev_n = -1;
 
-  const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
-  uint32_t phase[2] = {0u, 0u};
-  int commits[2] = {0, 0}, waits[2] = {0, 0};
-  for (int t = 0; t < ntiles; ++t) {
-    const int s = t & 1;
-    if (commits[s] > waits[s]) {
-      if (!mbar_wait(&mbar[s], phase[s])) timed_out = 1;
-      phase[s] ^= 1u;
-      ++waits[s];
+  for (int item = blockIdx.x; item < n_items && !timed_out; item += gridDim.x) {
+    const int2 it = gitems[item];
+    const int f = it.x, ch = it.y;
+    const FragDesc D = desc[f];
+    const int n = D.norb;
+    const int nb = (n + 15) & ~15;
+    const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
+    const long long p0 = (long long)ch * chunk;
+    const long long p1 = min(P, p0 + chunk);
+    const int Ry = 2 * nb + 128, Rz = 3 * nb;
+    const int ksY = (Ry / 8) * 128, ksZ = (Rz / 8) * 128;
+    const int ybytes = Ry * TKT * 2, zbytes = Rz * TKT * 2;
+    const int stage_bytes = ybytes + zbytes;
+    const float *Yf = Y + D.psi_off;
+    const float *Zf = HY + D.psi_off;
+    const bool vec = ((P | D.psi_off) & 3) == 0;
+    const uint32_t tS = tbase, tA = tbase + 3 * nb, tL = tbase + 6 * nb;
+    const uint32_t iS = idesc_bf16(128, 3 * nb), iL = idesc_bf16(128, nb);
+
+    // stage padding rows must be zero for this orbital count (no MMA is in flight here)
+    if (n != prev_n) {
+      for (int t = tid; t < 2 * stage_bytes / 16; t += TNT) reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
+      prev_n = n;
     }
+    for (int t = tid; t < 5 * n * n; t += TNT) acc[t] = 0.f;
+    const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
+    TileRegs ra, rb;
+    load_tile(ra, Yf, Zf, P, n, p0, p1, vec);
+    if (ntiles > 1) load_tile(rb, Yf, Zf, P, n, p0 + TKT, p1, vec);
     __syncthreads();
-    if (timed_out) break;
-    unsigned char *ys = sm + s * stage_bytes;
-    unsigned char *zs = ys + ybytes;
-    const long long pb = p0 + (long long)t * TKT;
-    for (int idx = tid; idx < n * (TKT / 2); idx += TNT) {
-      const int i = idx / (TKT / 2);
-      const int k = 2 * (idx - i * (TKT / 2));
-      const long long p = pb + k;
-      const float y0 = p < p1 ? Yf[(long long)i * P + p] : 0.f;
-      const float y1 = p + 1 < p1 ? Yf[(long long)i * P + p + 1] : 0.f;
-      const float z0 = p < p1 ? Zf[(long long)i * P + p] : 0.f;
-      const float z1 = p + 1 < p1 ? Zf[(long long)i * P + p + 1] : 0.f;
-      __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-      split3(y0, h0, m0, l0);
-      split3(y1, h1, m1, l1);
-      *reinterpret_cast<__nv_bfloat162 *>(ys + toff(i, k, ksY)) = __halves2bfloat162(h0, h1);
-      *reinterpret_cast<__nv_bfloat162 *>(ys + toff(nb + i, k, ksY)) = __halves2bfloat162(m0, m1);
-      *reinterpret_cast<__nv_bfloat162 *>(ys + toff(2 * nb + i, k, ksY)) = __halves2bfloat162(l0, l1);
-      split3(z0, h0, m0, l0);
-      split3(z1, h1, m1, l1);
-      *reinterpret_cast<__nv_bfloat162 *>(zs + toff(i, k, ksZ)) = __halves2bfloat162(h0, h1);
-      *reinterpret_cast<__nv_bfloat162 *>(zs + toff(nb + i, k, ksZ)) = __halves2bfloat162(m0, m1);
-      *reinterpret_cast<__nv_bfloat162 *>(zs + toff(2 * nb + i, k, ksZ)) = __halves2bfloat162(l0, l1);
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      const uint32_t ya = su32(ys), za = su32(zs);
-#pragma unroll
-      for (int kk = 0; kk < TKT / 16; ++kk) {
-        const uint32_t acc = (t > 0 || kk > 0) ? 1u : 0u;
-        const uint64_t aY = sdesc(ya + kk * 2 * ksY, ksY, 128);
-        const uint64_t aL = sdesc(ya + kk * 2 * ksY + (2 * nb / 8) * 128, ksY, 128);
-        const uint64_t bZ = sdesc(za + kk * 2 * ksZ, ksZ, 128);
-        mma_bf16(tS, aY, aY, iS, acc);
-        mma_bf16(tA, aY, bZ, iS, acc);
-        mma_bf16(tL, aL, bZ, iL, acc);
+
+    for (int t = 0; t < ntiles; ++t) {
+      const int s = gt & 1;
+      if (g.commits[s] > g.waits[s]) {
+        if (!mbar_wait(&mbar[s], g.phase[s])) timed_out = 1;
+        g.phase[s] ^= 1u;
+        ++g.waits[s];
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(&mbar[s])));
-    }
-    ++commits[s];
-  }
-  // drain
-  for (int s = 0; s < 2; ++s) {
-    while (commits[s] > waits[s]) {
-      if (!mbar_wait(&mbar[s], phase[s])) timed_out = 1;
-      phase[s] ^= 1u;
-      ++waits[s];
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (!timed_out) {
-    // partial sums from each thread's own accumulator row (row = tid)
-    float *P1S = reinterpret_cast<float *>(sm);  // [n][n] hh + hm + hl
-    float *HL = P1S + n * n;                     // [n][n] hl
-    float *P1A = HL + n * n;                     // [n][n] h.zh + h.zm + h.zl + l.zh
-    float *P2S = P1A + n * n;                    // [n][n] mh + mm
-    float *P2A = P2S + n * n;                    // [n][n] m.zh + m.zm
-    const int warp = tid >> 5;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const int r = tid;
-    const bool own = r < n, mrow = (r >= nb && r < nb + n);
-    const int i = own ? r : r - nb;
-    for (int cg = 0; cg < nb; cg += 8) {
-      float sh[8], sm_[8], sl[8], ah[8], am[8], al[8], ll[8];
-      tmem_ld8(tS + lane_base + cg, sh);
-      tmem_ld8(tS + lane_base + nb + cg, sm_);
-      tmem_ld8(tS + lane_base + 2 * nb + cg, sl);
-      tmem_ld8(tA + lane_base + cg, ah);
-      tmem_ld8(tA + lane_base + nb + cg, am);
-      tmem_ld8(tA + lane_base + 2 * nb + cg, al);
-      tmem_ld8(tL + lane_base + cg, ll);
+      __syncthreads();
+      if (timed_out) break;
+      unsigned char *ys = sm + s * stage_bytes;
+      unsigned char *zs = ys + ybytes;
+      // the registers of tile t hold ra (even t) or rb (odd t); refill them with tile t + 2
+      if ((t & 1) == 0) {
+        convert_tile(ra, ys, zs, n, nb, ksY, ksZ);
+        if (t + 2 < ntiles) load_tile(ra, Yf, Zf, P, n, p0 + (long long)(t + 2) * TKT, p1, vec);
+      } else {
+        convert_tile(rb, ys, zs, n, nb, ksY, ksZ);
+        if (t + 2 < ntiles) load_tile(rb, Yf, Zf, P, n, p0 + (long long)(t + 2) * TKT, p1, vec);
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const uint32_t ya = su32(ys), za = su32(zs);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int j = cg + e;
-        if (j >= n) break;
-        if (own) {
-          P1S[i * n + j] = sh[e] + sm_[e] + sl[e];
-          HL[i * n + j] = sl[e];
-          P1A[i * n + j] = ah[e] + am[e] + al[e] + ll[e];
-        } else if (mrow) {
-          P2S[i * n + j] = sh[e] + sm_[e];
-          P2A[i * n + j] = ah[e] + am[e];
+        for (int kk = 0; kk < TKT / 16; ++kk) {
+          const uint32_t accum = (t % TDR != 0 || kk > 0) ? 1u : 0u;
+          const uint64_t aY = sdesc(ya + kk * 2 * ksY, ksY, 128);
+          const uint64_t aL = sdesc(ya + kk * 2 * ksY + (2 * nb / 8) * 128, ksY, 128);
+          const uint64_t bZ = sdesc(za + kk * 2 * ksZ, ksZ, 128);
+          mma_bf16(tS, aY, aY, iS, accum);
+          mma_bf16(tA, aY, bZ, iS, accum);
+          mma_bf16(tL, aL, bZ, iL, accum);
         }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(&mbar[s])));
+      }
+      ++g.commits[s];
+      ++gt;
+      if (t % TDR == TDR - 1 || t == ntiles - 1) {
+        if (!wait_all(g, mbar)) timed_out = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        __syncthreads();
+        if (timed_out) break;
+        drain(tS, tA, tL, n, nb, acc);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
       }
     }
-    __syncthreads();
+    if (timed_out) break;
+    // the item's partial sums, each element once: S = P1S + P2S + HL^T, A = P1A + P2A
+    const float *P1S = acc, *HL = acc + n * n, *P1A = HL + n * n, *P2S = P1A + n * n, *P2A = P2S + n * n;
     double *o = out + goff[f] + (long long)ch * 2 * n * n;
     for (int t = tid; t < n * n; t += TNT) {
       const int a = t / n, b = t - a * n;
       o[t] = (double)P1S[t] + (double)P2S[t] + (double)HL[b * n + a];
       o[n * n + t] = (double)P1A[t] + (double)P2A[t];
     }
-  } else if (tid == 0) {
-    atomicOr(flags, DC_FLAG_TIMEOUT);
+    __syncthreads();
   }
+  if (timed_out && tid == 0) atomicOr(flags, DC_FLAG_TIMEOUT);
+  // every committed MMA group has completed (or timed out) before the tensor memory is freed
+  if (!wait_all(g, mbar) && tid == 0) atomicOr(flags, DC_FLAG_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -246,16 +340,18 @@ __global__ void __launch_bounds__(TNT) k_gram_tc(const FragDesc *desc, const int
 namespace dck {
 
 int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
-  const int nb = (c->layout.max_norb + 15) & ~15;
+  const int nmax = c->layout.max_norb;
+  const int nb = (nmax + 15) & ~15;
   if (nb > 64) {
     dc_set_error("mixed-precision Gram needs n <= 64 orbitals per fragment");
     return DC_ERR_ARG;
   }
   const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
-  const size_t sm = 2 * stage;
+  const size_t sm = 2 * stage + 5 * (size_t)nmax * nmax * sizeof(float);
   DC_CUDA(dc_set_smem((const void *)k_gram_tc, sm));
-  k_gram_tc<<<c->n_gram_items, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->d_gram_off, c->gram_chunk, Y, HY,
-                                            c->d_gram, c->d_flags);
+  const int grid = std::min(c->n_gram_items, c->sm_count);
+  k_gram_tc<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,
+                                  Y, HY, c->d_gram, c->d_flags);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

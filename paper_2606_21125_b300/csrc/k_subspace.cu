@@ -153,8 +153,14 @@ __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *
 }
 
 // ---------------------------------------------------------------------------------------------
-// FP64 subspace solve, one CTA per fragment: S = L L^T, Hs = L^-1 A L^-T, cyclic Jacobi
-// (round-robin ordering, n/2 disjoint rotations per round), C = L^-T Q sorted by eigenvalue.
+// Subspace solve, one CTA per fragment (FP64 results): S = L L^T, Hs = L^-1 A L^-T, eigenpairs of
+// Hs, C = L^-T Q sorted by eigenvalue.  The eigensolve is cyclic Jacobi (round-robin ordering, n/2
+// disjoint rotations per round) in two precisions: FP32 sweeps take Hs to the FP32 rounding floor
+// (off-diagonal ~1e-7 |Hs|) at 1/64 of the FP64 instruction cost on this part, one FP64
+// Newton-Schulz step makes their rotation Q32 orthonormal to FP64 rounding, and FP64 sweeps on
+// Q^T Hs Q (quadratically convergent from there, 1-3 sweeps) finish the solve.  FP64 contexts sweep
+// to full convergence; FP32/mixed ones stop after one FP64 sweep (eigenvalue error ~1e-14/gap Ha,
+// eigenvectors far below the FP32 rounding of the rotation that uses them).
 // ---------------------------------------------------------------------------------------------
 constexpr int SNT = 256;
 
@@ -170,19 +176,100 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
   return s;  // all threads
 }
 
+// Cyclic Jacobi on the symmetric np x np matrix M (leading dimension ld), V <- V J.  Before each
+// sweep the off-diagonal and diagonal sums of squares are formed; the solve stops when
+// off <= rel (dia + off) or after max_sweeps sweeps.  A rotation is skipped when
+// |a_pq| <= skip sqrt|a_pp a_qq|.
+template <typename T>
+__device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, double rel, double skip, double *red,
+                              double *rc, double *rs, int *rp, int *rq) {
+  const int tid = threadIdx.x;
+  const int half = np / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int t = tid; t < np * np; t += SNT) {
+      const int i = t / np, j = t - i * np;
+      const double v = (double)M[i * ld + j];
+      if (i == j) dia += v * v;
+      else off += v * v;
+    }
+    off = block_sum_d(off, red);
+    dia = block_sum_d(dia, red);
+    if (!(off > rel * (dia + off))) break;
+    for (int r = 0; r < np - 1; ++r) {
+      if (tid < half) {
+        int p, q;
+        if (tid == 0) {
+          p = r;
+          q = np - 1;
+        } else {
+          p = (r + tid) % (np - 1);
+          q = (r - tid + (np - 1)) % (np - 1);
+        }
+        if (p > q) {
+          const int tmp = p;
+          p = q;
+          q = tmp;
+        }
+        const T app = M[p * ld + p], aqq = M[q * ld + q], apq = M[q * ld + p];
+        T c = T(1), sn = T(0);
+        if (fabs((double)apq) > 1e-300 && fabs((double)apq) > skip * sqrt(fabs((double)app * (double)aqq))) {
+          const T tau = (aqq - app) / (T(2) * apq);
+          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + t * t);
+          sn = t * c;
+        }
+        rp[tid] = p;
+        rq[tid] = q;
+        rc[tid] = (double)c;
+        rs[tid] = (double)sn;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int t = tid; t < half * np; t += SNT) {
+        const int k = t / np, j = t - k * np;
+        const T sn = (T)rs[k];
+        if (sn == T(0)) continue;
+        const int p = rp[k], q = rq[k];
+        const T c = (T)rc[k];
+        const T ap = M[p * ld + j], aq = M[q * ld + j];
+        M[p * ld + j] = c * ap - sn * aq;
+        M[q * ld + j] = sn * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int t = tid; t < half * np; t += SNT) {
+        const int k = t / np, i = t - k * np;
+        const T sn = (T)rs[k];
+        if (sn == T(0)) continue;
+        const int p = rp[k], q = rq[k];
+        const T c = (T)rc[k];
+        const T ap = M[i * ld + p], aq = M[i * ld + q];
+        M[i * ld + p] = c * ap - sn * aq;
+        M[i * ld + q] = sn * ap + c * aq;
+        const T vp = V[i * ld + p], vq = V[i * ld + q];
+        V[i * ld + p] = c * vp - sn * vq;
+        V[i * ld + q] = sn * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const long long *goff, const int *gnchunk,
                                                   const double *gram, double dV, double *eps, double *C64,
-                                                  float *C32, unsigned *flags) {
+                                                  float *C32, unsigned *flags, int fp64_sweeps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = blockIdx.x;
   const FragDesc D = desc[f];
   const int n = D.norb;
   const int np = n + (n & 1);  // even size for the round-robin pairing (index n is a dummy)
   const int ld = np + 1;
-  double *M0 = reinterpret_cast<double *>(smem_raw);  // S -> L -> C
+  double *M0 = reinterpret_cast<double *>(smem_raw);  // S -> L; FP32 Jacobi arrays; V
   double *M1 = M0 + np * ld;                          // L^-1
-  double *M2 = M1 + np * ld;                          // A -> Hs -> diag
-  double *M3 = M2 + np * ld;                          // X -> V
+  double *M2 = M1 + np * ld;                          // A -> Hs -> Q^T Hs Q -> diag
+  double *M3 = M2 + np * ld;                          // X; Q32 promoted; Hs Q
+  double *M4 = M3 + np * ld;                          // Newton-Schulz factor; Q^T Hs Q unsymmetrised
   __shared__ double red[SNT / 32];
   __shared__ double rc[32], rs[32];
   __shared__ int rp[32], rq[32];
@@ -260,92 +347,66 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
     const int i = t / n, j = t - i * n;
     double s = 0.0;
     for (int k = 0; k <= j; ++k) s += M3[i * ld + k] * M1[j * ld + k];
-    M2[i * ld + j] = s;
+    M4[i * ld + j] = s;
   }
   __syncthreads();
+  // symmetrised Hs in M2 (FP64) and its FP32 copy plus Q32 = I in M0's space
+  float *Mf = reinterpret_cast<float *>(M0);
+  float *Vf = Mf + np * ld;
   for (int t = tid; t < np * np; t += SNT) {
     const int i = t / np, j = t - i * np;
     double v = 0.0;
-    if (i < n && j < n) v = 0.5 * (M2[i * ld + j] + M2[j * ld + i]);
-    M3[i * ld + j] = v;  // temporarily the symmetrised Hs
+    if (i < n && j < n) v = 0.5 * (M4[i * ld + j] + M4[j * ld + i]);
+    M2[i * ld + j] = v;
+    Mf[i * ld + j] = (float)v;
+    Vf[i * ld + j] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+
+  // 5a. FP32 Jacobi to the FP32 rounding floor
+  jacobi_sweeps<float>(Mf, Vf, np, ld, 30, 1e-12, 1e-9, red, rc, rs, rp, rq);
+  // 5b. Q = Q32 (3 I - Q32^T Q32) / 2 in FP64 (orthonormal to FP64 rounding; Q32^T Q32 = I + O(1e-7))
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    M3[i * ld + j] = (double)Vf[i * ld + j];
   }
   __syncthreads();
   for (int t = tid; t < np * np; t += SNT) {
     const int i = t / np, j = t - i * np;
-    M2[i * ld + j] = M3[i * ld + j];
-    M3[i * ld + j] = (i == j) ? 1.0 : 0.0;  // V = I
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) s += M3[k * ld + i] * M3[k * ld + j];
+    M4[i * ld + j] = 0.5 * ((i == j ? 3.0 : 0.0) - s);
   }
   __syncthreads();
-
-  // 5. cyclic Jacobi
-  const int half = np / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int t = tid; t < np * np; t += SNT) {
-      const int i = t / np, j = t - i * np;
-      const double v = M2[i * ld + j];
-      if (i == j) dia += v * v;
-      else off += v * v;
-    }
-    off = block_sum_d(off, red);
-    dia = block_sum_d(dia, red);
-    if (!(off > 1e-30 * (dia + off))) break;
-    for (int r = 0; r < np - 1; ++r) {
-      if (tid < half) {
-        int p, q;
-        if (tid == 0) {
-          p = r;
-          q = np - 1;
-        } else {
-          p = (r + tid) % (np - 1);
-          q = (r - tid + (np - 1)) % (np - 1);
-        }
-        if (p > q) {
-          const int tmp = p;
-          p = q;
-          q = tmp;
-        }
-        const double app = M2[p * ld + p], aqq = M2[q * ld + q], apq = M2[p * ld + q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-          const double tau = (aqq - app) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-        }
-        rp[tid] = p;
-        rq[tid] = q;
-        rc[tid] = c;
-        rs[tid] = s;
-      }
-      __syncthreads();
-      // rows: A <- J^T A
-      for (int t = tid; t < half * np; t += SNT) {
-        const int k = t / np, j = t - k * np;
-        const int p = rp[k], q = rq[k];
-        const double c = rc[k], s = rs[k];
-        if (s == 0.0) continue;
-        const double ap = M2[p * ld + j], aq = M2[q * ld + j];
-        M2[p * ld + j] = c * ap - s * aq;
-        M2[q * ld + j] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int t = tid; t < half * np; t += SNT) {
-        const int k = t / np, i = t - k * np;
-        const int p = rp[k], q = rq[k];
-        const double c = rc[k], s = rs[k];
-        if (s == 0.0) continue;
-        const double ap = M2[i * ld + p], aq = M2[i * ld + q];
-        M2[i * ld + p] = c * ap - s * aq;
-        M2[i * ld + q] = s * ap + c * aq;
-        const double vp = M3[i * ld + p], vq = M3[i * ld + q];
-        M3[i * ld + p] = c * vp - s * vq;
-        M3[i * ld + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) s += M3[i * ld + k] * M4[k * ld + j];
+    M0[i * ld + j] = s;  // Q
   }
+  __syncthreads();
+  // 5c. Q^T Hs Q (FP64), symmetrised
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) s += M2[i * ld + k] * M0[k * ld + j];
+    M3[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) s += M0[k * ld + i] * M3[k * ld + j];
+    M4[i * ld + j] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    M2[i * ld + j] = 0.5 * (M4[i * ld + j] + M4[j * ld + i]);
+  }
+  __syncthreads();
+  // 5d. FP64 Jacobi from there
+  jacobi_sweeps<double>(M2, M0, np, ld, fp64_sweeps, 1e-30, 1e-18, red, rc, rs, rp, rq);
 
   // 6. sort ascending (rank by value, ties by index) and C = L^-T V
   __shared__ int rank[DC_MAX_NORB];
@@ -364,7 +425,7 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
   for (int t = tid; t < n * n; t += SNT) {
     const int k = t / n, i = t - k * n;  // C[k][rank[i]] = sum_{m>=k} Linv[m][k] V[m][i]
     double s = 0.0;
-    for (int m = k; m < n; ++m) s += M1[m * ld + k] * M3[m * ld + i];
+    for (int m = k; m < n; ++m) s += M1[m * ld + k] * M0[m * ld + i];
     const long long o = D.sub_off + (long long)k * n + rank[i];
     C64[o] = s;
     if (C32) C32[o] = (float)s;
@@ -456,10 +517,12 @@ int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s) {
 
 int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
   const int np = c->layout.max_norb + (c->layout.max_norb & 1);
-  const size_t sm = 4 * (size_t)np * (np + 1) * sizeof(double);
+  const size_t sm = 5 * (size_t)np * (np + 1) * sizeof(double);
   DC_CUDA(dc_set_smem((const void *)k_subspace, sm));
+  const int fp64_sweeps = precision_bits == 32 ? 1 : 40;
   k_subspace<<<c->nfrag, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, c->d_eps,
-                                       c->d_C64, precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags);
+                                       c->d_C64, precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags,
+                                       fp64_sweeps);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
