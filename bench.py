@@ -324,7 +324,7 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     tun = solver.tuning()["fp64" if args.precision == "fp64" else "fp32"]
     stencil_name = ("k_hpair (orbital-pair FP32 stencil + local + nonlocal H-apply, fused Chebyshev step)"
-                    if tun["kind"] == 1 else "k_hstep (stencil + local + nonlocal H-apply, fused Chebyshev step)")
+                    if tun["kind"] >= 1 else "k_hstep (stencil + local + nonlocal H-apply, fused Chebyshev step)")
     stencil_name += f", {tun['threads']} threads x {tun['pairs']} point pairs"
     h = prof["hpsi"]
     achieved = h["bytes"] / (h["ms"] * 1e-3) / 1e9 if h["ms"] > 0 else 0.0

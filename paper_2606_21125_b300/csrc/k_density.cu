@@ -3,6 +3,7 @@
 #include <climits>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "dc_internal.h"
 
@@ -194,13 +195,99 @@ __global__ void k_density(const FragDesc *desc, const int32_t *owner, const int3
   rho[g] = s;
 }
 
+// ---- FP32 orbital blocks: FP32 products with double-word FP32 accumulation ---------------------
+// The FP64 pipe of this part runs at ~1/64 of FP32, so summing FP32 orbitals in FP64 made these
+// kernels FP64-bound.  Here every square is formed exactly as an unevaluated FP32 pair (product and
+// its FMA residual) and the sums are kept as (hi, lo) FP32 pairs (TwoSum), which carries ~2^-44
+// relative accuracy; the pair is converted to FP64 once per result.
+__device__ __forceinline__ void dw_add(float &hi, float &lo, float a) {
+  const float s = hi + a;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (a - bp);
+  hi = s;
+  lo += e;
+}
+
+// q_i = dV sum_core psi_i^2: CTA = (fragment, 8 orbitals), one warp per orbital.
+__global__ void __launch_bounds__(256) k_core_weights32(const FragDesc *desc, const float *psi, double dV,
+                                                        double *q) {
+  const FragDesc D = desc[blockIdx.x];
+  const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (i >= D.norb) return;
+  const int lane = threadIdx.x & 31;
+  const int Ex = D.E[0], Ey = D.E[1];
+  const long long P = (long long)Ex * Ey * D.E[2];
+  const float *y = psi + D.psi_off + (long long)i * P;
+  const int cx = D.c[0], cy = D.c[1];
+  const int ncore = cx * cy * D.c[2];
+  float hi = 0.f, lo = 0.f;
+  for (int t = lane; t < ncore; t += 32) {
+    const int x = t % cx, yz = t / cx, yy = yz % cy, z = yz / cy;
+    const float v = y[(x + D.b[0]) + Ex * ((yy + D.b[1]) + Ey * (z + D.b[2]))];
+    const float p = __fmul_rn(v, v);  // not contracted into the TwoSum below
+    dw_add(hi, lo, p);
+    lo += fmaf(v, v, -p);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    dw_add(hi, lo, h2);
+    lo += l2;
+  }
+  if (lane == 0) q[D.st_off + i] = dV * ((double)hi + (double)lo);
+}
+
+// rho(g) = sum_i 2 f_i psi_i(j)^2 over the core points of one fragment (CTA = fragment): each core
+// point is owned by exactly one fragment, so every global point is written once.  The occupations
+// are carried as FP32 pairs (2 f = oh + ol) and every term is formed with exact products, so the
+// density integrates to sum 2 f q = N_e to ~1e-12 (an FP32-rounded 2 f would break that at 1e-8).
+__global__ void __launch_bounds__(256) k_density32(const FragDesc *desc, const float *psi, const double *occ, int Nx,
+                                                   int Ny, double *rho) {
+  __shared__ float occh[DC_MAX_NORB], occl[DC_MAX_NORB];
+  const FragDesc D = desc[blockIdx.x];
+  const int n = D.norb;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const double o2 = 2.0 * occ[D.st_off + i];
+    const float h = (float)o2;
+    occh[i] = h;
+    occl[i] = (float)(o2 - (double)h);
+  }
+  __syncthreads();
+  const int Ex = D.E[0], Ey = D.E[1];
+  const long long P = (long long)Ex * Ey * D.E[2];
+  const float *y0 = psi + D.psi_off;
+  const int cx = D.c[0], cy = D.c[1];
+  const int ncore = cx * cy * D.c[2];
+  const int gx0 = D.org[0] + D.b[0], gy0 = D.org[1] + D.b[1], gz0 = D.org[2] + D.b[2];
+  for (int t = threadIdx.x; t < ncore; t += 256) {
+    const int x = t % cx, yz = t / cx, yy = yz % cy, z = yz / cy;
+    const float *y = y0 + (x + D.b[0]) + Ex * ((yy + D.b[1]) + Ey * (z + D.b[2]));
+    float hi = 0.f, lo = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < n; ++i) {
+      const float v = y[(long long)i * P];
+      const float p = __fmul_rn(v, v), pe = fmaf(v, v, -p);  // v^2 = p + pe exactly
+      const float oh = occh[i];
+      const float th = __fmul_rn(oh, p), te = fmaf(oh, p, -th);  // oh p = th + te exactly
+      dw_add(hi, lo, th);
+      lo += te + fmaf(oh, pe, occl[i] * p);
+    }
+    rho[(gx0 + x) + (long long)Nx * ((gy0 + yy) + (long long)Ny * (gz0 + z))] = (double)hi + (double)lo;
+  }
+}
+
 }  // namespace
 
 namespace dck {
 
 template <typename T>
 int launch_core_weights(dc_ctx *c, const T *psi, cudaStream_t s) {
-  k_core_weights<T><<<(unsigned)c->layout.nstates, QNT, 0, s>>>(c->d_desc, c->d_items, psi, c->dV, c->d_q);
+  if constexpr (std::is_same<T, float>::value) {
+    const dim3 grid((unsigned)c->nfrag, (unsigned)((c->layout.max_norb + 7) / 8));
+    k_core_weights32<<<grid, 256, 0, s>>>(c->d_desc, psi, c->dV, c->d_q);
+  } else {
+    k_core_weights<T><<<(unsigned)c->layout.nstates, QNT, 0, s>>>(c->d_desc, c->d_items, psi, c->dV, c->d_q);
+  }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -232,8 +319,12 @@ int launch_fermi(dc_ctx *c, cudaStream_t s) {
 
 template <typename T>
 int launch_density(dc_ctx *c, const T *psi, double *rho, cudaStream_t s) {
-  const unsigned nb = (unsigned)((c->npts + 255) / 256);
-  k_density<T><<<nb, 256, 0, s>>>(c->d_desc, c->d_owner, c->d_core_local, c->npts, psi, c->d_occ, rho);
+  if constexpr (std::is_same<T, float>::value) {
+    k_density32<<<(unsigned)c->nfrag, 256, 0, s>>>(c->d_desc, psi, c->d_occ, c->grid.n[0], c->grid.n[1], rho);
+  } else {
+    const unsigned nb = (unsigned)((c->npts + 255) / 256);
+    k_density<T><<<nb, 256, 0, s>>>(c->d_desc, c->d_owner, c->d_core_local, c->npts, psi, c->d_occ, rho);
+  }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

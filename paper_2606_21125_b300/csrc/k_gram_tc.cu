@@ -6,7 +6,7 @@
 // FP32 accuracy are accumulated in FP32 in tensor memory:
 //   S = hh + hm + mh + hl + lh + mm            (lh = (hl)^T by symmetry)
 //   A = h.zh + h.zm + m.zh + h.zl + l.zh + m.zm (z = HY split the same way)
-// Persistent CTAs (one per SM, 8 warps) walk the (fragment, 2048-point item) list.  Per 64-point
+// Persistent CTAs (one per SM, 16 warps) walk the (fragment, 2048-point item) list.  Per 64-point
 // K-tile the CTA splits Y and HY into BF16 rows in shared memory (K-major, no-swizzle canonical
 // layout), and one thread issues three MMAs per 16-point K-step:
 //   D_S[128 x 3nb] = [Yh;Ym;Yl..] x [Yh|Ym|Yl]^T,  D_A[128 x 3nb] = [Yh;Ym;..] x [Zh|Zm|Zl]^T,
@@ -26,7 +26,7 @@
 namespace {
 
 constexpr int TKT = 64;   // points per K-tile
-constexpr int TNT = 256;  // threads per CTA
+constexpr int TNT = 512;  // threads per CTA
 constexpr int TDR = 4;    // K-tiles per tensor-memory drain (256 points)
 constexpr int TMEM_COLS = 512;
 
@@ -78,12 +78,16 @@ __device__ __forceinline__ int toff(int r, int k, int kstride) {
   return (k >> 3) * kstride + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ void split3(float y, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
-  h = __float2bfloat16_rn(y);
-  const float r1 = y - __bfloat162float(h);
-  m = __float2bfloat16_rn(r1);
-  const float r2 = r1 - __bfloat162float(m);
-  l = __float2bfloat16_rn(r2);
+// Three-word BF16 split of two values at once: y = h + m + l per lane (paired conversions).
+__device__ __forceinline__ void split3x2(float y0, float y1, uint32_t &h, uint32_t &m, uint32_t &l) {
+  const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
+  const float r0 = y0 - __low2float(hb), r1 = y1 - __high2float(hb);
+  const __nv_bfloat162 mb = __floats2bfloat162_rn(r0, r1);
+  const float s0 = r0 - __low2float(mb), s1 = r1 - __high2float(mb);
+  const __nv_bfloat162 lb = __floats2bfloat162_rn(s0, s1);
+  h = *reinterpret_cast<const uint32_t *>(&hb);
+  m = *reinterpret_cast<const uint32_t *>(&mb);
+  l = *reinterpret_cast<const uint32_t *>(&lb);
 }
 
 // Loads of one K-tile: rows i < n, points pb..pb+63, as 16 float4 per row (slots idx = tid + j*TNT).
@@ -97,41 +101,43 @@ __device__ __forceinline__ float4 ld4g(const float *row, long long p, long long 
   return v;
 }
 
-constexpr int TSL = 4;  // float4 slots per thread per array: 64 rows x 16 float4 / 256 threads
+constexpr int TSL = 2;  // float4 slots per thread per array: 64 rows x 16 float4 / 512 threads
 
 struct TileRegs {
   float4 y[TSL], z[TSL];
 };
+
+// Slot idx of a K-tile -> (row i, 4-point quad kq): a warp covers 8 rows x 4 quads, so its 8-byte
+// shared-memory stores fill all 32 banks twice (16 rows apart in the canonical layout) instead of
+// piling 16 lanes onto one core-matrix column.
+__device__ __forceinline__ void tile_slot(int idx, int &i, int &kq) {
+  i = ((idx >> 7) << 3) | (idx & 7);
+  kq = (idx >> 3) & 15;
+}
 
 __device__ __forceinline__ void load_tile(TileRegs &r, const float *Yf, const float *Zf, long long P, int n,
                                           long long pb, long long p1, bool vec) {
 #pragma unroll
   for (int j = 0; j < TSL; ++j) {
     const int idx = threadIdx.x + j * TNT;
-    if (idx < n * 16) {
-      const int i = idx >> 4;
-      const long long p = pb + 4 * (idx & 15);
+    int i, kq;
+    tile_slot(idx, i, kq);
+    if (i < n) {
+      const long long p = pb + 4 * kq;
       r.y[j] = ld4g(Yf + (long long)i * P, p, p1, vec);
       r.z[j] = ld4g(Zf + (long long)i * P, p, p1, vec);
     }
   }
 }
 
-__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d) {
-  const __nv_bfloat162 lo = __halves2bfloat162(a, b), hi = __halves2bfloat162(c, d);
-  return make_uint2(*reinterpret_cast<const uint32_t *>(&lo), *reinterpret_cast<const uint32_t *>(&hi));
-}
-
 // Split 4 consecutive-point values of row i into h/m/l rows (base row offsets 0, nb, 2 nb).
 __device__ __forceinline__ void store_split(unsigned char *st, int i, int k, int ks, int nb, float4 v) {
-  __nv_bfloat16 h[4], m[4], l[4];
-  split3(v.x, h[0], m[0], l[0]);
-  split3(v.y, h[1], m[1], l[1]);
-  split3(v.z, h[2], m[2], l[2]);
-  split3(v.w, h[3], m[3], l[3]);
-  *reinterpret_cast<uint2 *>(st + toff(i, k, ks)) = pack4(h[0], h[1], h[2], h[3]);
-  *reinterpret_cast<uint2 *>(st + toff(nb + i, k, ks)) = pack4(m[0], m[1], m[2], m[3]);
-  *reinterpret_cast<uint2 *>(st + toff(2 * nb + i, k, ks)) = pack4(l[0], l[1], l[2], l[3]);
+  uint32_t h0, m0, l0, h1, m1, l1;
+  split3x2(v.x, v.y, h0, m0, l0);
+  split3x2(v.z, v.w, h1, m1, l1);
+  *reinterpret_cast<uint2 *>(st + toff(i, k, ks)) = make_uint2(h0, h1);
+  *reinterpret_cast<uint2 *>(st + toff(nb + i, k, ks)) = make_uint2(m0, m1);
+  *reinterpret_cast<uint2 *>(st + toff(2 * nb + i, k, ks)) = make_uint2(l0, l1);
 }
 
 __device__ __forceinline__ void convert_tile(const TileRegs &r, unsigned char *ys, unsigned char *zs, int n, int nb,
@@ -139,8 +145,10 @@ __device__ __forceinline__ void convert_tile(const TileRegs &r, unsigned char *y
 #pragma unroll
   for (int j = 0; j < TSL; ++j) {
     const int idx = threadIdx.x + j * TNT;
-    if (idx < n * 16) {
-      const int i = idx >> 4, k = 4 * (idx & 15);
+    int i, kq;
+    tile_slot(idx, i, kq);
+    if (i < n) {
+      const int k = 4 * kq;
       store_split(ys, i, k, ksY, nb, r.y[j]);
       store_split(zs, i, k, ksZ, nb, r.z[j]);
     }
@@ -167,16 +175,17 @@ __device__ __forceinline__ bool wait_all(GramPipe &g, uint64_t *mbar) {
 
 // Adds the tensor-memory accumulators into the FP32 sums: rows r < n (h rows) give
 // P1S += hh + hm + hl, HL += hl, P1A += h.zh + h.zm + h.zl + l.zh; rows nb <= r < nb + n (m rows)
-// give P2S += mh + mm, P2A += m.zh + m.zm.  Warp w reads lanes 32 (w % 4) .. +31, warps 0-3 the
-// even 8-column groups and warps 4-7 the odd ones.
+// give P2S += mh + mm, P2A += m.zh + m.zm.  Warp w reads lanes 32 (w % 4) .. +31 and the 8-column
+// groups g with g % 4 == w / 4.
 __device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int n, int nb, float *acc) {
-  float *P1S = acc, *HL = acc + n * n, *P1A = HL + n * n, *P2S = P1A + n * n, *P2A = P2S + n * n;
+  const int ld = n + 1;  // odd row stride: the 32 lanes (rows) of a warp hit 32 different banks
+  float *P1S = acc, *HL = acc + n * ld, *P1A = HL + n * ld, *P2S = P1A + n * ld, *P2A = P2S + n * ld;
   const int warp = threadIdx.x >> 5;
   const int r = 32 * (warp & 3) + (threadIdx.x & 31);
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const bool own = r < n, mrow = (r >= nb && r < nb + n);
   const int i = own ? r : r - nb;
-  for (int cg = 8 * (warp >> 2); cg < nb; cg += 16) {
+  for (int cg = 8 * (warp >> 2); cg < nb; cg += 32) {
     float sh[8], sm_[8], sl[8], ah[8], am[8], al[8], ll[8];
     tmem_ld8(tS + lane_base + cg, sh);
     tmem_ld8(tS + lane_base + nb + cg, sm_);
@@ -190,12 +199,12 @@ __device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int
       const int j = cg + e;
       if (j < n) {
         if (own) {
-          P1S[i * n + j] += sh[e] + sm_[e] + sl[e];
-          HL[i * n + j] += sl[e];
-          P1A[i * n + j] += ah[e] + am[e] + al[e] + ll[e];
+          P1S[i * ld + j] += sh[e] + sm_[e] + sl[e];
+          HL[i * ld + j] += sl[e];
+          P1A[i * ld + j] += ah[e] + am[e] + al[e] + ll[e];
         } else if (mrow) {
-          P2S[i * n + j] += sh[e] + sm_[e];
-          P2A[i * n + j] += ah[e] + am[e];
+          P2S[i * ld + j] += sh[e] + sm_[e];
+          P2A[i * ld + j] += ah[e] + am[e];
         }
       }
     }
@@ -212,7 +221,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   const int tid = threadIdx.x;
   const int nbmax = (nmax + 15) & ~15;
   const int stage_max = (2 * nbmax + 128) * TKT * 2 + 3 * nbmax * TKT * 2;
-  float *acc = reinterpret_cast<float *>(sm + 2 * stage_max);  // [5][n][n]
+  float *acc = reinterpret_cast<float *>(sm + 2 * stage_max);  // [5][n][n + 1]
 
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
       for (int t = tid; t < 2 * stage_bytes / 16; t += TNT) reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
       prev_n = n;
     }
-    for (int t = tid; t < 5 * n * n; t += TNT) acc[t] = 0.f;
+    for (int t = tid; t < 5 * n * (n + 1); t += TNT) acc[t] = 0.f;
     const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
     TileRegs ra, rb;
     load_tile(ra, Yf, Zf, P, n, p0, p1, vec);
@@ -317,12 +326,14 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
     }
     if (timed_out) break;
     // the item's partial sums, each element once: S = P1S + P2S + HL^T, A = P1A + P2A
-    const float *P1S = acc, *HL = acc + n * n, *P1A = HL + n * n, *P2S = P1A + n * n, *P2A = P2S + n * n;
+    const int ld = n + 1;
+    const float *P1S = acc, *HL = acc + n * ld, *P1A = HL + n * ld, *P2S = P1A + n * ld, *P2A = P2S + n * ld;
     double *o = out + goff[f] + (long long)ch * 2 * n * n;
     for (int t = tid; t < n * n; t += TNT) {
       const int a = t / n, b = t - a * n;
-      o[t] = (double)P1S[t] + (double)P2S[t] + (double)HL[b * n + a];
-      o[n * n + t] = (double)P1A[t] + (double)P2A[t];
+      const int u = a * ld + b;
+      o[t] = (double)P1S[u] + (double)P2S[u] + (double)HL[b * ld + a];
+      o[n * n + t] = (double)P1A[u] + (double)P2A[u];
     }
     __syncthreads();
   }
@@ -347,7 +358,7 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     return DC_ERR_ARG;
   }
   const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
-  const size_t sm = 2 * stage + 5 * (size_t)nmax * nmax * sizeof(float);
+  const size_t sm = 2 * stage + 5 * (size_t)nmax * (nmax + 1) * sizeof(float);
   DC_CUDA(dc_set_smem((const void *)k_gram_tc, sm));
   const int grid = std::min(c->n_gram_items, c->sm_count);
   k_gram_tc<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,

@@ -562,10 +562,12 @@ __device__ __forceinline__ float2 lap_pair(const PairK<ISO> &K, float2 c, const 
 // Shared-memory carve of the orbital-pair kernels (sizes in the fragment's own extents).
 struct PairSmem {
   float2 *pin, *pout, *gx2, *pacc, *sk2;
-  float4 *rec;
+  float4 *rec;  // [nrec][maxent] (u_i, u_i+1, float4 index of the slot's x factors, gz gy)
+  int *recky;   // [nrec][maxent] slot | row << 16
   int2 *box;
   int *rb;
-  float *red;
+  float *red;  // [2][NT / 32] (at most 2 x 32 floats)
+  float *pf;   // prefetch ring of k_hpair
 };
 
 __device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int Ey, int Ez, int A, int maxent,
@@ -580,19 +582,28 @@ __device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int E
   size_t off = (size_t)(reinterpret_cast<unsigned char *>(m.sk2 + A) - raw);
   off = (off + 15) & ~(size_t)15;
   m.rec = reinterpret_cast<float4 *>(raw + off);
-  m.box = reinterpret_cast<int2 *>(m.rec + nrec * maxent);
+  m.recky = reinterpret_cast<int *>(m.rec + nrec * maxent);
+  m.box = reinterpret_cast<int2 *>(m.recky + ((nrec * maxent + 1) & ~1));
   m.rb = reinterpret_cast<int *>(m.box + A);
   m.red = reinterpret_cast<float *>(m.rb + Ez * Ey + 1);
+  off = (size_t)(reinterpret_cast<unsigned char *>(m.red + 2 * 32) - raw);
+  m.pf = reinterpret_cast<float *>(raw + ((off + 15) & ~(size_t)15));
   return m;
 }
 
-size_t pair_smem_bytes(int Ex, int Ey, int Ez, int A, int maxent, int nrec, bool halo, int NT) {
+// Per-thread prefetch ring of k_hpair: 3 planes x PP pairs x 6 values (V at 2 points, Y_{k-1} at
+// 2 points x 2 orbitals), laid out [plane slot][pair][value][thread].
+constexpr int kPfVals = 6;
+
+size_t pair_smem_bytes(int Ex, int Ey, int Ez, int A, int maxent, int nrec, bool halo, int NT, int PP = 0) {
   const int pitch = (Ex + 9) & ~1, pitch2 = (Ex + 1) & ~1;
   size_t n2 = (halo ? 2 * (size_t)(Ey + 8) * pitch : 0) + 2 * (size_t)Ey * pitch2 + (size_t)A * pitch2 +
               (size_t)Ey * A + A;
   size_t b = (n2 * sizeof(float2) + 15) & ~(size_t)15;
-  b += (size_t)nrec * maxent * sizeof(float4) + (size_t)A * sizeof(int2) + (size_t)(Ez * Ey + 1) * sizeof(int) +
-       2 * (size_t)(NT / 32) * sizeof(float);
+  b += (size_t)nrec * maxent * sizeof(float4) + (size_t)((nrec * maxent + 1) & ~1) * sizeof(int) +
+       (size_t)A * sizeof(int2) + (size_t)(Ez * Ey + 1) * sizeof(int) + 2 * 32 * sizeof(float);
+  b = (b + 15) & ~(size_t)15;
+  b += 3 * (size_t)PP * kPfVals * NT * sizeof(float);
   return b + 64;
 }
 
@@ -628,11 +639,11 @@ __device__ __forceinline__ void pair_setup(const HArgs<float> &a, const FragDesc
 // Projection tasks of one plane: one task per row-list entry (row y, slot k) forms
 // gz gy sum_x gx_k[x] out(x, y) for both orbitals and adds it to pacc[y][k] (one writer per plane).
 template <int NT>
-__device__ __forceinline__ void pair_project(const float2 *pl, const float4 *rc, int ne, const PairSmem &m,
-                                             int pitch2, int A) {
+__device__ __forceinline__ void pair_project(const float2 *pl, const float4 *rc, const int *rky, int ne,
+                                             const PairSmem &m, int pitch2, int A) {
   for (int t = threadIdx.x; t < ne; t += NT) {
-    const float4 r = rc[t];
-    const int kb = __float_as_int(r.z);
+    const int kb = rky[t];
+    const float w = rc[t].w;
     const int k = kb & 0xffff, y = kb >> 16;
     const int2 bx = m.box[k];
     const float4 *o4 = reinterpret_cast<const float4 *>(pl + y * pitch2);
@@ -645,7 +656,7 @@ __device__ __forceinline__ void pair_project(const float2 *pl, const float4 *rc,
       s1 = fma2(hi2(o), hi2(g), s1);
     }
     float2 &pa = m.pacc[y * A + k];
-    pa = fma2(f2(r.w, r.w), add2(s0, s1), pa);
+    pa = fma2(f2(w, w), add2(s0, s1), pa);
   }
 }
 
@@ -666,27 +677,26 @@ __device__ __forceinline__ void pair_finish(const HArgs<float> &a, const FragDes
   }
 }
 
-// Records of plane z: (u_i, u_i+1, slot|row, gz gy) with u = alpha D C <p|y> gz gy.  The first 2 NT
-// entries come from registers (loaded one plane ahead), any further ones straight from global memory.
+// Records of plane z from its row-list entries: (u_i, u_i+1, float4 index k pitch2/2 of the slot's
+// x factors, gz gy) and slot|row, with u = alpha D C <p|y> gz gy.  The first 2 NT entries come from
+// registers (loaded one plane ahead), any further ones straight from global memory.
+__device__ __forceinline__ void pair_record(int t, int2 e, const float2 *sk2, int pitch2, float4 *rc, int *rky) {
+  const float w = __int_as_float(e.y);
+  const int k = e.x & 0xffff;
+  const float2 u = sk2[k];
+  rc[t] = make_float4(u.x * w, u.y * w, __int_as_float(k * (pitch2 >> 1)), w);
+  rky[t] = e.x;
+}
+
 template <int NT>
 __device__ __forceinline__ void pair_records(const int2 *ent, int ne, const int2 (&pre)[2], const float2 *sk2,
-                                             float4 *rc) {
+                                             int pitch2, float4 *rc, int *rky) {
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const int t = threadIdx.x + j * NT;
-    if (t < ne) {
-      const int2 e = pre[j];
-      const float w = __int_as_float(e.y);
-      const float2 u = sk2[e.x & 0xffff];
-      rc[t] = make_float4(u.x * w, u.y * w, __int_as_float(e.x), w);
-    }
+    if (t < ne) pair_record(t, pre[j], sk2, pitch2, rc, rky);
   }
-  for (int t = threadIdx.x + 2 * NT; t < ne; t += NT) {
-    const int2 e = ent[t];
-    const float w = __int_as_float(e.y);
-    const float2 u = sk2[e.x & 0xffff];
-    rc[t] = make_float4(u.x * w, u.y * w, __int_as_float(e.x), w);
-  }
+  for (int t = threadIdx.x + 2 * NT; t < ne; t += NT) pair_record(t, ent[t], sk2, pitch2, rc, rky);
 }
 
 template <int NT>
@@ -698,24 +708,213 @@ __device__ __forceinline__ void pair_prefetch(const int2 *ent, int ne, int2 (&pr
   }
 }
 
-template <int NT, int PP, bool ISO>
-__global__ void __launch_bounds__(NT, (PP == 1 && NT <= 256) ? 512 / NT : 1) k_hpair(HArgs<float> a) {
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+
+// Per-CTA constants of k_hpair.
+template <int PP>
+struct HPair {
+  int Ex, Ey, Ez, plane, pitch, pitch2, pplane, A, P, nvalid, o1off;
+  bool proj, use_prev, periodic;
+  int mode;
+  float vsh, alpha;
+  float2 bb, occ2;
+  const float *yin, *yprev, *vf;
+  float *yout;
+  const int2 *ent;
+  int t0[PP];  // point offset y Ex + x of each owned pair (x even)
+  int px[PP], py[PP];
+  bool valid[PP], v1[PP];
+};
+
+// Issue the asynchronous copies of plane zz's V and Y_{k-1} values of this thread's pairs into ring
+// slot `slot` (each thread reads back only its own values, so no barrier is involved), and close the
+// copy group (an empty group past the last plane keeps the group count uniform).
+template <int NT, int PP>
+__device__ __forceinline__ void hpair_prefetch(const HPair<PP> &H, float *pf, int zz, int slot) {
+  if (zz < H.Ez) {
+    const int oh = zz * H.plane;
+#pragma unroll
+    for (int r = 0; r < PP; ++r) {
+      if (!H.valid[r]) continue;
+      float *d = pf + ((slot * PP + r) * kPfVals) * NT + threadIdx.x;
+      const float *v = H.vf + oh + H.t0[r];
+      cp_async4(d, v);
+      if (H.v1[r]) cp_async4(d + NT, v + 1);
+      if (H.use_prev) {
+        const float *p = H.yprev + oh + H.t0[r];
+        cp_async4(d + 2 * NT, p);
+        cp_async4(d + 3 * NT, p + H.o1off);
+        if (H.v1[r]) {
+          cp_async4(d + 4 * NT, p + 1);
+          cp_async4(d + 5 * NT, p + H.o1off + 1);
+        }
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+// One plane z of k_hpair.  ZI = z mod 9 names the register slots: q[r][(ZI + k) % 9] holds plane
+// z - 4 + k, so the column advances without moving registers (the kernel unrolls z by 9).
+template <int NT, int PP, bool ISO, int ZI>
+__device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO> &K, const PairSmem &m, int maxent,
+                                            float4 (&q)[PP][9], int2 (&pre)[2], float2 &dot, int z, int b3) {
+  float2 *P0 = m.pin + (z & 1) * H.pplane;
+  // centre values of plane z (and the periodic halo)
+#pragma unroll
+  for (int r = 0; r < PP; ++r) {
+    if (!H.valid[r]) continue;
+    const float4 cv = q[r][(ZI + 4) % 9];
+    const int x = H.px[r], y = H.py[r];
+    const int c = (y + 4) * H.pitch + x + 4;
+    if (H.v1[r]) *reinterpret_cast<float4 *>(P0 + c) = cv;
+    else P0[c] = lo2(cv);
+    if (H.periodic) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !H.v1[r]) continue;
+        const int xx = x + h;
+        const float2 vv = h == 0 ? lo2(cv) : hi2(cv);
+        if (xx < 4) P0[c + h + H.Ex] = vv;
+        if (xx >= H.Ex - 4) P0[c + h - H.Ex] = vv;
+        if (y < 4) P0[c + h + H.Ey * H.pitch] = vv;
+        if (y >= H.Ey - 4) P0[c + h - H.Ey * H.pitch] = vv;
+      }
+    }
+  }
+  const int rz = z * H.Ey;
+  const int e0 = m.rb[rz];
+  const int nez = m.rb[rz + H.Ey] - e0;
+  float4 *RC = m.rec + b3 * maxent;
+  pair_records<NT>(H.ent + e0, nez, pre, m.sk2, H.pitch2, RC, m.recky + b3 * maxent);
+  if (z + 1 < H.Ez) pair_prefetch<NT>(H.ent + m.rb[rz + H.Ey], m.rb[rz + 2 * H.Ey] - m.rb[rz + H.Ey], pre);
+  __syncthreads();
+  if (H.proj && z > 0) {
+    const int bp = b3 == 0 ? 2 : b3 - 1;
+    pair_project<NT>(m.pout + ((z - 1) & 1) * H.Ey * H.pitch2, m.rec + bp * maxent, m.recky + bp * maxent,
+                     e0 - m.rb[rz - H.Ey], m, H.pitch2, H.A);
+  }
+
+  int zn = z + 5;
+  bool zin = zn < H.Ez;
+  if (!zin && H.periodic) {
+    zn -= H.Ez;
+    zin = true;
+  }
+  const int zoff = zn * H.plane;
+  const int oh = z * H.plane;
+  // V and Y_{k-1} of plane z + 2 start loading; plane z's copies (two groups back) must be complete
+  hpair_prefetch<NT, PP>(H, m.pf, z + 2, (ZI + 2) % 3);
+  cp_async_wait2();
+#pragma unroll
+  for (int r = 0; r < PP; ++r) {
+    if (!H.valid[r]) continue;
+    const int x = H.px[r], y = H.py[r];
+    const bool v1 = H.v1[r];
+    const int t0 = H.t0[r];
+    const float *pn = H.yin + zoff + t0;
+    const float4 nxt = make_float4(zin ? pn[0] : 0.f, zin ? pn[H.o1off] : 0.f, (zin && v1) ? pn[1] : 0.f,
+                                   (zin && v1) ? pn[H.o1off + 1] : 0.f);
+    const float *ps = m.pf + (((ZI % 3) * PP + r) * kPfVals) * NT + threadIdx.x;
+    const float va = fmaf(H.alpha, ps[0], H.vsh);
+    const float vb = v1 ? fmaf(H.alpha, ps[NT], H.vsh) : 0.f;
+    float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (H.use_prev) pv = make_float4(ps[2 * NT], ps[3 * NT], v1 ? ps[4 * NT] : 0.f, v1 ? ps[5 * NT] : 0.f);
+    const float2 *co = P0 + (y + 4) * H.pitch + x + 4;
+    float2 row[10];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const float4 X = *reinterpret_cast<const float4 *>(co - 4 + 2 * j);
+      row[2 * j] = lo2(X);
+      row[2 * j + 1] = hi2(X);
+    }
+    float2 ym0[4], yp0[4], ym1[4], yp1[4], zm0[4], zp0[4], zm1[4], zp1[4], xm0[4], xp0[4], xm1[4], xp1[4];
+#pragma unroll
+    for (int n = 1; n <= 4; ++n) {
+      const float4 u = *reinterpret_cast<const float4 *>(co + n * H.pitch);
+      const float4 d = *reinterpret_cast<const float4 *>(co - n * H.pitch);
+      yp0[n - 1] = lo2(u);
+      yp1[n - 1] = hi2(u);
+      ym0[n - 1] = lo2(d);
+      ym1[n - 1] = hi2(d);
+      zp0[n - 1] = lo2(q[r][(ZI + 4 + n) % 9]);
+      zp1[n - 1] = hi2(q[r][(ZI + 4 + n) % 9]);
+      zm0[n - 1] = lo2(q[r][(ZI + 4 - n) % 9]);
+      zm1[n - 1] = hi2(q[r][(ZI + 4 - n) % 9]);
+      xp0[n - 1] = row[4 + n];
+      xm0[n - 1] = row[4 - n];
+      xp1[n - 1] = row[5 + n];
+      xm1[n - 1] = row[5 - n];
+    }
+    const float2 c0 = lo2(q[r][(ZI + 4) % 9]), c1 = hi2(q[r][(ZI + 4) % 9]);
+    float2 h0 = fma2(f2(va, va), c0, mul2(H.bb, lo2(pv)));
+    float2 h1 = fma2(f2(vb, vb), c1, mul2(H.bb, hi2(pv)));
+    h0 = lap_pair<ISO>(K, c0, xm0, xp0, ym0, yp0, zm0, zp0, h0);
+    h1 = lap_pair<ISO>(K, c1, xm1, xp1, ym1, yp1, zm1, zp1, h1);
+    // nonlocal term over the row's records
+    {
+      const int eb = m.rb[rz + y] - e0, ee = m.rb[rz + y + 1] - e0;
+      const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2 + x);
+      for (int e = eb; e < ee; ++e) {
+        const float4 rr = RC[e];
+        const float4 g = g4[__float_as_int(rr.z)];
+        const float2 u = lo2(rr);
+        h0 = fma2(u, lo2(g), h0);
+        h1 = fma2(u, hi2(g), h1);
+      }
+    }
+    float2 out0 = h0, out1 = h1;
+    if (H.mode == HSTEP_ADJ) {
+      dot = fma2(c0, h0, dot);
+      if (v1) dot = fma2(c1, h1, dot);
+      out0 = mul2(H.occ2, h0);
+      out1 = mul2(H.occ2, h1);
+    }
+    if (H.yout) {
+      float *po = H.yout + oh + t0;
+      po[0] = out0.x;
+      if (v1) po[1] = out1.x;
+      if (H.nvalid > 1) {
+        po[H.P] = out0.y;
+        if (v1) po[H.P + 1] = out1.y;
+      }
+    }
+    if (H.proj) {
+      float2 *pp = m.pout + (z & 1) * H.Ey * H.pitch2 + y * H.pitch2 + x;
+      *reinterpret_cast<float4 *>(pp) = make_float4(out0.x, out0.y, v1 ? out1.x : 0.f, v1 ? out1.y : 0.f);
+    }
+    q[r][ZI % 9] = nxt;  // plane z + 5 replaces plane z - 4
+  }
+}
+
+template <int NT, int PP, bool ISO, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 fi = a.items[blockIdx.x];
   const int f = fi.x, i0 = fi.y;
   const FragDesc D = a.desc[f];
-  const int nvalid = min(2, D.norb - i0);
-  const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2];
-  const int plane = Ex * Ey;
-  const int nxp = (Ex + 1) >> 1;
-  const int npairs = nxp * Ey;
-  const int pitch = (Ex + 9) & ~1;
-  const int pitch2 = (Ex + 1) & ~1;
-  const int pplane = pitch * (Ey + 8);
-  const int A = D.natom;
-  const long long P = (long long)plane * Ez;
-  const bool proj = a.cout != nullptr;
-  const PairSmem m = pair_carve(smem_raw, Ex, Ey, Ez, A, a.maxent, 3, true);
+  HPair<PP> H;
+  H.nvalid = min(2, D.norb - i0);
+  H.Ex = D.E[0];
+  H.Ey = D.E[1];
+  H.Ez = D.E[2];
+  H.plane = H.Ex * H.Ey;
+  H.pitch = (H.Ex + 9) & ~1;
+  H.pitch2 = (H.Ex + 1) & ~1;
+  H.pplane = H.pitch * (H.Ey + 8);
+  H.A = D.natom;
+  H.P = H.plane * H.Ez;
+  H.o1off = H.nvalid > 1 ? H.P : 0;
+  H.proj = a.cout != nullptr;
+  H.periodic = a.periodic != 0;
+  H.mode = a.mode;
+  const PairSmem m = pair_carve(smem_raw, H.Ex, H.Ey, H.Ez, H.A, a.maxent, 3, true);
 
   float alpha = 1.f, beta = 0.f, shift = 0.f;
   if (a.mode == HSTEP_CHEB) {
@@ -724,9 +923,24 @@ __global__ void __launch_bounds__(NT, (PP == 1 && NT <= 256) ? 512 / NT : 1) k_h
     alpha = float(bd[4 + 2 * a.step]);
     beta = float(bd[5 + 2 * a.step]);
   }
-  const bool use_prev = (a.mode == HSTEP_CHEB) && a.yprev != nullptr && a.step > 0;
-  pair_setup<NT>(a, D, m, i0, nvalid, alpha);
-  for (int t = threadIdx.x; t < 2 * pplane; t += NT) m.pin[t] = f2(0.f, 0.f);
+  H.use_prev = (a.mode == HSTEP_CHEB) && a.yprev != nullptr && a.step > 0;
+  H.alpha = alpha;
+  H.vsh = -alpha * shift;
+  H.bb = f2(beta, beta);
+  H.occ2 = f2(0.f, 0.f);
+  if (a.mode == HSTEP_ADJ) {
+    H.occ2.x = float(2.0 * a.occ[D.st_off + i0] * a.dV);
+    if (H.nvalid > 1) H.occ2.y = float(2.0 * a.occ[D.st_off + i0 + 1] * a.dV);
+  }
+  // orbital i0 at element offset base, i0+1 at base + P (an invalid second orbital reads the first)
+  const long long base = D.psi_off + (long long)i0 * H.P;
+  H.yin = a.yin + base;
+  H.yprev = H.use_prev ? a.yprev + base : nullptr;
+  H.yout = a.yout ? a.yout + base : nullptr;
+  H.vf = a.vf + D.pt_off;
+  H.ent = a.row_ent + a.row_beg[D.row_off];
+  pair_setup<NT>(a, D, m, i0, H.nvalid, alpha);
+  for (int t = threadIdx.x; t < 2 * H.pplane; t += NT) m.pin[t] = f2(0.f, 0.f);
 
   PairK<ISO> K;
   {
@@ -744,189 +958,68 @@ __global__ void __launch_bounds__(NT, (PP == 1 && NT <= 256) ? 512 / NT : 1) k_h
     }
     K.kc = f2(-2.f * s34, -2.f * s34);
   }
-  const float2 bb = f2(beta, beta);
-  const float vsh = -alpha * shift;
-  float2 occ2 = f2(0.f, 0.f);
-  if (a.mode == HSTEP_ADJ) {
-    occ2.x = float(2.0 * a.occ[D.st_off + i0] * a.dV);
-    if (nvalid > 1) occ2.y = float(2.0 * a.occ[D.st_off + i0 + 1] * a.dV);
-  }
-  // orbital i0 at element offset base, i0+1 at base + P (an invalid second orbital reads the first)
-  const long long base = D.psi_off + (long long)i0 * P;
-  const long long o1off = nvalid > 1 ? P : 0;
-  const float *vf = a.vf + D.pt_off;
-  const int2 *ent = a.row_ent + a.row_beg[D.row_off];
 
-  int px[PP], py[PP];
-  bool valid[PP], v1[PP];
+  const int nxp = (H.Ex + 1) >> 1;
+  const int npairs = nxp * H.Ey;
   float4 q[PP][9];
 #pragma unroll
   for (int r = 0; r < PP; ++r) {
     const int p = threadIdx.x + r * NT;
-    valid[r] = p < npairs;
-    py[r] = valid[r] ? p / nxp : 0;
-    px[r] = valid[r] ? 2 * (p - py[r] * nxp) : 0;
-    v1[r] = valid[r] && (px[r] + 1 < Ex);
-    const float *col = a.yin + base + px[r] + py[r] * Ex;
+    H.valid[r] = p < npairs;
+    H.py[r] = H.valid[r] ? p / nxp : 0;
+    H.px[r] = H.valid[r] ? 2 * (p - H.py[r] * nxp) : 0;
+    H.v1[r] = H.valid[r] && (H.px[r] + 1 < H.Ex);
+    H.t0[r] = H.px[r] + H.py[r] * H.Ex;
+    const float *col = H.yin + H.t0[r];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       int zz = k - 4;
-      bool in = zz >= 0 && zz < Ez;
-      if (!in && a.periodic) {
-        zz = zz < 0 ? zz + Ez : zz - Ez;
+      bool in = zz >= 0 && zz < H.Ez;
+      if (!in && H.periodic) {
+        zz = zz < 0 ? zz + H.Ez : zz - H.Ez;
         in = true;
       }
-      const float *pz = col + (long long)zz * plane;
-      const bool i0k = in && valid[r], i1k = in && v1[r];
-      q[r][k] = make_float4(i0k ? pz[0] : 0.f, i0k ? pz[o1off] : 0.f, i1k ? pz[1] : 0.f, i1k ? pz[o1off + 1] : 0.f);
+      const float *pz = col + zz * H.plane;
+      const bool i0k = in && H.valid[r], i1k = in && H.v1[r];
+      q[r][k] = make_float4(i0k ? pz[0] : 0.f, i0k ? pz[H.o1off] : 0.f, i1k ? pz[1] : 0.f,
+                            i1k ? pz[H.o1off + 1] : 0.f);
     }
   }
+  hpair_prefetch<NT, PP>(H, m.pf, 0, 0);
+  hpair_prefetch<NT, PP>(H, m.pf, 1, 1);
   __syncthreads();
   int2 pre[2];
-  pair_prefetch<NT>(ent, m.rb[Ey], pre);
+  pair_prefetch<NT>(H.ent, m.rb[H.Ey], pre);
 
   float2 dot = f2(0.f, 0.f);
-  int b3 = 0;
-  for (int z = 0; z < Ez; ++z) {
-    float2 *P0 = m.pin + (z & 1) * pplane;
-    // centre values of plane z (and the periodic halo)
-#pragma unroll
-    for (int r = 0; r < PP; ++r) {
-      if (!valid[r]) continue;
-      const int x = px[r], y = py[r];
-      const int c = (y + 4) * pitch + x + 4;
-      if (v1[r]) *reinterpret_cast<float4 *>(P0 + c) = q[r][4];
-      else P0[c] = lo2(q[r][4]);
-      if (a.periodic) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          if (h == 1 && !v1[r]) continue;
-          const int xx = x + h;
-          const float2 vv = h == 0 ? lo2(q[r][4]) : hi2(q[r][4]);
-          if (xx < 4) P0[c + h + Ex] = vv;
-          if (xx >= Ex - 4) P0[c + h - Ex] = vv;
-          if (y < 4) P0[c + h + Ey * pitch] = vv;
-          if (y >= Ey - 4) P0[c + h - Ey * pitch] = vv;
-        }
-      }
-    }
-    const int e0 = m.rb[z * Ey];
-    const int nez = m.rb[(z + 1) * Ey] - e0;
-    float4 *RC = m.rec + b3 * a.maxent;
-    pair_records<NT>(ent + e0, nez, pre, m.sk2, RC);
-    if (z + 1 < Ez) pair_prefetch<NT>(ent + m.rb[(z + 1) * Ey], m.rb[(z + 2) * Ey] - m.rb[(z + 1) * Ey], pre);
-    __syncthreads();
-    if (proj && z > 0) {
-      const int zp = z - 1;
-      const int bp = b3 == 0 ? 2 : b3 - 1;
-      pair_project<NT>(m.pout + (zp & 1) * Ey * pitch2, m.rec + bp * a.maxent,
-                       m.rb[(zp + 1) * Ey] - m.rb[zp * Ey], m, pitch2, A);
-    }
-
-    int zn = z + 5;
-    bool zin = zn < Ez;
-    if (!zin && a.periodic) {
-      zn -= Ez;
-      zin = true;
-    }
-    const long long zoff = (long long)zn * plane;
-    const long long o_here = (long long)z * plane;
-#pragma unroll
-    for (int r = 0; r < PP; ++r) {
-      if (!valid[r]) continue;
-      const int x = px[r], y = py[r];
-      const int t0 = y * Ex + x;
-      const float *pn = a.yin + base + zoff + t0;
-      const float4 nxt = make_float4(zin ? pn[0] : 0.f, zin ? pn[o1off] : 0.f, (zin && v1[r]) ? pn[1] : 0.f,
-                                     (zin && v1[r]) ? pn[o1off + 1] : 0.f);
-      const float va = fmaf(alpha, vf[o_here + t0], vsh);
-      const float vb = v1[r] ? fmaf(alpha, vf[o_here + t0 + 1], vsh) : 0.f;
-      float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (use_prev) {
-        const float *pp = a.yprev + base + o_here + t0;
-        pv = make_float4(pp[0], pp[o1off], v1[r] ? pp[1] : 0.f, v1[r] ? pp[o1off + 1] : 0.f);
-      }
-      const float2 *co = P0 + (y + 4) * pitch + x + 4;
-      float4 X[5];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) X[j] = *reinterpret_cast<const float4 *>(co - 4 + 2 * j);
-      // point m of the row (m = -4 .. 5 relative to x): X[(m + 4) / 2], low half for even m
-      float2 row[10];
-#pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        row[2 * j] = lo2(X[j]);
-        row[2 * j + 1] = hi2(X[j]);
-      }
-      float2 ym0[4], yp0[4], ym1[4], yp1[4], zm0[4], zp0[4], zm1[4], zp1[4], xm0[4], xp0[4], xm1[4], xp1[4];
-#pragma unroll
-      for (int n = 1; n <= 4; ++n) {
-        const float4 u = *reinterpret_cast<const float4 *>(co + n * pitch);
-        const float4 d = *reinterpret_cast<const float4 *>(co - n * pitch);
-        yp0[n - 1] = lo2(u);
-        yp1[n - 1] = hi2(u);
-        ym0[n - 1] = lo2(d);
-        ym1[n - 1] = hi2(d);
-        zp0[n - 1] = lo2(q[r][4 + n]);
-        zp1[n - 1] = hi2(q[r][4 + n]);
-        zm0[n - 1] = lo2(q[r][4 - n]);
-        zm1[n - 1] = hi2(q[r][4 - n]);
-        xp0[n - 1] = row[4 + n];
-        xm0[n - 1] = row[4 - n];
-        xp1[n - 1] = row[5 + n];
-        xm1[n - 1] = row[5 - n];
-      }
-      const float2 c0 = lo2(q[r][4]), c1 = hi2(q[r][4]);
-      float2 h0 = fma2(f2(va, va), c0, mul2(bb, lo2(pv)));
-      float2 h1 = fma2(f2(vb, vb), c1, mul2(bb, hi2(pv)));
-      h0 = lap_pair<ISO>(K, c0, xm0, xp0, ym0, yp0, zm0, zp0, h0);
-      h1 = lap_pair<ISO>(K, c1, xm1, xp1, ym1, yp1, zm1, zp1, h1);
-      // nonlocal term over the row's records
-      {
-        const int eb = m.rb[z * Ey + y] - e0, ee = m.rb[z * Ey + y + 1] - e0;
-        const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2 + x);
-        for (int e = eb; e < ee; ++e) {
-          const float4 rr = RC[e];
-          const int k = __float_as_int(rr.z) & 0xffff;
-          const float4 g = g4[(k * pitch2) >> 1];
-          const float2 u = lo2(rr);
-          h0 = fma2(u, lo2(g), h0);
-          h1 = fma2(u, hi2(g), h1);
-        }
-      }
-      float2 out0 = h0, out1 = h1;
-      if (a.mode == HSTEP_ADJ) {
-        dot = fma2(c0, h0, dot);
-        if (v1[r]) dot = fma2(c1, h1, dot);
-        out0 = mul2(occ2, h0);
-        out1 = mul2(occ2, h1);
-      }
-      if (a.yout) {
-        float *po = a.yout + base + o_here + t0;
-        po[0] = out0.x;
-        if (v1[r]) po[1] = out1.x;
-        if (nvalid > 1) {
-          po[P] = out0.y;
-          if (v1[r]) po[P + 1] = out1.y;
-        }
-      }
-      if (proj) {
-        float2 *pp = m.pout + (z & 1) * Ey * pitch2 + y * pitch2 + x;
-        *reinterpret_cast<float4 *>(pp) = make_float4(out0.x, out0.y, v1[r] ? out1.x : 0.f, v1[r] ? out1.y : 0.f);
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) q[r][k] = q[r][k + 1];
-      q[r][8] = nxt;
-    }
-    b3 = b3 == 2 ? 0 : b3 + 1;
+  const int maxent = a.maxent;
+  for (int z0 = 0; z0 < H.Ez; z0 += 9) {
+    hpair_plane<NT, PP, ISO, 0>(H, K, m, maxent, q, pre, dot, z0, 0);
+    if (z0 + 1 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 1>(H, K, m, maxent, q, pre, dot, z0 + 1, 1);
+    if (z0 + 2 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 2>(H, K, m, maxent, q, pre, dot, z0 + 2, 2);
+    if (z0 + 3 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 3>(H, K, m, maxent, q, pre, dot, z0 + 3, 0);
+    if (z0 + 4 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 4>(H, K, m, maxent, q, pre, dot, z0 + 4, 1);
+    if (z0 + 5 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 5>(H, K, m, maxent, q, pre, dot, z0 + 5, 2);
+    if (z0 + 6 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 6>(H, K, m, maxent, q, pre, dot, z0 + 6, 0);
+    if (z0 + 7 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 7>(H, K, m, maxent, q, pre, dot, z0 + 7, 1);
+    if (z0 + 8 >= H.Ez) break;
+    hpair_plane<NT, PP, ISO, 8>(H, K, m, maxent, q, pre, dot, z0 + 8, 2);
   }
-  if (proj) {
+  if (H.proj) {
     __syncthreads();
-    const int zp = Ez - 1;
-    const int bp = b3 == 0 ? 2 : b3 - 1;
-    pair_project<NT>(m.pout + (zp & 1) * Ey * pitch2, m.rec + bp * a.maxent, m.rb[(zp + 1) * Ey] - m.rb[zp * Ey], m,
-                     pitch2, A);
+    const int zp = H.Ez - 1;
+    const int bp = zp % 3;
+    pair_project<NT>(m.pout + (zp & 1) * H.Ey * H.pitch2, m.rec + bp * maxent, m.recky + bp * maxent,
+                     m.rb[(zp + 1) * H.Ey] - m.rb[zp * H.Ey], m, H.pitch2, H.A);
     __syncthreads();
-    pair_finish<NT>(a, D, m, i0, nvalid);
+    pair_finish<NT>(a, D, m, i0, H.nvalid);
   }
   if (a.mode == HSTEP_ADJ) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -940,11 +1033,11 @@ __global__ void __launch_bounds__(NT, (PP == 1 && NT <= 256) ? 512 / NT : 1) k_h
       m.red[NT / 32 + w] = dot.y;
     }
     __syncthreads();
-    if (threadIdx.x < nvalid) {
-      float s = 0.f;
-      for (int i = 0; i < NT / 32; ++i) s += m.red[threadIdx.x * (NT / 32) + i];
+    if (threadIdx.x < H.nvalid) {
+      float sum = 0.f;
+      for (int i = 0; i < NT / 32; ++i) sum += m.red[threadIdx.x * (NT / 32) + i];
       const int st = D.st_off + i0 + threadIdx.x;
-      a.dots[st] = a.occ[st] * a.dV * (double)s;
+      a.dots[st] = a.occ[st] * a.dV * (double)sum;
     }
   }
 }
@@ -981,10 +1074,12 @@ __global__ void __launch_bounds__(NT) k_project_pair(HArgs<float> a) {
       pl[y * pitch2 + x] = f2(p[0], p[o1off]);
     }
     const int e0 = m.rb[z * Ey];
-    pair_records<NT>(ent + e0, m.rb[(z + 1) * Ey] - e0, pre, m.sk2, m.rec + (z & 1) * a.maxent);
+    pair_records<NT>(ent + e0, m.rb[(z + 1) * Ey] - e0, pre, m.sk2, pitch2, m.rec + (z & 1) * a.maxent,
+                     m.recky + (z & 1) * a.maxent);
     if (z + 1 < Ez) pair_prefetch<NT>(ent + m.rb[(z + 1) * Ey], m.rb[(z + 2) * Ey] - m.rb[(z + 1) * Ey], pre);
     __syncthreads();
-    pair_project<NT>(pl, m.rec + (z & 1) * a.maxent, m.rb[(z + 1) * Ey] - e0, m, pitch2, A);
+    pair_project<NT>(pl, m.rec + (z & 1) * a.maxent, m.recky + (z & 1) * a.maxent, m.rb[(z + 1) * Ey] - e0, m,
+                     pitch2, A);
   }
   __syncthreads();
   pair_finish<NT>(a, D, m, i0, nvalid);
@@ -1076,19 +1171,20 @@ int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
 }
 
 // Launch shapes of the stencil kernels: kind 0 = x-adjacent point pairs of one orbital (NO orbitals
-// per CTA), kind 1 = orbital-pair kernel (FP32 only); threads per CTA; point pairs per thread.
+// per CTA), kind 1 = orbital-pair kernel (FP32 only), kind 2 = the orbital-pair kernel with its
+// registers capped for three 256-thread CTAs per SM; threads per CTA; point pairs per thread.
 struct Shape {
   int kind, nt, pp;
 };
 constexpr Shape kShapes[] = {{0, 128, 1}, {0, 128, 2}, {0, 256, 1}, {0, 256, 2}, {0, 512, 1},
                              {0, 512, 2}, {0, 512, 4}, {1, 128, 1}, {1, 256, 1}, {1, 512, 1},
-                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}};
+                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}, {2, 128, 1}, {2, 256, 1}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 static_assert(kNumShapes <= DC_TUNE_SLOTS, "tuning slots");
 
-size_t hpair_smem(const dc_ctx *c, int NT) {
+size_t hpair_smem(const dc_ctx *c, int NT, int PP) {
   return pair_smem_bytes(c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms, std::max(1, c->max_plane_ent), 3,
-                         true, NT);
+                         true, NT, PP);
 }
 size_t project_pair_smem(const dc_ctx *c) {
   return pair_smem_bytes(c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms, std::max(1, c->max_plane_ent), 2,
@@ -1102,9 +1198,11 @@ bool iso_coeffs(const HArgs<float> &a) {
   return true;
 }
 
-template <int NT, int PP>
+// MINB: CTAs per SM the register budget is cut for (launch bounds); the default keeps two
+// 256-thread CTAs per SM, the register-capped variant three.
+template <int NT, int PP, int MINB = ((PP == 1 && NT <= 256) ? 512 / NT : 1)>
 int run_hpair(dc_ctx *c, HArgs<float> a, cudaStream_t s) {
-  const size_t sm = hpair_smem(c, NT);
+  const size_t sm = hpair_smem(c, NT, PP);
   if (sm > 227 * 1024) {
     dc_set_error("hpsi: fragment tables exceed shared memory (orbital-pair kernel)");
     return DC_ERR_ARG;
@@ -1112,11 +1210,11 @@ int run_hpair(dc_ctx *c, HArgs<float> a, cudaStream_t s) {
   a.items = c->d_items2;
   a.maxent = std::max(1, c->max_plane_ent);
   if (iso_coeffs(a)) {
-    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, true>, sm));
-    k_hpair<NT, PP, true><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
+    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, true, MINB>, sm));
+    k_hpair<NT, PP, true, MINB><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
   } else {
-    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, false>, sm));
-    k_hpair<NT, PP, false><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
+    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, false, MINB>, sm));
+    k_hpair<NT, PP, false, MINB><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
   }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
@@ -1154,7 +1252,9 @@ int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
     case 9: return run_hpair<512, 1>(c, a, s);
     case 10: return run_hpair<1024, 1>(c, a, s);
     case 11: return run_hpair<256, 2>(c, a, s);
-    default: return run_hpair<512, 2>(c, a, s);
+    case 12: return run_hpair<512, 2>(c, a, s);
+    case 13: return run_hpair<128, 1, 6>(c, a, s);
+    default: return run_hpair<256, 1, 3>(c, a, s);
   }
 }
 
@@ -1163,7 +1263,7 @@ int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
 bool shape_ok(const dc_ctx *c, int shape, size_t esz) {
   if (shape < 0 || shape >= kNumShapes) return false;
   const Shape S = kShapes[shape];
-  if (S.kind == 1 && (esz != sizeof(float) || hpair_smem(c, S.nt) > 227 * 1024)) return false;
+  if (S.kind >= 1 && (esz != sizeof(float) || hpair_smem(c, S.nt, S.pp) > 227 * 1024)) return false;
   const int pairs = ((c->max_E[0] + 1) / 2) * c->max_E[1];
   const int cover = S.nt * S.pp;
   return cover >= pairs && (cover <= 4 * pairs || S.nt == 128);

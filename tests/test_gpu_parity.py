@@ -139,7 +139,7 @@ def test_hpsi(case, dtype):
 
 # (kind, threads per CTA, point pairs per thread) of the stencil kernels
 SHAPES = [(0, 128, 1), (0, 128, 2), (0, 256, 1), (0, 256, 2), (0, 512, 1), (0, 512, 2), (0, 512, 4),
-          (1, 128, 1), (1, 256, 1), (1, 512, 1), (1, 1024, 1), (1, 256, 2), (1, 512, 2)]
+          (1, 128, 1), (1, 256, 1), (1, 512, 1), (1, 1024, 1), (1, 256, 2), (1, 512, 2), (2, 128, 1), (2, 256, 1)]
 
 
 @pytest.mark.parametrize("case", ["si8", "uneven", "periodic", "wide", "water_auto"])
@@ -149,7 +149,7 @@ def test_hpsi_every_launch_shape(case, dtype):
     ran = _hpsi_against_oracle(case, dtype, SHAPES)
     assert any(k == 0 for k, _, _ in ran)
     if dtype == "fp32":
-        assert any(k == 1 for k, _, _ in ran)
+        assert any(k == 1 for k, _, _ in ran) and any(k == 2 for k, _, _ in ran)
     else:
         assert all(k == 0 for k, _, _ in ran)
 
@@ -177,7 +177,7 @@ def test_subspace_and_one_chefsi_pass_fp64(case):
 
 
 @pytest.mark.parametrize("case", ["periodic", "uneven", "water_auto"])
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_subspace_and_one_chefsi_pass_fp32(case, kind):
     """FP32 filter steps (with their in-kernel projections) under both stencil kernel kinds."""
     cfg = CASES[case](precision="fp32")
