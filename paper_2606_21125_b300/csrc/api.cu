@@ -75,7 +75,7 @@ void free_ctx(dc_ctx *c) {
                   c->blk64[1], c->blk64[2], c->d_hy64, c->d_c64[0], c->d_c64[1], c->d_c32[0], c->d_c32[1],
                   c->d_eps, c->d_q, c->d_occ, c->d_bounds, c->d_gram, c->d_gram_off, c->d_gram_nchunk, c->d_C64,
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
-                  c->d_items2, c->d_row_beg, c->d_row_ent,
+                  c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
                   c->d_dots};
   for (void *p : ptrs)
@@ -216,7 +216,9 @@ int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
   const double pj = es * proj_elems(c);
   int cur = ib;
   int cbuf = 0;
-  {
+  if (c->proj_ok == (int)sizeof(T)) {
+    cbuf = c->proj_buf;  // <p|Psi> of the state block, rotated at the end of the previous pass
+  } else {
     StageScope sc(c, DC_STAGE_PROJECT, s, blk + pj, 1);
     DC_TRY(dck::launch_project<T>(c, B[cur], cproj<T>(c, 0), s));
   }
@@ -258,6 +260,13 @@ int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
     StageScope sc(c, DC_STAGE_ROTATE, s, 2.0 * blk, 1);
     DC_TRY(dck::launch_rotate<T>(c, B[cur], B[hy], s));
   }
+  {
+    // <p|Y C> = <p|Y> C: the next pass starts from rotated projections instead of a pass over Psi
+    StageScope sc(c, DC_STAGE_PROJECT, s, 2.0 * pj, 1);
+    DC_TRY(dck::launch_rotate_proj<T>(c, cproj<T>(c, cbuf), cproj<T>(c, cbuf ^ 1), s));
+  }
+  c->proj_ok = (int)sizeof(T);
+  c->proj_buf = cbuf ^ 1;
   ib = hy;
   return DC_OK;
 }
@@ -316,6 +325,7 @@ int tune(dc_ctx *c, const T *y, T *out, cudaStream_t s) {
       if (c->hstep_shape[ti] >= 0) return DC_OK;
     }
   }
+  c->proj_ok = 0;  // the projection buffers serve as scratch here
   DC_TRY(dck::launch_project<T>(c, y, cproj<T>(c, 0), s));
   DC_TRY(dck::tune_hstep<T>(c, y, out, cproj<T>(c, 0), s));
   if (path && path[0]) {
@@ -359,6 +369,8 @@ int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
 int capture_step(dc_ctx *c, double *rin, cudaStream_t s) {
   StepGraph g;
   g.ib_before = c->ib_psi;
+  g.proj_before = c->proj_ok;
+  g.pbuf_before = c->proj_buf;
   g.rho = rin;
   g.prof = c->prof_on;
   if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -372,7 +384,11 @@ int capture_step(dc_ctx *c, double *rin, cudaStream_t s) {
   const int st = step_body(c, rin, s);
   c->prof_sink = sink;
   g.ib_after = c->ib_psi;
+  g.proj_after = c->proj_ok;
+  g.pbuf_after = c->proj_buf;
   c->ib_psi = ib;
+  c->proj_ok = g.proj_before;
+  c->proj_buf = g.pbuf_before;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &graph);
   if (st == DC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
@@ -462,6 +478,25 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   std::vector<double> Datom(c->natom), posv(c->h_pos);
   for (int a = 0; a < c->natom; ++a) Datom[a] = c->h_Ds[c->h_species[a]];
   DC_TRY(upload(&c->d_atom_D, Datom));
+  {
+    // Upper bound of the nonlocal term per fragment (Sec. 2.2 filter bounds): sum over its slots of
+    // max(D, 0) dV C^2 |gx|^2 |gy|^2 |gz|^2, fixed for the context.
+    std::vector<double> nlb(c->nfrag, 0.0);
+    for (int f = 0; f < c->nfrag; ++f) {
+      const FragDesc &D = c->h_desc[f];
+      const int tw = tab_width(D);
+      for (int k = 0; k < D.natom; ++k) {
+        const ProjSlot &S = ht.slots[D.at_off + k];
+        const double *g = &ht.tab[D.tab_off + (long long)k * tw];
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int j = 0; j < D.E[0]; ++j) sx += g[j] * g[j];
+        for (int j = 0; j < D.E[1]; ++j) sy += g[D.E[0] + j] * g[D.E[0] + j];
+        for (int j = 0; j < D.E[2]; ++j) sz += g[D.E[0] + D.E[1] + j] * g[D.E[0] + D.E[1] + j];
+        nlb[f] += std::max(Datom[S.atom], 0.0) * c->dV * S.coef * S.coef * sx * sy * sz;
+      }
+    }
+    DC_TRY(upload(&c->d_nl_bound, nlb));
+  }
   DC_TRY(upload(&c->d_atom_pos, posv));
   DC_TRY(upload(&c->d_atom_species, c->h_species));
   std::vector<double> spec;
@@ -702,6 +737,7 @@ int dc_hpsi(dc_ctx *c, const void *d_psi, void *d_hpsi, int dtype, void *stream)
     dc_set_error("dc_hpsi: invalid argument");
     return DC_ERR_ARG;
   }
+  c->proj_ok = 0;  // projection buffer 0 holds the caller block's projections below
   const double es = dtype == DC_FP64 ? 8.0 : 4.0, blk = es * (double)c->layout.psi_elems;
   const double vfb = es * (double)c->layout.frag_points, pj = es * proj_elems(c);
   if (dtype == DC_FP64) {
@@ -744,6 +780,7 @@ int dc_warmup(dc_ctx *c, void *stream) {
   cudaStream_t s = S(stream);
   DC_TRY(dck::launch_potential(c, c->d_rho0, s));
   DC_TRY(dck::launch_gather(c, s));
+  c->proj_ok = 0;
   if (c->params.precision == DC_FP64) {
     DC_TRY(dck::launch_init_psi(c, (double *)c->blk[0], s));
     c->ib_psi = 0;
@@ -762,6 +799,7 @@ int dc_warmup(dc_ctx *c, void *stream) {
     if (st == DC_OK) st = check_flags(c, s);
     for (int p = 0; st == DC_OK && p < c->params.n_warmup; ++p) st = chefsi_pass<double>(c, c->blk64, ib, true, s);
     if (st == DC_OK) st = dck::launch_convert(c->blk64[ib], (float *)c->blk[0], (long long)ne, s);
+    c->proj_ok = 0;  // the FP32 state has no projections yet
     cudaStreamSynchronize(s);
     for (int k = 0; k < 3; ++k) {
       cudaFree(c->blk64[k]);
@@ -792,6 +830,7 @@ int dc_set_state(dc_ctx *c, const void *d_psi, const double *d_eps, void *stream
     DC_CUDA(cudaMemcpyAsync(c->blk[c->ib_psi], d_psi, (size_t)c->layout.element_bytes * c->layout.psi_elems,
                             cudaMemcpyDeviceToDevice, S(stream)));
   if (d_eps) DC_CUDA(cudaMemcpyAsync(c->d_eps, d_eps, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, S(stream)));
+  if (d_psi) c->proj_ok = 0;
   c->warmed = true;
   return DC_OK;
 }
@@ -829,7 +868,8 @@ int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, vo
   int gi = -1;
   if (c->graphs_enabled && c->steps_done >= 1) {
     for (size_t k = 0; k < c->graphs.size(); ++k)
-      if (c->graphs[k].ib_before == c->ib_psi && c->graphs[k].rho == rin && c->graphs[k].prof == c->prof_on)
+      if (c->graphs[k].ib_before == c->ib_psi && c->graphs[k].rho == rin && c->graphs[k].prof == c->prof_on &&
+          c->graphs[k].proj_before == c->proj_ok && c->graphs[k].pbuf_before == c->proj_buf)
         gi = (int)k;
     if (gi < 0) {
       if (c->graphs.size() >= 12) destroy_graphs(c);
@@ -839,6 +879,8 @@ int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, vo
   if (gi >= 0) {
     DC_CUDA(cudaGraphLaunch(c->graphs[gi].exec, s));
     c->ib_psi = c->graphs[gi].ib_after;
+    c->proj_ok = c->graphs[gi].proj_after;
+    c->proj_buf = c->graphs[gi].pbuf_after;
   } else {
     DC_TRY(step_body(c, rin, s));
   }
@@ -886,6 +928,7 @@ int dc_get_rho_out(dc_ctx *c, double *d_rho, void *stream) {
 
 int dc_eb_adjoint(dc_ctx *c, const void *d_psi, int dtype, const double *d_occ, const double *d_V, const double *d_D,
                   double *h_Eb, void *d_dpsi, double *d_dV, double *d_dD, void *stream) {
+  if (c) c->proj_ok = 0;  // projection buffer 0 holds the caller block's projections
   if (!c || !d_psi || !d_occ || !d_V || !d_D || (dtype != DC_FP64 && dtype != DC_FP32)) {
     dc_set_error("dc_eb_adjoint: invalid argument");
     return DC_ERR_ARG;

@@ -65,6 +65,7 @@ struct ProfRec {
 struct StepGraph {
   cudaGraphExec_t exec = nullptr;
   int ib_before = 0, ib_after = 0;
+  int proj_before = 0, pbuf_before = 0, proj_after = 0, pbuf_after = 0;
   const double *rho = nullptr;
   bool prof = false;
   std::vector<ProfRec> recs;
@@ -104,6 +105,7 @@ struct dc_ctx {
   int *d_row_beg = nullptr;    // per-row (z, y) list starts into d_row_ent
   int2 *d_row_ent = nullptr;   // (slot | y << 16, FP32 bits of gz(z) gy(y))
   double *d_atom_D = nullptr;  // D per atom (global index)
+  double *d_nl_bound = nullptr;  // per fragment: upper bound of the nonlocal operator (filter bounds)
   double *d_atom_pos = nullptr;
   int *d_atom_species = nullptr;
   double *d_species = nullptr;  // [4][nspecies]: Z, sigma_loc, sigma_proj, D
@@ -133,6 +135,10 @@ struct dc_ctx {
   // projections (n_f * A_f per fragment), two buffers (input / output of a step)
   double *d_c64[2] = {nullptr, nullptr};
   float *d_c32[2] = {nullptr, nullptr};
+  // <p|Psi> of the state block is valid in buffer proj_buf when proj_ok equals the element size
+  // (8 or 4); 0 = not valid (the next pass projects the block itself)
+  int proj_ok = 0;
+  int proj_buf = 0;
 
   // subspace arrays
   double *d_eps = nullptr;      // Ritz values [nstates]
@@ -257,6 +263,8 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s);
 int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s);
 template <typename T>
 int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s);
+template <typename T>
+int launch_rotate_proj(dc_ctx *c, const T *cin, T *cout, cudaStream_t s);
 
 // density
 template <typename T>

@@ -87,8 +87,7 @@ __global__ void k_veff(long long n, const double *vion, const double2 *vh, doubl
 // Per-fragment potential gather and rigorous spectral upper bound of H_f:
 //   b_up = max symbol of -1/2 L8 + max_j V_f(j) + sum_k max(D_k, 0) <p_k|p_k>.
 __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const double *veff, double *vf64, float *vf32,
-                         const ProjSlot *slots, const double *tab, const double *Datom, double dV, double kin_max,
-                         double *bounds, int bstride) {
+                         const double *nl_bound, double kin_max, double *bounds, int bstride) {
   __shared__ double red[8];
   const int f = blockIdx.x;
   const FragDesc D = desc[f];
@@ -106,18 +105,7 @@ __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const dou
   if (threadIdx.x == 0) {
     double m = red[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    const int tabw = tab_width(D);
-    double nl = 0.0;
-    for (int k = 0; k < D.natom; ++k) {
-      const ProjSlot S = slots[D.at_off + k];
-      const double *g = tab + D.tab_off + (long long)k * tabw;
-      double sx = 0.0, sy = 0.0, sz = 0.0;
-      for (int j = 0; j < D.E[0]; ++j) sx += g[j] * g[j];
-      for (int j = 0; j < D.E[1]; ++j) sy += g[D.E[0] + j] * g[D.E[0] + j];
-      for (int j = 0; j < D.E[2]; ++j) sz += g[D.E[0] + D.E[1] + j] * g[D.E[0] + D.E[1] + j];
-      nl += fmax(Datom[S.atom], 0.0) * dV * S.coef * S.coef * sx * sy * sz;
-    }
-    bounds[(long long)f * bstride + 1] = kin_max + m + nl;
+    bounds[(long long)f * bstride + 1] = kin_max + m + nl_bound[f];
   }
 }
 
@@ -340,8 +328,8 @@ int launch_gather(dc_ctx *c, cudaStream_t s) {
   const double sym = fd[0] + 2.0 * (-fd[1] + fd[2] - fd[3] + fd[4]);
   double kin = 0.0;
   for (int d = 0; d < 3; ++d) kin += -sym / (2.0 * c->h[d] * c->h[d]);
-  k_gather<<<c->nfrag, 256, 0, s>>>(c->d_desc, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32, c->d_slots,
-                                    c->d_tab64, c->d_atom_D, c->dV, kin, c->d_bounds, 4 + 2 * c->params.cheb_degree);
+  k_gather<<<c->nfrag, 256, 0, s>>>(c->d_desc, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32, c->d_nl_bound, kin,
+                                    c->d_bounds, 4 + 2 * c->params.cheb_degree);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

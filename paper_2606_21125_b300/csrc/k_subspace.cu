@@ -159,42 +159,45 @@ __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *
 // (off-diagonal ~1e-7 |Hs|) at 1/64 of the FP64 instruction cost on this part, one FP64
 // Newton-Schulz step makes their rotation Q32 orthonormal to FP64 rounding, and FP64 sweeps on
 // Q^T Hs Q (quadratically convergent from there, 1-3 sweeps) finish the solve.  FP64 contexts sweep
-// to full convergence; FP32/mixed ones stop after one FP64 sweep (eigenvalue error ~1e-14/gap Ha,
-// eigenvectors far below the FP32 rounding of the rotation that uses them).
+// to full convergence.  FP32/mixed contexts take the diagonal of the FP64 Q^T Hs Q as it stands:
+// with off-diagonals ~1e-7 |Hs| these Rayleigh quotients are within ~1e-14/gap Ha of the
+// eigenvalues, and the vectors' ~1e-7 mixing is below the FP32 rounding of the rotation that
+// applies them.
 // ---------------------------------------------------------------------------------------------
 constexpr int SNT = 256;
 
-__device__ __forceinline__ double block_sum_d(double v, double *red) {
+template <typename T>
+__device__ __forceinline__ T block_sum_t(T v, T *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   for (int i = 0; i < SNT / 32; ++i) s += red[i];
   __syncthreads();
   return s;  // all threads
 }
 
-// Cyclic Jacobi on the symmetric np x np matrix M (leading dimension ld), V <- V J.  Before each
-// sweep the off-diagonal and diagonal sums of squares are formed; the solve stops when
-// off <= rel (dia + off) or after max_sweeps sweeps.  A rotation is skipped when
-// |a_pq| <= skip sqrt|a_pp a_qq|.
+// Cyclic Jacobi on the symmetric np x np matrix M (leading dimension ld), V <- V J, all arithmetic
+// in T.  Before each sweep the off-diagonal and diagonal sums of squares are formed; the solve
+// stops when off <= rel (dia + off) or after max_sweeps sweeps.  A rotation is skipped when
+// |a_pq| <= skip sqrt|a_pp a_qq|.  rc, rs, red: shared scratch of T.
 template <typename T>
-__device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, double rel, double skip, double *red,
-                              double *rc, double *rs, int *rp, int *rq) {
+__device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, T rel, T skip, T *red, T *rc, T *rs,
+                              int *rp, int *rq) {
   const int tid = threadIdx.x;
   const int half = np / 2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, dia = 0.0;
+    T off = T(0), dia = T(0);
     for (int t = tid; t < np * np; t += SNT) {
       const int i = t / np, j = t - i * np;
-      const double v = (double)M[i * ld + j];
+      const T v = M[i * ld + j];
       if (i == j) dia += v * v;
       else off += v * v;
     }
-    off = block_sum_d(off, red);
-    dia = block_sum_d(dia, red);
+    off = block_sum_t<T>(off, red);
+    dia = block_sum_t<T>(dia, red);
     if (!(off > rel * (dia + off))) break;
     for (int r = 0; r < np - 1; ++r) {
       if (tid < half) {
@@ -213,7 +216,7 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, double
         }
         const T app = M[p * ld + p], aqq = M[q * ld + q], apq = M[q * ld + p];
         T c = T(1), sn = T(0);
-        if (fabs((double)apq) > 1e-300 && fabs((double)apq) > skip * sqrt(fabs((double)app * (double)aqq))) {
+        if (apq != T(0) && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
           const T tau = (aqq - app) / (T(2) * apq);
           const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
           c = T(1) / sqrt(T(1) + t * t);
@@ -221,17 +224,17 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, double
         }
         rp[tid] = p;
         rq[tid] = q;
-        rc[tid] = (double)c;
-        rs[tid] = (double)sn;
+        rc[tid] = c;
+        rs[tid] = sn;
       }
       __syncthreads();
       // rows: A <- J^T A
       for (int t = tid; t < half * np; t += SNT) {
         const int k = t / np, j = t - k * np;
-        const T sn = (T)rs[k];
+        const T sn = rs[k];
         if (sn == T(0)) continue;
         const int p = rp[k], q = rq[k];
-        const T c = (T)rc[k];
+        const T c = rc[k];
         const T ap = M[p * ld + j], aq = M[q * ld + j];
         M[p * ld + j] = c * ap - sn * aq;
         M[q * ld + j] = sn * ap + c * aq;
@@ -240,10 +243,10 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, double
       // columns: A <- A J, V <- V J
       for (int t = tid; t < half * np; t += SNT) {
         const int k = t / np, i = t - k * np;
-        const T sn = (T)rs[k];
+        const T sn = rs[k];
         if (sn == T(0)) continue;
         const int p = rp[k], q = rq[k];
-        const T c = (T)rc[k];
+        const T c = rc[k];
         const T ap = M[i * ld + p], aq = M[i * ld + q];
         M[i * ld + p] = c * ap - sn * aq;
         M[i * ld + q] = sn * ap + c * aq;
@@ -254,6 +257,18 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, double
       __syncthreads();
     }
   }
+}
+
+// Upper-triangle index t in [0, np (np + 1) / 2) -> (i, j) with i <= j, row-major.  Threads walk the
+// triangle itself: masked lanes would still occupy the FP64 pipe.
+__device__ __forceinline__ void tri_ij(int t, int np, int &i, int &j) {
+  const float b = 2.f * np + 1.f;
+  int r = (int)((b - sqrtf(b * b - 8.f * (float)t)) * 0.5f);
+  r = max(0, min(r, np - 1));
+  while (r > 0 && r * (2 * np - r + 1) / 2 > t) --r;
+  while ((r + 1) * (2 * np - r) / 2 <= t) ++r;
+  i = r;
+  j = t - r * (2 * np - r + 1) / 2 + r;
 }
 
 __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const long long *goff, const int *gnchunk,
@@ -272,6 +287,7 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
   double *M4 = M3 + np * ld;                          // Newton-Schulz factor; Q^T Hs Q unsymmetrised
   __shared__ double red[SNT / 32];
   __shared__ double rc[32], rs[32];
+  __shared__ float redf[SNT / 32], rcf[32], rsf[32];
   __shared__ int rp[32], rq[32];
   __shared__ int failed;
   const int tid = threadIdx.x;
@@ -364,18 +380,22 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
   __syncthreads();
 
   // 5a. FP32 Jacobi to the FP32 rounding floor
-  jacobi_sweeps<float>(Mf, Vf, np, ld, 30, 1e-12, 1e-9, red, rc, rs, rp, rq);
+  jacobi_sweeps<float>(Mf, Vf, np, ld, 30, 1e-12f, 1e-9f, redf, rcf, rsf, rp, rq);
   // 5b. Q = Q32 (3 I - Q32^T Q32) / 2 in FP64 (orthonormal to FP64 rounding; Q32^T Q32 = I + O(1e-7))
   for (int t = tid; t < np * np; t += SNT) {
     const int i = t / np, j = t - i * np;
     M3[i * ld + j] = (double)Vf[i * ld + j];
   }
   __syncthreads();
-  for (int t = tid; t < np * np; t += SNT) {
-    const int i = t / np, j = t - i * np;
+  const int ntri = np * (np + 1) / 2;
+  for (int t = tid; t < ntri; t += SNT) {
+    int i, j;
+    tri_ij(t, np, i, j);
     double s = 0.0;
     for (int k = 0; k < np; ++k) s += M3[k * ld + i] * M3[k * ld + j];
-    M4[i * ld + j] = 0.5 * ((i == j ? 3.0 : 0.0) - s);
+    const double v = 0.5 * ((i == j ? 3.0 : 0.0) - s);
+    M4[i * ld + j] = v;
+    M4[j * ld + i] = v;
   }
   __syncthreads();
   for (int t = tid; t < np * np; t += SNT) {
@@ -393,16 +413,14 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
     M3[i * ld + j] = s;
   }
   __syncthreads();
-  for (int t = tid; t < np * np; t += SNT) {
-    const int i = t / np, j = t - i * np;
+  // Q^T (Hs Q) is symmetric up to rounding: form the upper triangle and mirror it
+  for (int t = tid; t < ntri; t += SNT) {
+    int i, j;
+    tri_ij(t, np, i, j);
     double s = 0.0;
     for (int k = 0; k < np; ++k) s += M0[k * ld + i] * M3[k * ld + j];
-    M4[i * ld + j] = s;
-  }
-  __syncthreads();
-  for (int t = tid; t < np * np; t += SNT) {
-    const int i = t / np, j = t - i * np;
-    M2[i * ld + j] = 0.5 * (M4[i * ld + j] + M4[j * ld + i]);
+    M2[i * ld + j] = s;
+    M2[j * ld + i] = s;
   }
   __syncthreads();
   // 5d. FP64 Jacobi from there
@@ -496,6 +514,23 @@ __global__ void __launch_bounds__(256) k_rotate(const FragDesc *desc, const int2
   }
 }
 
+// Projections of the rotated block, per fragment: cout[i][k] = sum_j C[j][i] cin[j][k].  C maps the
+// filtered block to Psi = Y C, so <p_k|Psi_i> = sum_j C[j][i] <p_k|Y_j>.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rotate_proj(const FragDesc *desc, const T *C, const T *cin, T *cout) {
+  const FragDesc D = desc[blockIdx.x];
+  const int n = D.norb, A = D.natom;
+  const T *Cf = C + D.sub_off;
+  const T *ci = cin + D.c_off;
+  T *co = cout + D.c_off;
+  for (int t = threadIdx.x; t < n * A; t += 256) {
+    const int i = t / A, k = t - i * A;
+    T s = T(0);
+    for (int j = 0; j < n; ++j) s += Cf[j * n + i] * ci[j * A + k];
+    co[t] = s;
+  }
+}
+
 }  // namespace
 
 namespace dck {
@@ -519,7 +554,7 @@ int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
   const int np = c->layout.max_norb + (c->layout.max_norb & 1);
   const size_t sm = 5 * (size_t)np * (np + 1) * sizeof(double);
   DC_CUDA(dc_set_smem((const void *)k_subspace, sm));
-  const int fp64_sweeps = precision_bits == 32 ? 1 : 40;
+  const int fp64_sweeps = precision_bits == 32 ? 0 : 40;
   k_subspace<<<c->nfrag, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, c->d_eps,
                                        c->d_C64, precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags,
                                        fp64_sweeps);
@@ -539,6 +574,18 @@ int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s) {
   return DC_OK;
 }
 
+template <typename T>
+int launch_rotate_proj(dc_ctx *c, const T *cin, T *cout, cudaStream_t s) {
+  const T *C = nullptr;
+  if (sizeof(T) == 8) C = reinterpret_cast<const T *>(c->d_C64);
+  else C = reinterpret_cast<const T *>(c->d_C32);
+  k_rotate_proj<T><<<c->nfrag, 256, 0, s>>>(c->d_desc, C, cin, cout);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+
+template int launch_rotate_proj<double>(dc_ctx *, const double *, double *, cudaStream_t);
+template int launch_rotate_proj<float>(dc_ctx *, const float *, float *, cudaStream_t);
 template int launch_gram<double>(dc_ctx *, const double *, const double *, cudaStream_t);
 template int launch_gram<float>(dc_ctx *, const float *, const float *, cudaStream_t);
 template int launch_rotate<double>(dc_ctx *, const double *, double *, cudaStream_t);
