@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--sample-frags", type=int, default=8, help="fragments in the oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
+    p.add_argument("--shape", default=None,
+                   help="pin the FP32 stencil launch shape 'kind,threads,pairs' instead of autotuning")
     return p.parse_args()
 
 
@@ -242,6 +244,10 @@ def run_ours(args):
 
     cfg = workloads.make_config(args.workload, precision=args.precision)
     solver = DCSolver(cfg)
+    if args.shape:
+        kind, threads, pairs = (int(v) for v in args.shape.split(","))
+        if not solver.set_tuning("fp64" if args.precision == "fp64" else "fp32", kind, threads, pairs):
+            raise SystemExit(f"--shape {args.shape} does not fit this workload")
     t0 = time.perf_counter()
     solver.warmup()
     torch.cuda.synchronize()
