@@ -35,6 +35,8 @@ WORKLOAD_TEXT = {
                  "(22^3), 48 orbitals",
     "si_weak4096": "Si4096 weak-scaling cell (8^3 supercell, N(0,0.3)), 160^3 grid, 16^3 fragments of 10^3 core + 6 "
                    "(22^3), 48 orbitals",
+    "water": "water-like liquid, 1378 rigid H2O at 1 g/cm^3 (random sequential addition, O-O >= 2.5 A) in a 65.6 "
+             "bohr box, 192^3 grid, 12^3 fragments of 16^3 core + 8 (32^3), orbitals from each fragment's electrons",
 }
 
 

@@ -6,17 +6,23 @@
 // FP32 accuracy are accumulated in FP32 in tensor memory:
 //   S = hh + hm + mh + hl + lh + mm            (lh = (hl)^T by symmetry)
 //   A = h.zh + h.zm + m.zh + h.zl + l.zh + m.zm (z = HY split the same way)
-// Persistent CTAs (one per SM, 16 warps) walk the (fragment, 2048-point item) list.  Per 64-point
-// K-tile the CTA splits Y and HY into BF16 rows in shared memory (K-major, no-swizzle canonical
-// layout), and one thread issues three MMAs per 16-point K-step:
+// Persistent CTAs (one per SM, 16 warps) walk the (fragment, 2048-point item) list as a warp-
+// specialised pipeline.  Eleven converter warps copy 64-point K-tiles of Y and HY into a ring of
+// raw FP32 tiles in shared memory (cp.async, 16 bytes per copy, up to three tiles ahead; each
+// thread later converts exactly the chunks it copied, so a per-thread wait is enough), split them
+// into BF16 rows in a ring of shared-memory stages (K-major, no-swizzle canonical layout) and arrive
+// on the stage's `full` barrier; one thread of warp 15 waits on it and issues three MMAs per
+// 16-point K-step:
 //   D_S[128 x 3nb] = [Yh;Ym;Yl..] x [Yh|Ym|Yl]^T,  D_A[128 x 3nb] = [Yh;Ym;..] x [Zh|Zm|Zl]^T,
 //   D_L[128 x nb]  = [Yl;0] x [Zh]^T                                   (nb = n rounded up to 16)
-// with two K-tile stages in flight (mbarrier per stage) and the FP32 tiles of the next two K-tiles
-// already loading into registers (16-byte loads).  The FP32 accumulators in tensor memory are
-// drained every 256 points into FP32 sums in shared memory (the rounding of a tensor-memory sum
-// grows with its length), and each item leaves as one FP64 partial of S and A that the FP64
-// subspace kernel adds in a fixed order.  Every wait is bounded; on a timeout the kernel sets
-// DC_FLAG_TIMEOUT, frees its tensor memory and returns.
+// and commits them to the stage's `empty` barrier, which frees it for the converters.  The FP32
+// accumulators in tensor memory are drained every 256 points (the rounding of a tensor-memory sum
+// grows with its length): the MMA thread commits to `dready`, warps 11-14 add the accumulators
+// into FP32 sums in shared memory and arrive on `ddone`, and only then may the next group overwrite
+// them.  Each role has its own warps so that no role's registers spill.
+// Each item leaves as one FP64 partial of S and A that the FP64 subspace kernel adds in a fixed
+// order.  Every wait is bounded; after a timeout every later wait returns at once, the kernel sets
+// DC_FLAG_TIMEOUT, waits (bounded) for its committed MMAs, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -49,6 +55,26 @@ __device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t a, uint64_t b, ui
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Bounded wait; gives up at once when another thread of the CTA has already timed out.
+__device__ __forceinline__ bool mbar_wait_or(uint64_t *bar, uint32_t phase, volatile int *timed_out) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < DC_SPIN_LIMIT; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && *timed_out) return false;
+  }
+  *timed_out = 1;
+  return false;
 }
 
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
@@ -101,33 +127,51 @@ __device__ __forceinline__ float4 ld4g(const float *row, long long p, long long 
   return v;
 }
 
-constexpr int TSL = 2;  // float4 slots per thread per array: 64 rows x 16 float4 / 512 threads
-
-struct TileRegs {
-  float4 y[TSL], z[TSL];
-};
+constexpr int TCV = 352;  // converter threads (warps 0-10); warps 11-14 drain, warp 15 issues the MMAs
+constexpr int TSL = 3;    // float4 slots per converter thread per array: 64 rows x 16 float4 / 352
 
 // Slot idx of a K-tile -> (row i, 4-point quad kq): a warp covers 8 rows x 4 quads, so its 8-byte
 // shared-memory stores fill all 32 banks twice (16 rows apart in the canonical layout) instead of
-// piling 16 lanes onto one core-matrix column.
+// piling 16 lanes onto one core-matrix column.  Rows below n use slots idx < ((n + 7) / 8) * 128.
 __device__ __forceinline__ void tile_slot(int idx, int &i, int &kq) {
   i = ((idx >> 7) << 3) | (idx & 7);
   kq = (idx >> 3) & 15;
 }
 
-__device__ __forceinline__ void load_tile(TileRegs &r, const float *Yf, const float *Zf, long long P, int n,
-                                          long long pb, long long p1, bool vec) {
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+
+// Copy this thread's slots of the K-tile starting at point pb into one raw ring slot (raw[2][nslots]
+// float4: Y then HY).  Aligned whole chunks go by cp.async; ragged or unaligned ones by plain loads,
+// zero past p1.  Closes one copy group.
+__device__ __forceinline__ void fetch_tile(float4 *raw, int nslots, const float *Yf, const float *Zf, long long P,
+                                           int n, long long pb, long long p1, bool vec) {
 #pragma unroll
   for (int j = 0; j < TSL; ++j) {
-    const int idx = threadIdx.x + j * TNT;
+    const int idx = threadIdx.x + j * TCV;
     int i, kq;
     tile_slot(idx, i, kq);
-    if (i < n) {
+    if (idx < 1024 && i < n) {
       const long long p = pb + 4 * kq;
-      r.y[j] = ld4g(Yf + (long long)i * P, p, p1, vec);
-      r.z[j] = ld4g(Zf + (long long)i * P, p, p1, vec);
+      const float *yr = Yf + (long long)i * P, *zr = Zf + (long long)i * P;
+      if (vec && p + 3 < p1) {
+        cp_async16(&raw[idx], yr + p);
+        cp_async16(&raw[nslots + idx], zr + p);
+      } else {
+        raw[idx] = ld4g(yr, p, p1, vec);
+        raw[nslots + idx] = ld4g(zr, p, p1, vec);
+      }
     }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait until at most `pending` of this thread's copy groups are still in flight.
+__device__ __forceinline__ void cp_async_wait(int pending) {
+  if (pending <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else asm volatile("cp.async.wait_group 2;" ::: "memory");
 }
 
 // Split 4 consecutive-point values of row i into h/m/l rows (base row offsets 0, nb, 2 nb).
@@ -140,43 +184,25 @@ __device__ __forceinline__ void store_split(unsigned char *st, int i, int k, int
   *reinterpret_cast<uint2 *>(st + toff(2 * nb + i, k, ks)) = make_uint2(l0, l1);
 }
 
-__device__ __forceinline__ void convert_tile(const TileRegs &r, unsigned char *ys, unsigned char *zs, int n, int nb,
-                                             int ksY, int ksZ) {
+__device__ __forceinline__ void convert_tile(const float4 *raw, int nslots, unsigned char *ys, unsigned char *zs,
+                                             int n, int nb, int ksY, int ksZ) {
 #pragma unroll
   for (int j = 0; j < TSL; ++j) {
-    const int idx = threadIdx.x + j * TNT;
+    const int idx = threadIdx.x + j * TCV;
     int i, kq;
     tile_slot(idx, i, kq);
-    if (i < n) {
+    if (idx < 1024 && i < n) {
       const int k = 4 * kq;
-      store_split(ys, i, k, ksY, nb, r.y[j]);
-      store_split(zs, i, k, ksZ, nb, r.z[j]);
+      store_split(ys, i, k, ksY, nb, raw[idx]);
+      store_split(zs, i, k, ksZ, nb, raw[nslots + idx]);
     }
   }
-}
-
-struct GramPipe {
-  uint32_t phase[2];
-  int commits[2], waits[2];
-};
-
-// Wait until every committed MMA group has completed.
-__device__ __forceinline__ bool wait_all(GramPipe &g, uint64_t *mbar) {
-  bool ok = true;
-  for (int s = 0; s < 2; ++s) {
-    while (g.commits[s] > g.waits[s]) {
-      if (!mbar_wait(&mbar[s], g.phase[s])) ok = false;
-      g.phase[s] ^= 1u;
-      ++g.waits[s];
-    }
-  }
-  return ok;
 }
 
 // Adds the tensor-memory accumulators into the FP32 sums: rows r < n (h rows) give
 // P1S += hh + hm + hl, HL += hl, P1A += h.zh + h.zm + h.zl + l.zh; rows nb <= r < nb + n (m rows)
-// give P2S += mh + mm, P2A += m.zh + m.zm.  Warp w reads lanes 32 (w % 4) .. +31 and the 8-column
-// groups g with g % 4 == w / 4.
+// give P2S += mh + mm, P2A += m.zh + m.zm.  Run by warps 11-14: warp w reads lanes 32 (w % 4) .. +31
+// and every 8-column group.
 __device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int n, int nb, float *acc) {
   const int ld = n + 1;  // odd row stride: the 32 lanes (rows) of a warp hit 32 different banks
   float *P1S = acc, *HL = acc + n * ld, *P1A = HL + n * ld, *P2S = P1A + n * ld, *P2A = P2S + n * ld;
@@ -185,7 +211,7 @@ __device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const bool own = r < n, mrow = (r >= nb && r < nb + n);
   const int i = own ? r : r - nb;
-  for (int cg = 8 * (warp >> 2); cg < nb; cg += 32) {
+  for (int cg = 0; cg < nb; cg += 8) {
     float sh[8], sm_[8], sl[8], ah[8], am[8], al[8], ll[8];
     tmem_ld8(tS + lane_base + cg, sh);
     tmem_ld8(tS + lane_base + nb + cg, sm_);
@@ -211,17 +237,24 @@ __device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int
   }
 }
 
+constexpr int TDW = 128;  // drain threads (warps 11-14)
+
 __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const int2 *gitems, int n_items,
-                                                    const long long *goff, int chunk, int nmax, const float *Y,
-                                                    const float *HY, double *out, unsigned *flags) {
+                                                    const long long *goff, int chunk, int nmax, int nstages,
+                                                    int nraw, const float *Y, const float *HY, double *out,
+                                                    unsigned *flags) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[3], empty[3], dready, ddone;
   __shared__ int timed_out;
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const bool mma_warp = warp == TNT / 32 - 1;
   const int nbmax = (nmax + 15) & ~15;
   const int stage_max = (2 * nbmax + 128) * TKT * 2 + 3 * nbmax * TKT * 2;
-  float *acc = reinterpret_cast<float *>(sm + 2 * stage_max);  // [5][n][n + 1]
+  const int nslots = ((nmax + 7) / 8) * 128;                          // raw float4 slots per array
+  float4 *rawring = reinterpret_cast<float4 *>(sm + nstages * stage_max);  // [nraw][2][nslots]
+  float *acc = reinterpret_cast<float *>(rawring + (size_t)nraw * 2 * nslots);  // [5][n][n + 1]
 
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
@@ -230,19 +263,24 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   }
   if (tid == 0) {
     timed_out = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar[1])), "r"(1));
+    for (int k = 0; k < 3; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[k])), "r"(TCV));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[k])), "r"(1));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&dready)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ddone)), "r"(TDW));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tslot;
-  GramPipe g{{0u, 0u}, {0, 0}, {0, 0}};
-  int gt = 0;         // K-tiles issued by this CTA (selects the stage)
+  int gt = 0;     // K-tiles this CTA has passed through the ring (stage gt % nstages, use gt / nstages)
+  int gd = 0;     // drains done by this CTA (phase of dready / ddone)
   int prev_n = -1;
+  int commits = 0;  // MMA groups committed by the MMA thread (tracked for the final wait)
 
-  for (int item = blockIdx.x; item < n_items && !timed_out; item += gridDim.x) {
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int2 it = gitems[item];
     const int f = it.x, ch = it.y;
     const FragDesc D = desc[f];
@@ -260,43 +298,67 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
     const bool vec = ((P | D.psi_off) & 3) == 0;
     const uint32_t tS = tbase, tA = tbase + 3 * nb, tL = tbase + 6 * nb;
     const uint32_t iS = idesc_bf16(128, 3 * nb), iL = idesc_bf16(128, nb);
+    const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
 
-    // stage padding rows must be zero for this orbital count (no MMA is in flight here)
+    // item start (the whole CTA is here, no MMA in flight): stage padding rows zero for this orbital
+    // count, FP32 sums zero
     if (n != prev_n) {
-      for (int t = tid; t < 2 * stage_bytes / 16; t += TNT) reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
+      for (int t = tid; t < nstages * stage_bytes / 16; t += TNT)
+        reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
       prev_n = n;
     }
     for (int t = tid; t < 5 * n * (n + 1); t += TNT) acc[t] = 0.f;
-    const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
-    TileRegs ra, rb;
-    load_tile(ra, Yf, Zf, P, n, p0, p1, vec);
-    if (ntiles > 1) load_tile(rb, Yf, Zf, P, n, p0 + TKT, p1, vec);
     __syncthreads();
+    if (timed_out) break;
 
-    for (int t = 0; t < ntiles; ++t) {
-      const int s = gt & 1;
-      if (g.commits[s] > g.waits[s]) {
-        if (!mbar_wait(&mbar[s], g.phase[s])) timed_out = 1;
-        g.phase[s] ^= 1u;
-        ++g.waits[s];
+    if (tid < TCV) {
+      // ---- converters: tile t's raw copy was issued nraw tiles earlier into ring slot t % nraw ----
+      for (int r = 0; r < nraw; ++r) {
+        if (r < ntiles) fetch_tile(rawring + (size_t)r * 2 * nslots, nslots, Yf, Zf, P, n, p0 + (long long)r * TKT,
+                                   p1, vec);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
       }
-      __syncthreads();
-      if (timed_out) break;
-      unsigned char *ys = sm + s * stage_bytes;
-      unsigned char *zs = ys + ybytes;
-      // the registers of tile t hold ra (even t) or rb (odd t); refill them with tile t + 2
-      if ((t & 1) == 0) {
-        convert_tile(ra, ys, zs, n, nb, ksY, ksZ);
-        if (t + 2 < ntiles) load_tile(ra, Yf, Zf, P, n, p0 + (long long)(t + 2) * TKT, p1, vec);
-      } else {
-        convert_tile(rb, ys, zs, n, nb, ksY, ksZ);
-        if (t + 2 < ntiles) load_tile(rb, Yf, Zf, P, n, p0 + (long long)(t + 2) * TKT, p1, vec);
+      for (int t = 0; t < ntiles; ++t, ++gt) {
+        const int s = gt % nstages;
+        const uint32_t use = (uint32_t)(gt / nstages);
+        float4 *raw = rawring + (size_t)(t % nraw) * 2 * nslots;
+        cp_async_wait(nraw - 1);  // this thread's chunks of tile t have landed
+        if (!mbar_wait_or(&empty[s], (use & 1u) ^ 1u, &timed_out)) break;
+        unsigned char *ys = sm + s * stage_bytes;
+        unsigned char *zs = ys + ybytes;
+        convert_tile(raw, nslots, ys, zs, n, nb, ksY, ksZ);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&full[s]);
+        // the slot's values are in the stage now: refill it with tile t + nraw
+        if (t + nraw < ntiles)
+          fetch_tile(raw, nslots, Yf, Zf, P, n, p0 + (long long)(t + nraw) * TKT, p1, vec);
+        else
+          asm volatile("cp.async.commit_group;" ::: "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
+      cp_async_wait(0);
+    } else if (!mma_warp) {
+      // ---- drain warps ----
+      const int ngroups = (ntiles + TDR - 1) / TDR;
+      for (int g = 0; g < ngroups; ++g, ++gd) {
+        if (!mbar_wait_or(&dready, (uint32_t)(gd & 1), &timed_out)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        drain(tS, tA, tL, n, nb, acc);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        mbar_arrive(&ddone);
+      }
+    } else if ((tid & 31) == 0) {
+      // ---- MMA issuer ----
+      for (int t = 0; t < ntiles; ++t, ++gt) {
+        const int s = gt % nstages;
+        const uint32_t use = (uint32_t)(gt / nstages);
+        if (t % TDR == 0 && t > 0) {
+          // the previous group's accumulators must be drained before they are overwritten
+          if (!mbar_wait_or(&ddone, (uint32_t)((gd - 1) & 1), &timed_out)) break;
+        }
+        if (!mbar_wait_or(&full[s], use & 1u, &timed_out)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        unsigned char *ys = sm + s * stage_bytes;
+        unsigned char *zs = ys + ybytes;
         const uint32_t ya = su32(ys), za = su32(zs);
 #pragma unroll
         for (int kk = 0; kk < TKT / 16; ++kk) {
@@ -309,21 +371,21 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
           mma_bf16(tL, aL, bZ, iL, accum);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            su32(&mbar[s])));
+            su32(&empty[s])));
+        ++commits;
+        if (t % TDR == TDR - 1 || t == ntiles - 1) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(&dready)));
+          ++gd;
+        }
       }
-      ++g.commits[s];
-      ++gt;
-      if (t % TDR == TDR - 1 || t == ntiles - 1) {
-        if (!wait_all(g, mbar)) timed_out = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        __syncthreads();
-        if (timed_out) break;
-        drain(tS, tA, tL, n, nb, acc);
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-      }
+      // the item's last drain must be complete before the partial is read
+      if (!timed_out) mbar_wait_or(&ddone, (uint32_t)((gd - 1) & 1), &timed_out);
+    } else {
+      // lanes 1-31 of the MMA warp: no role
     }
+    // every role counted the same tiles and drains
+    __syncthreads();
     if (timed_out) break;
     // the item's partial sums, each element once: S = P1S + P2S + HL^T, A = P1A + P2A
     const int ld = n + 1;
@@ -338,8 +400,12 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
     __syncthreads();
   }
   if (timed_out && tid == 0) atomicOr(flags, DC_FLAG_TIMEOUT);
-  // every committed MMA group has completed (or timed out) before the tensor memory is freed
-  if (!wait_all(g, mbar) && tid == 0) atomicOr(flags, DC_FLAG_TIMEOUT);
+  // the MMA thread waits (bounded) for everything it committed before the tensor memory is freed
+  if (mma_warp && (tid & 31) == 0 && commits > 0) {
+    const int s = (gt - 1) % nstages;
+    const uint32_t use = (uint32_t)((gt - 1) / nstages);
+    if (!mbar_wait(&empty[s], use & 1u)) atomicOr(flags, DC_FLAG_TIMEOUT);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -358,11 +424,29 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     return DC_ERR_ARG;
   }
   const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
-  const size_t sm = 2 * stage + 5 * (size_t)nmax * (nmax + 1) * sizeof(float);
+  const size_t rawslot = 2 * (size_t)((nmax + 7) / 8) * 128 * sizeof(float4);
+  const size_t accb = 5 * (size_t)nmax * (nmax + 1) * sizeof(float);
+  // deepest (BF16 stages, raw tiles) pair that fits: two stages keep the MMA and the conversion
+  // overlapped, the raw ring keeps up to three tiles of loads in flight
+  int nstages = 0, nraw = 0;
+  for (int ns : {2, 1}) {
+    for (int nr : {3, 2, 1})
+      if (ns * stage + nr * rawslot + accb + 1024 <= 227 * 1024) {
+        nstages = ns;
+        nraw = nr;
+        break;
+      }
+    if (nstages) break;
+  }
+  if (!nstages) {
+    dc_set_error("mixed-precision Gram: tiles exceed shared memory");
+    return DC_ERR_ARG;
+  }
+  const size_t sm = nstages * stage + nraw * rawslot + accb;
   DC_CUDA(dc_set_smem((const void *)k_gram_tc, sm));
   const int grid = std::min(c->n_gram_items, c->sm_count);
   k_gram_tc<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,
-                                  Y, HY, c->d_gram, c->d_flags);
+                                  nstages, nraw, Y, HY, c->d_gram, c->d_flags);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

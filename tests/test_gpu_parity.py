@@ -281,6 +281,26 @@ def test_scf_kerker_mixing_fp64():
     assert np.max(np.abs(rin - st.rho_in.reshape(-1))) < 1e-9 * np.max(np.abs(st.rho_in))
 
 
+def test_fixed_density_dc_fp64():
+    """The paper's fixed-density DC (mix_alpha = 0): the input density is never changed and each step's
+    energy, chemical potential and residual match the oracle's."""
+    cfg = CASES["periodic"](precision="fp64", mix_alpha=0.0, n_warmup=3)
+    st = oracle_state(cfg)
+    st.warmup()
+    ref = [st.scf_step() for _ in range(3)]
+    natom = len(cfg["pos"])
+    with _solver(cfg) as s:
+        s.warmup()
+        _, rho0 = s.initial()
+        rho = rho0.clone()
+        for k, r in enumerate(ref):
+            got = s.scf_step(rho)
+            assert abs(got["E"] - r["E"]) / natom < 1e-9, (k, got["E"], r["E"])
+            assert abs(got["mu"] - r["mu"]) < 1e-8
+            assert abs(got["drho"] - r["drho"]) < 1e-8
+        assert torch.equal(rho, rho0)
+
+
 def test_scf_step_host_buffers_match_device_buffers():
     cfg = CASES["uneven"](precision="fp32", n_warmup=3)
     res = []
