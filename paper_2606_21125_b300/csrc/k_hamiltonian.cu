@@ -567,7 +567,6 @@ struct PairSmem {
   int2 *box;
   int *rb;
   float *red;  // [2][NT / 32] (at most 2 x 32 floats)
-  float *pf;   // prefetch ring of k_hpair
 };
 
 __device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int Ey, int Ez, int A, int maxent,
@@ -586,14 +585,8 @@ __device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int E
   m.box = reinterpret_cast<int2 *>(m.recky + ((nrec * maxent + 1) & ~1));
   m.rb = reinterpret_cast<int *>(m.box + A);
   m.red = reinterpret_cast<float *>(m.rb + Ez * Ey + 1);
-  off = (size_t)(reinterpret_cast<unsigned char *>(m.red + 2 * 32) - raw);
-  m.pf = reinterpret_cast<float *>(raw + ((off + 15) & ~(size_t)15));
   return m;
 }
-
-// Per-thread prefetch ring of k_hpair: 3 planes x PP pairs x 6 values (V at 2 points, Y_{k-1} at
-// 2 points x 2 orbitals), laid out [plane slot][pair][value][thread].
-constexpr int kPfVals = 6;
 
 size_t pair_smem_bytes(int Ex, int Ey, int Ez, int A, int maxent, int nrec, bool halo, int NT, int PP = 0) {
   const int pitch = (Ex + 9) & ~1, pitch2 = (Ex + 1) & ~1;
@@ -602,8 +595,7 @@ size_t pair_smem_bytes(int Ex, int Ey, int Ez, int A, int maxent, int nrec, bool
   size_t b = (n2 * sizeof(float2) + 15) & ~(size_t)15;
   b += (size_t)nrec * maxent * sizeof(float4) + (size_t)((nrec * maxent + 1) & ~1) * sizeof(int) +
        (size_t)A * sizeof(int2) + (size_t)(Ez * Ey + 1) * sizeof(int) + 2 * 32 * sizeof(float);
-  b = (b + 15) & ~(size_t)15;
-  b += 3 * (size_t)PP * kPfVals * NT * sizeof(float);
+  (void)PP;
   return b + 64;
 }
 
@@ -708,14 +700,6 @@ __device__ __forceinline__ void pair_prefetch(const int2 *ent, int ne, int2 (&pr
   }
 }
 
-__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
-
 // Per-CTA constants of k_hpair.
 template <int PP>
 struct HPair {
@@ -732,39 +716,14 @@ struct HPair {
   bool valid[PP], v1[PP];
 };
 
-// Issue the asynchronous copies of plane zz's V and Y_{k-1} values of this thread's pairs into ring
-// slot `slot` (each thread reads back only its own values, so no barrier is involved), and close the
-// copy group (an empty group past the last plane keeps the group count uniform).
-template <int NT, int PP>
-__device__ __forceinline__ void hpair_prefetch(const HPair<PP> &H, float *pf, int zz, int slot) {
-  if (zz < H.Ez) {
-    const int oh = zz * H.plane;
-#pragma unroll
-    for (int r = 0; r < PP; ++r) {
-      if (!H.valid[r]) continue;
-      float *d = pf + ((slot * PP + r) * kPfVals) * NT + threadIdx.x;
-      const float *v = H.vf + oh + H.t0[r];
-      cp_async4(d, v);
-      if (H.v1[r]) cp_async4(d + NT, v + 1);
-      if (H.use_prev) {
-        const float *p = H.yprev + oh + H.t0[r];
-        cp_async4(d + 2 * NT, p);
-        cp_async4(d + 3 * NT, p + H.o1off);
-        if (H.v1[r]) {
-          cp_async4(d + 4 * NT, p + 1);
-          cp_async4(d + 5 * NT, p + H.o1off + 1);
-        }
-      }
-    }
-  }
-  cp_async_commit();
-}
-
 // One plane z of k_hpair.  ZI = z mod 9 names the register slots: q[r][(ZI + k) % 9] holds plane
 // z - 4 + k, so the column advances without moving registers (the kernel unrolls z by 9).
+// vv/pvv hold this plane's V (2 points) and Y_{k-1} (2 points x 2 orbitals) per pair, loaded one
+// plane earlier; the plane refills them for plane z + 1 right after reading them.
 template <int NT, int PP, bool ISO, int ZI>
 __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO> &K, const PairSmem &m, int maxent,
-                                            float4 (&q)[PP][9], int2 (&pre)[2], float2 &dot, int z, int b3) {
+                                            float4 (&q)[PP][9], float2 (&vv)[PP], float4 (&pvv)[PP],
+                                            int2 (&pre)[2], float2 &dot, int z, int b3) {
   float2 *P0 = m.pin + (z & 1) * H.pplane;
   // centre values of plane z (and the periodic halo)
 #pragma unroll
@@ -809,9 +768,6 @@ __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO>
   }
   const int zoff = zn * H.plane;
   const int oh = z * H.plane;
-  // V and Y_{k-1} of plane z + 2 start loading; plane z's copies (two groups back) must be complete
-  hpair_prefetch<NT, PP>(H, m.pf, z + 2, (ZI + 2) % 3);
-  cp_async_wait2();
 #pragma unroll
   for (int r = 0; r < PP; ++r) {
     if (!H.valid[r]) continue;
@@ -821,11 +777,17 @@ __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO>
     const float *pn = H.yin + zoff + t0;
     const float4 nxt = make_float4(zin ? pn[0] : 0.f, zin ? pn[H.o1off] : 0.f, (zin && v1) ? pn[1] : 0.f,
                                    (zin && v1) ? pn[H.o1off + 1] : 0.f);
-    const float *ps = m.pf + (((ZI % 3) * PP + r) * kPfVals) * NT + threadIdx.x;
-    const float va = fmaf(H.alpha, ps[0], H.vsh);
-    const float vb = v1 ? fmaf(H.alpha, ps[NT], H.vsh) : 0.f;
-    float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (H.use_prev) pv = make_float4(ps[2 * NT], ps[3 * NT], v1 ? ps[4 * NT] : 0.f, v1 ? ps[5 * NT] : 0.f);
+    const float va = fmaf(H.alpha, vv[r].x, H.vsh);
+    const float vb = v1 ? fmaf(H.alpha, vv[r].y, H.vsh) : 0.f;
+    const float4 pv = pvv[r];
+    if (z + 1 < H.Ez) {
+      const int t1 = oh + H.plane + t0;
+      vv[r] = make_float2(H.vf[t1], v1 ? H.vf[t1 + 1] : 0.f);
+      if (H.use_prev) {
+        const float *pp = H.yprev + t1;
+        pvv[r] = make_float4(pp[0], pp[H.o1off], v1 ? pp[1] : 0.f, v1 ? pp[H.o1off + 1] : 0.f);
+      }
+    }
     const float2 *co = P0 + (y + 4) * H.pitch + x + 4;
     float2 row[10];
 #pragma unroll
@@ -985,8 +947,20 @@ __global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
                             i1k ? pz[H.o1off + 1] : 0.f);
     }
   }
-  hpair_prefetch<NT, PP>(H, m.pf, 0, 0);
-  hpair_prefetch<NT, PP>(H, m.pf, 1, 1);
+  float2 vv[PP];
+  float4 pvv[PP];
+#pragma unroll
+  for (int r = 0; r < PP; ++r) {
+    vv[r] = make_float2(0.f, 0.f);
+    pvv[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!H.valid[r]) continue;
+    const int t0 = H.t0[r];
+    vv[r] = make_float2(H.vf[t0], H.v1[r] ? H.vf[t0 + 1] : 0.f);
+    if (H.use_prev) {
+      const float *pp = H.yprev + t0;
+      pvv[r] = make_float4(pp[0], pp[H.o1off], H.v1[r] ? pp[1] : 0.f, H.v1[r] ? pp[H.o1off + 1] : 0.f);
+    }
+  }
   __syncthreads();
   int2 pre[2];
   pair_prefetch<NT>(H.ent, m.rb[H.Ey], pre);
@@ -994,23 +968,23 @@ __global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
   float2 dot = f2(0.f, 0.f);
   const int maxent = a.maxent;
   for (int z0 = 0; z0 < H.Ez; z0 += 9) {
-    hpair_plane<NT, PP, ISO, 0>(H, K, m, maxent, q, pre, dot, z0, 0);
+    hpair_plane<NT, PP, ISO, 0>(H, K, m, maxent, q, vv, pvv, pre, dot, z0, 0);
     if (z0 + 1 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 1>(H, K, m, maxent, q, pre, dot, z0 + 1, 1);
+    hpair_plane<NT, PP, ISO, 1>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 1, 1);
     if (z0 + 2 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 2>(H, K, m, maxent, q, pre, dot, z0 + 2, 2);
+    hpair_plane<NT, PP, ISO, 2>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 2, 2);
     if (z0 + 3 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 3>(H, K, m, maxent, q, pre, dot, z0 + 3, 0);
+    hpair_plane<NT, PP, ISO, 3>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 3, 0);
     if (z0 + 4 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 4>(H, K, m, maxent, q, pre, dot, z0 + 4, 1);
+    hpair_plane<NT, PP, ISO, 4>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 4, 1);
     if (z0 + 5 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 5>(H, K, m, maxent, q, pre, dot, z0 + 5, 2);
+    hpair_plane<NT, PP, ISO, 5>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 5, 2);
     if (z0 + 6 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 6>(H, K, m, maxent, q, pre, dot, z0 + 6, 0);
+    hpair_plane<NT, PP, ISO, 6>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 6, 0);
     if (z0 + 7 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 7>(H, K, m, maxent, q, pre, dot, z0 + 7, 1);
+    hpair_plane<NT, PP, ISO, 7>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 7, 1);
     if (z0 + 8 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 8>(H, K, m, maxent, q, pre, dot, z0 + 8, 2);
+    hpair_plane<NT, PP, ISO, 8>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 8, 2);
   }
   if (H.proj) {
     __syncthreads();
