@@ -55,7 +55,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="si512", choices=sorted(WORKLOAD_TEXT))
-    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp32", "fp64", "mixed"],
+                   help="mixed (default): FP32 stencil, 3xBF16 tensor-core Gram, FP64 subspace and Fermi level")
     p.add_argument("--sample-frags", type=int, default=8, help="fragments in the oracle's timed sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
