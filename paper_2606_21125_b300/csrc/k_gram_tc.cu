@@ -7,7 +7,7 @@
 //   S = hh + hm + mh + hl + lh + mm            (lh = (hl)^T by symmetry)
 //   A = h.zh + h.zm + m.zh + h.zl + l.zh + m.zm (z = HY split the same way)
 // Persistent CTAs (one per SM, 16 warps) walk the (fragment, 2048-point item) list as a warp-
-// specialised pipeline.  Eleven converter warps copy 64-point K-tiles of Y and HY into a ring of
+// specialised pipeline.  Seven converter warps copy 64-point K-tiles of Y and HY into a ring of
 // raw FP32 tiles in shared memory (cp.async, 16 bytes per copy, up to three tiles ahead; each
 // thread later converts exactly the chunks it copied, so a per-thread wait is enough), split them
 // into BF16 rows in a ring of shared-memory stages (K-major, no-swizzle canonical layout) and arrive
@@ -17,9 +17,10 @@
 //   D_L[128 x nb]  = [Yl;0] x [Zh]^T                                   (nb = n rounded up to 16)
 // and commits them to the stage's `empty` barrier, which frees it for the converters.  The FP32
 // accumulators in tensor memory are drained every 256 points (the rounding of a tensor-memory sum
-// grows with its length): the MMA thread commits to `dready`, warps 11-14 add the accumulators
-// into FP32 sums in shared memory and arrive on `ddone`, and only then may the next group overwrite
-// them.  Each role has its own warps so that no role's registers spill.
+// grows with its length): the MMA thread commits to `dready`, warps 7-14 add the accumulators into
+// FP32 sums kept in their registers (two warps per tensor-memory lane group, half the columns each)
+// and arrive on `ddone`, and only then may the next group overwrite them.  The register sums go to
+// shared memory once per item.  Each role has its own warps.
 // Each item leaves as one FP64 partial of S and A that the FP64 subspace kernel adds in a fixed
 // order.  Every wait is bounded; after a timeout every later wait returns at once, the kernel sets
 // DC_FLAG_TIMEOUT, waits (bounded) for its committed MMAs, frees its tensor memory and returns.
@@ -127,8 +128,8 @@ __device__ __forceinline__ float4 ld4g(const float *row, long long p, long long 
   return v;
 }
 
-constexpr int TCV = 352;  // converter threads (warps 0-10); warps 11-14 drain, warp 15 issues the MMAs
-constexpr int TSL = 3;    // float4 slots per converter thread per array: 64 rows x 16 float4 / 352
+constexpr int TCV = 224;  // converter threads (warps 0-6); warps 7-14 drain, warp 15 issues the MMAs
+constexpr int TSL = 5;    // float4 slots per converter thread per array: 64 rows x 16 float4 / 224
 
 // Slot idx of a K-tile -> (row i, 4-point quad kq): a warp covers 8 rows x 4 quads, so its 8-byte
 // shared-memory stores fill all 32 banks twice (16 rows apart in the canonical layout) instead of
@@ -199,46 +200,84 @@ __device__ __forceinline__ void convert_tile(const float4 *raw, int nslots, unsi
   }
 }
 
-// Adds the tensor-memory accumulators into the FP32 sums: rows r < n (h rows) give
-// P1S += hh + hm + hl, HL += hl, P1A += h.zh + h.zm + h.zl + l.zh; rows nb <= r < nb + n (m rows)
-// give P2S += mh + mm, P2A += m.zh + m.zm.  Run by warps 11-14: warp w reads lanes 32 (w % 4) .. +31
-// and every 8-column group.
-__device__ __forceinline__ void drain(uint32_t tS, uint32_t tA, uint32_t tL, int n, int nb, float *acc) {
-  const int ld = n + 1;  // odd row stride: the 32 lanes (rows) of a warp hit 32 different banks
-  float *P1S = acc, *HL = acc + n * ld, *P1A = HL + n * ld, *P2S = P1A + n * ld, *P2A = P2S + n * ld;
+// Drain warps 7-14: warp w reads tensor-memory lanes 32 (w % 4) .. +31 (its rows r) and the
+// 8-column groups 2 j + h (h = (w - 7) / 4, j < NG).  Rows r < n (h rows) keep P1S = hh + hm + hl,
+// HL = hl, P1A = h.zh + h.zm + h.zl + l.zh; rows nb <= r < nb + n (m rows) keep P2S = mh + mm and
+// P2A = m.zh + m.zm; columns past n and other rows add nothing.
+template <int NG>
+struct DrainRegs {
+  float a0[8 * NG], a1[8 * NG], a2[8 * NG];
+};
+
+template <int NG>
+__device__ __forceinline__ void drain_add(DrainRegs<NG> &R, uint32_t tS, uint32_t tA, uint32_t tL, int n, int nb) {
   const int warp = threadIdx.x >> 5;
+  const int half = (warp - 7) >> 2;
   const int r = 32 * (warp & 3) + (threadIdx.x & 31);
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   const bool own = r < n, mrow = (r >= nb && r < nb + n);
-  const int i = own ? r : r - nb;
-  for (int cg = 0; cg < nb; cg += 8) {
-    float sh[8], sm_[8], sl[8], ah[8], am[8], al[8], ll[8];
-    tmem_ld8(tS + lane_base + cg, sh);
-    tmem_ld8(tS + lane_base + nb + cg, sm_);
-    tmem_ld8(tS + lane_base + 2 * nb + cg, sl);
-    tmem_ld8(tA + lane_base + cg, ah);
-    tmem_ld8(tA + lane_base + nb + cg, am);
-    tmem_ld8(tA + lane_base + 2 * nb + cg, al);
-    tmem_ld8(tL + lane_base + cg, ll);
+#pragma unroll
+  for (int j = 0; j < NG; ++j) {
+    const int cg = 8 * (2 * j + half);
+    if (cg >= nb) continue;  // warp-uniform
+    float x0[8], x1[8], x2[8];
+    tmem_ld8(tS + lane_base + cg, x0);
+    tmem_ld8(tS + lane_base + nb + cg, x1);
+    tmem_ld8(tS + lane_base + 2 * nb + cg, x2);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      const int j = cg + e;
-      if (j < n) {
-        if (own) {
-          P1S[i * ld + j] += sh[e] + sm_[e] + sl[e];
-          HL[i * ld + j] += sl[e];
-          P1A[i * ld + j] += ah[e] + am[e] + al[e] + ll[e];
-        } else if (mrow) {
-          P2S[i * ld + j] += sh[e] + sm_[e];
-          P2A[i * ld + j] += ah[e] + am[e];
-        }
+      if (own) {
+        R.a0[8 * j + e] += x0[e] + x1[e] + x2[e];
+        R.a1[8 * j + e] += x2[e];
+      } else if (mrow) {
+        R.a0[8 * j + e] += x0[e] + x1[e];
+      }
+    }
+    float y0[8], y1[8], y2[8], y3[8];
+    tmem_ld8(tA + lane_base + cg, y0);
+    tmem_ld8(tA + lane_base + nb + cg, y1);
+    tmem_ld8(tA + lane_base + 2 * nb + cg, y2);
+    tmem_ld8(tL + lane_base + cg, y3);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (own) R.a2[8 * j + e] += y0[e] + y1[e] + y2[e] + y3[e];
+      else if (mrow) R.a1[8 * j + e] += y0[e] + y1[e];
+    }
+  }
+}
+
+// The item's register sums to shared memory (row stride n + 1), each element by its one owner.
+template <int NG>
+__device__ __forceinline__ void drain_store(const DrainRegs<NG> &R, int n, int nb, float *acc) {
+  const int ld = n + 1;
+  float *P1S = acc, *HL = acc + n * ld, *P1A = HL + n * ld, *P2S = P1A + n * ld, *P2A = P2S + n * ld;
+  const int warp = threadIdx.x >> 5;
+  const int half = (warp - 7) >> 2;
+  const int r = 32 * (warp & 3) + (threadIdx.x & 31);
+  const bool own = r < n, mrow = (r >= nb && r < nb + n);
+  const int i = own ? r : r - nb;
+#pragma unroll
+  for (int j = 0; j < NG; ++j) {
+    const int cg = 8 * (2 * j + half);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = cg + e;
+      if (c >= n) continue;
+      if (own) {
+        P1S[i * ld + c] = R.a0[8 * j + e];
+        HL[i * ld + c] = R.a1[8 * j + e];
+        P1A[i * ld + c] = R.a2[8 * j + e];
+      } else if (mrow) {
+        P2S[i * ld + c] = R.a0[8 * j + e];
+        P2A[i * ld + c] = R.a1[8 * j + e];
       }
     }
   }
 }
 
-constexpr int TDW = 128;  // drain threads (warps 11-14)
+constexpr int TDW = 256;  // drain threads (warps 7-14)
 
+template <int NG>
 __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const int2 *gitems, int n_items,
                                                     const long long *goff, int chunk, int nmax, int nstages,
                                                     int nraw, const float *Y, const float *HY, double *out,
@@ -307,7 +346,6 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
       prev_n = n;
     }
-    for (int t = tid; t < 5 * n * (n + 1); t += TNT) acc[t] = 0.f;
     __syncthreads();
     if (timed_out) break;
 
@@ -338,14 +376,18 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
       cp_async_wait(0);
     } else if (!mma_warp) {
       // ---- drain warps ----
+      DrainRegs<NG> R;
+#pragma unroll
+      for (int k = 0; k < 8 * NG; ++k) R.a0[k] = R.a1[k] = R.a2[k] = 0.f;
       const int ngroups = (ntiles + TDR - 1) / TDR;
       for (int g = 0; g < ngroups; ++g, ++gd) {
         if (!mbar_wait_or(&dready, (uint32_t)(gd & 1), &timed_out)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        drain(tS, tA, tL, n, nb, acc);
+        drain_add<NG>(R, tS, tA, tL, n, nb);
         asm volatile("tcgen05.fence::before_thread_sync;");
         mbar_arrive(&ddone);
       }
+      drain_store<NG>(R, n, nb, acc);
     } else if ((tid & 31) == 0) {
       // ---- MMA issuer ----
       for (int t = 0; t < ntiles; ++t, ++gt) {
@@ -443,12 +485,22 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     return DC_ERR_ARG;
   }
   const size_t sm = nstages * stage + nraw * rawslot + accb;
-  DC_CUDA(dc_set_smem((const void *)k_gram_tc, sm));
   const int grid = std::min(c->n_gram_items, c->sm_count);
-  k_gram_tc<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,
-                                  nstages, nraw, Y, HY, c->d_gram, c->d_flags);
-  DC_CUDA(cudaGetLastError());
-  return DC_OK;
+  // column groups per drain warp: nb / 8 groups split over two warps per lane group
+  const int ng = (nb / 8 + 1) / 2;
+  auto run = [&](auto kern) -> int {
+    DC_CUDA(dc_set_smem((const void *)kern, sm));
+    kern<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,
+                               nstages, nraw, Y, HY, c->d_gram, c->d_flags);
+    DC_CUDA(cudaGetLastError());
+    return DC_OK;
+  };
+  switch (ng) {
+    case 1: return run(k_gram_tc<1>);
+    case 2: return run(k_gram_tc<2>);
+    case 3: return run(k_gram_tc<3>);
+    default: return run(k_gram_tc<4>);
+  }
 }
 
 }  // namespace dck
