@@ -335,6 +335,7 @@ def run_ours(args):
     stencil_name = ("k_hpair (orbital-pair FP32 stencil + local + nonlocal H-apply, fused Chebyshev step)"
                     if tun["kind"] >= 1 else "k_hstep (stencil + local + nonlocal H-apply, fused Chebyshev step)")
     stencil_name += f", {tun['threads']} threads x {tun['pairs']} point pairs"
+    stencil_name += {2: ", register-capped", 3: ", every projector record of a fragment staged once"}.get(tun["kind"], "")
     h = prof["hpsi"]
     achieved = h["bytes"] / (h["ms"] * 1e-3) / 1e9 if h["ms"] > 0 else 0.0
     traffic, traffic_note = kernel_traffic("k_hamiltonian.cu")

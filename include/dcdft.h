@@ -259,7 +259,8 @@ int dc_eb_adjoint(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_occ
  * fragments and keeps the fastest, separately for FP32 and FP64 elements.  A shape is (kind, threads
  * per CTA, point pairs per thread); kind 0 pairs x-adjacent points of one orbital (FP32: two
  * orbitals per CTA), kind 1 (FP32 only) interleaves two orbitals at every point, kind 2 is kind 1
- * compiled with registers capped for three 256-thread CTAs per SM.  With the
+ * compiled with registers capped for three 256-thread CTAs per SM, kind 3 is kind 1 with every
+ * plane's projector records built once per CTA (only where they fit in shared memory).  With the
  * environment variable DC_TUNE_CACHE=<file> results are looked up in / appended to that text file
  * (one line per fragment shape, atom and orbital count, type).
  * h_shape[6] = {fp32 kind, threads, pairs, fp64 kind, threads, pairs} (threads 0 = not tuned yet);

@@ -75,7 +75,7 @@ void free_ctx(dc_ctx *c) {
                   c->blk64[1], c->blk64[2], c->d_hy64, c->d_c64[0], c->d_c64[1], c->d_c32[0], c->d_c32[1],
                   c->d_eps, c->d_q, c->d_occ, c->d_bounds, c->d_gram, c->d_gram_off, c->d_gram_nchunk, c->d_C64,
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
-                  c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound,
+                  c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
                   c->d_dots};
   for (void *p : ptrs)
@@ -536,7 +536,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
       const int v = atoi(gc);
       if (v >= 64 && v <= 65536 && v % 64 == 0) c->gram_chunk = v;
     }
-    std::vector<int2> gi, ri;
+    std::vector<int2> gi, ri, ri2;
     std::vector<long long> goff(c->nfrag);
     std::vector<int> gn(c->nfrag);
     long long off = 0;
@@ -550,12 +550,16 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
       for (int ch = 0; ch < nch; ++ch) gi.push_back(make_int2(f, ch));
       const int nr = (int)((Pf + 127) / 128);
       for (int ch = 0; ch < nr; ++ch) ri.push_back(make_int2(f, ch));
+      const int nr2 = (int)((Pf + 255) / 256);
+      for (int ch = 0; ch < nr2; ++ch) ri2.push_back(make_int2(f, ch));
     }
     c->gram_elems = off;
     c->n_gram_items = (int)gi.size();
     c->n_rot_items = (int)ri.size();
+    c->n_rot2_items = (int)ri2.size();
     DC_TRY(upload(&c->d_gram_items, gi));
     DC_TRY(upload(&c->d_rot_items, ri));
+    DC_TRY(upload(&c->d_rot2_items, ri2));
     DC_TRY(upload(&c->d_gram_off, goff));
     DC_TRY(upload(&c->d_gram_nchunk, gn));
     DC_TRY(dmalloc(&c->d_gram, (size_t)off));

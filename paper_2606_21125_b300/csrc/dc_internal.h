@@ -85,6 +85,7 @@ struct dc_ctx {
   int max_atoms;      // max |A_f|
   int max_zlist;      // max over f of total per-plane list length
   int max_plane_ent;  // max over f and z of the row-list entries of one plane
+  int max_frag_ent;   // max over f of the row-list entries of the whole fragment
 
   // host copies of maps (for dc_get_maps and launch planning)
   std::vector<FragDesc> h_desc;
@@ -163,8 +164,10 @@ struct dc_ctx {
   int n_items2 = 0;
   int2 *d_gram_items = nullptr;  // (fragment, chunk) of the Gram kernel
   int n_gram_items = 0;
-  int2 *d_rot_items = nullptr;   // (fragment, 128-point chunk) of the rotation kernel
+  int2 *d_rot_items = nullptr;   // (fragment, 128-point chunk) of the FP64 rotation kernel
   int n_rot_items = 0;
+  int2 *d_rot2_items = nullptr;  // (fragment, 256-point chunk) of the FP32 rotation kernel
+  int n_rot2_items = 0;
   int *d_Fn = nullptr;           // num_fragment on the device
   // adjoint data: per-atom lists of (fragment, slot) entries, scratch
   int *d_atom_slot_beg = nullptr, *d_atom_slots = nullptr;

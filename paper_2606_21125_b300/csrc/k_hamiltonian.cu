@@ -569,9 +569,14 @@ struct PairSmem {
   float *red;  // [2][NT / 32] (at most 2 x 32 floats)
 };
 
+// Row pitch (in float2) of the haloed plane of the pair kernels: at least Ex + 8, and congruent modulo
+// 16 to the 2 ceil(Ex/2) float2 that one row of threads covers, so that the 16-byte loads of a warp whose
+// threads run over several rows still fall on consecutive banks (no shared-memory bank conflicts).
+__host__ __device__ __forceinline__ int pair_pitch(int Ex) { return 2 * ((Ex + 1) >> 1) + 16; }
+
 __device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int Ey, int Ez, int A, int maxent,
                                                int nrec, bool halo) {
-  const int pitch = (Ex + 9) & ~1, pitch2 = (Ex + 1) & ~1;
+  const int pitch = pair_pitch(Ex), pitch2 = (Ex + 1) & ~1;
   PairSmem m;
   m.pin = reinterpret_cast<float2 *>(raw);
   m.pout = m.pin + (halo ? 2 * (Ey + 8) * pitch : 0);
@@ -589,7 +594,7 @@ __device__ __forceinline__ PairSmem pair_carve(unsigned char *raw, int Ex, int E
 }
 
 size_t pair_smem_bytes(int Ex, int Ey, int Ez, int A, int maxent, int nrec, bool halo, int NT, int PP = 0) {
-  const int pitch = (Ex + 9) & ~1, pitch2 = (Ex + 1) & ~1;
+  const int pitch = pair_pitch(Ex), pitch2 = (Ex + 1) & ~1;
   size_t n2 = (halo ? 2 * (size_t)(Ey + 8) * pitch : 0) + 2 * (size_t)Ey * pitch2 + (size_t)A * pitch2 +
               (size_t)Ey * A + A;
   size_t b = (n2 * sizeof(float2) + 15) & ~(size_t)15;
@@ -720,7 +725,9 @@ struct HPair {
 // z - 4 + k, so the column advances without moving registers (the kernel unrolls z by 9).
 // vv/pvv hold this plane's V (2 points) and Y_{k-1} (2 points x 2 orbitals) per pair, loaded one
 // plane earlier; the plane refills them for plane z + 1 right after reading them.
-template <int NT, int PP, bool ISO, int ZI>
+// ALLREC: the records of every plane were built once at CTA start (m.rec / m.recky indexed by the
+// fragment's entry number); otherwise plane z builds its own into ring slot b3.
+template <int NT, int PP, bool ISO, bool ALLREC, int ZI>
 __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO> &K, const PairSmem &m, int maxent,
                                             float4 (&q)[PP][9], float2 (&vv)[PP], float4 (&pvv)[PP],
                                             int2 (&pre)[2], float2 &dot, int z, int b3) {
@@ -749,15 +756,27 @@ __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO>
   }
   const int rz = z * H.Ey;
   const int e0 = m.rb[rz];
-  const int nez = m.rb[rz + H.Ey] - e0;
-  float4 *RC = m.rec + b3 * maxent;
-  pair_records<NT>(H.ent + e0, nez, pre, m.sk2, H.pitch2, RC, m.recky + b3 * maxent);
-  if (z + 1 < H.Ez) pair_prefetch<NT>(H.ent + m.rb[rz + H.Ey], m.rb[rz + 2 * H.Ey] - m.rb[rz + H.Ey], pre);
+  const float4 *RC;
+  if (ALLREC) {
+    RC = m.rec + e0;
+  } else {
+    const int nez = m.rb[rz + H.Ey] - e0;
+    float4 *rc = m.rec + b3 * maxent;
+    pair_records<NT>(H.ent + e0, nez, pre, m.sk2, H.pitch2, rc, m.recky + b3 * maxent);
+    if (z + 1 < H.Ez) pair_prefetch<NT>(H.ent + m.rb[rz + H.Ey], m.rb[rz + 2 * H.Ey] - m.rb[rz + H.Ey], pre);
+    RC = rc;
+  }
   __syncthreads();
   if (H.proj && z > 0) {
-    const int bp = b3 == 0 ? 2 : b3 - 1;
-    pair_project<NT>(m.pout + ((z - 1) & 1) * H.Ey * H.pitch2, m.rec + bp * maxent, m.recky + bp * maxent,
-                     e0 - m.rb[rz - H.Ey], m, H.pitch2, H.A);
+    const int zb = m.rb[rz - H.Ey];
+    if (ALLREC) {
+      pair_project<NT>(m.pout + ((z - 1) & 1) * H.Ey * H.pitch2, m.rec + zb, m.recky + zb, e0 - zb, m, H.pitch2,
+                       H.A);
+    } else {
+      const int bp = b3 == 0 ? 2 : b3 - 1;
+      pair_project<NT>(m.pout + ((z - 1) & 1) * H.Ey * H.pitch2, m.rec + bp * maxent, m.recky + bp * maxent,
+                       e0 - zb, m, H.pitch2, H.A);
+    }
   }
 
   int zn = z + 5;
@@ -855,7 +874,7 @@ __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO>
   }
 }
 
-template <int NT, int PP, bool ISO, int MINB>
+template <int NT, int PP, bool ISO, int MINB, bool ALLREC>
 __global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int2 fi = a.items[blockIdx.x];
@@ -867,7 +886,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
   H.Ey = D.E[1];
   H.Ez = D.E[2];
   H.plane = H.Ex * H.Ey;
-  H.pitch = (H.Ex + 9) & ~1;
+  H.pitch = pair_pitch(H.Ex);
   H.pitch2 = (H.Ex + 1) & ~1;
   H.pplane = H.pitch * (H.Ey + 8);
   H.A = D.natom;
@@ -876,7 +895,7 @@ __global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
   H.proj = a.cout != nullptr;
   H.periodic = a.periodic != 0;
   H.mode = a.mode;
-  const PairSmem m = pair_carve(smem_raw, H.Ex, H.Ey, H.Ez, H.A, a.maxent, 3, true);
+  const PairSmem m = pair_carve(smem_raw, H.Ex, H.Ey, H.Ez, H.A, a.maxent, ALLREC ? 1 : 3, true);
 
   float alpha = 1.f, beta = 0.f, shift = 0.f;
   if (a.mode == HSTEP_CHEB) {
@@ -963,35 +982,49 @@ __global__ void __launch_bounds__(NT, MINB) k_hpair(HArgs<float> a) {
   }
   __syncthreads();
   int2 pre[2];
-  pair_prefetch<NT>(H.ent, m.rb[H.Ey], pre);
+  if (ALLREC) {
+    // every plane's records at once (sk2 is set): entry t of the fragment -> slot t
+    const int ne = m.rb[H.Ez * H.Ey];
+    for (int t = threadIdx.x; t < ne; t += NT) pair_record(t, H.ent[t], m.sk2, H.pitch2, m.rec, m.recky);
+    pre[0] = pre[1] = make_int2(0, 0);
+    __syncthreads();
+  } else {
+    pair_prefetch<NT>(H.ent, m.rb[H.Ey], pre);
+  }
 
   float2 dot = f2(0.f, 0.f);
   const int maxent = a.maxent;
   for (int z0 = 0; z0 < H.Ez; z0 += 9) {
-    hpair_plane<NT, PP, ISO, 0>(H, K, m, maxent, q, vv, pvv, pre, dot, z0, 0);
+    hpair_plane<NT, PP, ISO, ALLREC, 0>(H, K, m, maxent, q, vv, pvv, pre, dot, z0, 0);
     if (z0 + 1 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 1>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 1, 1);
+    hpair_plane<NT, PP, ISO, ALLREC, 1>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 1, 1);
     if (z0 + 2 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 2>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 2, 2);
+    hpair_plane<NT, PP, ISO, ALLREC, 2>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 2, 2);
     if (z0 + 3 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 3>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 3, 0);
+    hpair_plane<NT, PP, ISO, ALLREC, 3>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 3, 0);
     if (z0 + 4 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 4>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 4, 1);
+    hpair_plane<NT, PP, ISO, ALLREC, 4>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 4, 1);
     if (z0 + 5 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 5>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 5, 2);
+    hpair_plane<NT, PP, ISO, ALLREC, 5>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 5, 2);
     if (z0 + 6 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 6>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 6, 0);
+    hpair_plane<NT, PP, ISO, ALLREC, 6>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 6, 0);
     if (z0 + 7 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 7>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 7, 1);
+    hpair_plane<NT, PP, ISO, ALLREC, 7>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 7, 1);
     if (z0 + 8 >= H.Ez) break;
-    hpair_plane<NT, PP, ISO, 8>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 8, 2);
+    hpair_plane<NT, PP, ISO, ALLREC, 8>(H, K, m, maxent, q, vv, pvv, pre, dot, z0 + 8, 2);
   }
   if (H.proj) {
     __syncthreads();
     const int zp = H.Ez - 1;
-    const int bp = zp % 3;
-    pair_project<NT>(m.pout + (zp & 1) * H.Ey * H.pitch2, m.rec + bp * maxent, m.recky + bp * maxent,
-                     m.rb[(zp + 1) * H.Ey] - m.rb[zp * H.Ey], m, H.pitch2, H.A);
+    const int zb = m.rb[zp * H.Ey];
+    if (ALLREC) {
+      pair_project<NT>(m.pout + (zp & 1) * H.Ey * H.pitch2, m.rec + zb, m.recky + zb, m.rb[(zp + 1) * H.Ey] - zb, m,
+                       H.pitch2, H.A);
+    } else {
+      const int bp = zp % 3;
+      pair_project<NT>(m.pout + (zp & 1) * H.Ey * H.pitch2, m.rec + bp * maxent, m.recky + bp * maxent,
+                       m.rb[(zp + 1) * H.Ey] - zb, m, H.pitch2, H.A);
+    }
     __syncthreads();
     pair_finish<NT>(a, D, m, i0, H.nvalid);
   }
@@ -1146,17 +1179,22 @@ int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
 
 // Launch shapes of the stencil kernels: kind 0 = x-adjacent point pairs of one orbital (NO orbitals
 // per CTA), kind 1 = orbital-pair kernel (FP32 only), kind 2 = the orbital-pair kernel with its
-// registers capped for three 256-thread CTAs per SM; threads per CTA; point pairs per thread.
+// registers capped for three 256-thread CTAs per SM, kind 3 = the orbital-pair kernel with every
+// plane's projector records built once per CTA (when a fragment's records fit in shared memory);
+// threads per CTA; point pairs per thread.
 struct Shape {
   int kind, nt, pp;
 };
 constexpr Shape kShapes[] = {{0, 128, 1}, {0, 128, 2}, {0, 256, 1}, {0, 256, 2}, {0, 512, 1},
                              {0, 512, 2}, {0, 512, 4}, {1, 128, 1}, {1, 256, 1}, {1, 512, 1},
-                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}, {2, 128, 1}, {2, 256, 1}};
+                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}, {2, 128, 1}, {2, 256, 1}, {3, 256, 1}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 static_assert(kNumShapes <= DC_TUNE_SLOTS, "tuning slots");
 
-size_t hpair_smem(const dc_ctx *c, int NT, int PP) {
+size_t hpair_smem(const dc_ctx *c, int NT, int PP, bool allrec = false) {
+  if (allrec)
+    return pair_smem_bytes(c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms, std::max(1, c->max_frag_ent), 1,
+                           true, NT, PP);
   return pair_smem_bytes(c->max_E[0], c->max_E[1], c->max_E[2], c->max_atoms, std::max(1, c->max_plane_ent), 3,
                          true, NT, PP);
 }
@@ -1174,21 +1212,21 @@ bool iso_coeffs(const HArgs<float> &a) {
 
 // MINB: CTAs per SM the register budget is cut for (launch bounds); the default keeps two
 // 256-thread CTAs per SM, the register-capped variant three.
-template <int NT, int PP, int MINB = ((PP == 1 && NT <= 256) ? 512 / NT : 1)>
+template <int NT, int PP, int MINB = ((PP == 1 && NT <= 256) ? 512 / NT : 1), bool ALLREC = false>
 int run_hpair(dc_ctx *c, HArgs<float> a, cudaStream_t s) {
-  const size_t sm = hpair_smem(c, NT, PP);
+  const size_t sm = hpair_smem(c, NT, PP, ALLREC);
   if (sm > 227 * 1024) {
     dc_set_error("hpsi: fragment tables exceed shared memory (orbital-pair kernel)");
     return DC_ERR_ARG;
   }
   a.items = c->d_items2;
-  a.maxent = std::max(1, c->max_plane_ent);
+  a.maxent = std::max(1, ALLREC ? c->max_frag_ent : c->max_plane_ent);
   if (iso_coeffs(a)) {
-    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, true, MINB>, sm));
-    k_hpair<NT, PP, true, MINB><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
+    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, true, MINB, ALLREC>, sm));
+    k_hpair<NT, PP, true, MINB, ALLREC><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
   } else {
-    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, false, MINB>, sm));
-    k_hpair<NT, PP, false, MINB><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
+    DC_CUDA(dc_set_smem((const void *)k_hpair<NT, PP, false, MINB, ALLREC>, sm));
+    k_hpair<NT, PP, false, MINB, ALLREC><<<(unsigned)c->n_items2, NT, sm, s>>>(a);
   }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
@@ -1228,7 +1266,8 @@ int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
     case 11: return run_hpair<256, 2>(c, a, s);
     case 12: return run_hpair<512, 2>(c, a, s);
     case 13: return run_hpair<128, 1, 6>(c, a, s);
-    default: return run_hpair<256, 1, 3>(c, a, s);
+    case 14: return run_hpair<256, 1, 3>(c, a, s);
+    default: return run_hpair<256, 1, 2, true>(c, a, s);
   }
 }
 
@@ -1237,7 +1276,7 @@ int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
 bool shape_ok(const dc_ctx *c, int shape, size_t esz) {
   if (shape < 0 || shape >= kNumShapes) return false;
   const Shape S = kShapes[shape];
-  if (S.kind >= 1 && (esz != sizeof(float) || hpair_smem(c, S.nt, S.pp) > 227 * 1024)) return false;
+  if (S.kind >= 1 && (esz != sizeof(float) || hpair_smem(c, S.nt, S.pp, S.kind == 3) > 227 * 1024)) return false;
   const int pairs = ((c->max_E[0] + 1) / 2) * c->max_E[1];
   const int cover = S.nt * S.pp;
   return cover >= pairs && (cover <= 4 * pairs || S.nt == 128);

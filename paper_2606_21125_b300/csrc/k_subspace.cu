@@ -5,6 +5,8 @@
 // dominant costs are diagonalisation and orthonormalisation.  Here one pass is a scaled
 // Chebyshev filter (Zhou, Saad, Tiago & Chelikowsky, J. Comput. Phys. 219 (2006) 172) followed by
 // S = <Y|Y> = L L^T, Hs = L^-1 <Y|HY> L^-T = Q diag(eps) Q^T and Psi = Y L^-T Q.
+#include <type_traits>
+
 #include "dc_internal.h"
 
 namespace {
@@ -514,6 +516,115 @@ __global__ void __launch_bounds__(256) k_rotate(const FragDesc *desc, const int2
   }
 }
 
+// FP32 rotation out[i][p] = sum_k C[k][i] Y[k][p] with paired FP32 FMAs.  One CTA per (fragment,
+// 256-point chunk); warp w owns output orbitals [w OPT, (w + 1) OPT) (OPT = ceil(max n / 8)), lane l
+// the points 4l..4l+3 and 128+4l..128+4l+3 (two conflict-free 16-byte shared loads per k); C is
+// splatted over point pairs in shared memory and read as a warp broadcast.
+constexpr int R2CH = 256;
+constexpr int R2PAD = R2CH + 4;
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int OPT>
+__global__ void __launch_bounds__(256) k_rotate32(const FragDesc *desc, const int2 *ritems, const float *C,
+                                                  const float *Y, float *out, int nmax) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 it = ritems[blockIdx.x];
+  const int f = it.x, ch = it.y;
+  const FragDesc D = desc[f];
+  const int n = D.norb;
+  const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
+  const long long p0 = (long long)ch * R2CH;
+  constexpr int NC = 8 * OPT;                                     // padded orbital count
+  float *sY = reinterpret_cast<float *>(smem_raw);               // [n][R2PAD]
+  float2 *sC = reinterpret_cast<float2 *>(sY + nmax * R2PAD);  // [n][NC] splatted
+  const float *Cf = C + D.sub_off;
+  const float *Yf = Y + D.psi_off;
+  const bool vec = ((P | D.psi_off) & 3) == 0;
+  if (vec) {
+    // Every 16-byte copy of the Y tile in flight at once; a quad past the fragment's end is zero-filled
+    // (P is a multiple of 4, so a quad is either wholly inside or wholly outside).
+    for (int t = threadIdx.x; t < n * (R2CH / 4); t += 256) {
+      const int k = t / (R2CH / 4), q = t - k * (R2CH / 4);
+      const long long pp = p0 + 4 * q;
+      const float *src = Yf + (long long)k * P + (pp < P ? pp : 0);
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(sY + k * R2PAD + 4 * q);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(pp < P ? 16 : 0)
+                   : "memory");
+    }
+  } else {
+    for (int t = threadIdx.x; t < n * (R2CH / 4); t += 256) {
+      const int k = t / (R2CH / 4), q = t - k * (R2CH / 4);
+      const long long pp = p0 + 4 * q;
+      const float *row = Yf + (long long)k * P;
+      float4 v;
+      v.x = pp < P ? row[pp] : 0.f;
+      v.y = pp + 1 < P ? row[pp + 1] : 0.f;
+      v.z = pp + 2 < P ? row[pp + 2] : 0.f;
+      v.w = pp + 3 < P ? row[pp + 3] : 0.f;
+      *reinterpret_cast<float4 *>(sY + k * R2PAD + 4 * q) = v;
+    }
+  }
+  // C splatted to (c, c) pairs: the loads of one thread are independent and issued together.
+  constexpr int CPT = (8 * OPT * 8 * OPT + 255) / 256;
+  float cv[CPT];
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int t = threadIdx.x + 256 * j, k = t / NC, i = t - k * NC;
+    cv[j] = (k < n && i < n) ? Cf[k * n + i] : 0.f;
+  }
+#pragma unroll
+  for (int j = 0; j < CPT; ++j) {
+    const int t = threadIdx.x + 256 * j;
+    if (t < n * NC) sC[t] = make_float2(cv[j], cv[j]);
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i0 = w * OPT;
+  if (i0 >= n) return;
+  float2 acc[OPT][4];
+#pragma unroll
+  for (int o = 0; o < OPT; ++o)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[o][b] = make_float2(0.f, 0.f);
+  for (int k = 0; k < n; ++k) {
+    const float4 ya = *reinterpret_cast<const float4 *>(sY + k * R2PAD + 4 * lane);
+    const float4 yb = *reinterpret_cast<const float4 *>(sY + k * R2PAD + 128 + 4 * lane);
+    const float2 y0 = make_float2(ya.x, ya.y), y1 = make_float2(ya.z, ya.w);
+    const float2 y2 = make_float2(yb.x, yb.y), y3 = make_float2(yb.z, yb.w);
+    const float2 *cr = sC + k * NC + i0;
+#pragma unroll
+    for (int o = 0; o < OPT; ++o) {
+      const float2 c = cr[o];
+      acc[o][0] = ffma2(c, y0, acc[o][0]);
+      acc[o][1] = ffma2(c, y1, acc[o][1]);
+      acc[o][2] = ffma2(c, y2, acc[o][2]);
+      acc[o][3] = ffma2(c, y3, acc[o][3]);
+    }
+  }
+  float *of = out + D.psi_off;
+#pragma unroll
+  for (int o = 0; o < OPT; ++o) {
+    const int i = i0 + o;
+    if (i >= n) break;
+    float *row = of + (long long)i * P;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long pp = p0 + 128 * h + 4 * lane;
+      const float4 v = make_float4(acc[o][2 * h].x, acc[o][2 * h].y, acc[o][2 * h + 1].x, acc[o][2 * h + 1].y);
+      if (vec && pp + 3 < P) {
+        *reinterpret_cast<float4 *>(row + pp) = v;
+      } else {
+        if (pp < P) row[pp] = v.x;
+        if (pp + 1 < P) row[pp + 1] = v.y;
+        if (pp + 2 < P) row[pp + 2] = v.z;
+        if (pp + 3 < P) row[pp + 3] = v.w;
+      }
+    }
+  }
+}
+
 // Projections of the rotated block, per fragment: cout[i][k] = sum_j C[j][i] cin[j][k].  C maps the
 // filtered block to Psi = Y C, so <p_k|Psi_i> = sum_j C[j][i] <p_k|Y_j>.
 template <typename T>
@@ -564,6 +675,27 @@ int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
 
 template <typename T>
 int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s) {
+  if constexpr (std::is_same<T, float>::value) {
+    const int opt = (c->layout.max_norb + 7) / 8;
+    const int nmax = c->layout.max_norb;
+    const size_t sm = (size_t)nmax * R2PAD * sizeof(float) + (size_t)nmax * 8 * opt * sizeof(float2);
+    auto run = [&](auto kern) -> int {
+      DC_CUDA(dc_set_smem((const void *)kern, sm));
+      kern<<<c->n_rot2_items, 256, sm, s>>>(c->d_desc, c->d_rot2_items, c->d_C32, Y, out, nmax);
+      DC_CUDA(cudaGetLastError());
+      return DC_OK;
+    };
+    switch (opt) {
+      case 1: return run(k_rotate32<1>);
+      case 2: return run(k_rotate32<2>);
+      case 3: return run(k_rotate32<3>);
+      case 4: return run(k_rotate32<4>);
+      case 5: return run(k_rotate32<5>);
+      case 6: return run(k_rotate32<6>);
+      case 7: return run(k_rotate32<7>);
+      default: return run(k_rotate32<8>);
+    }
+  }
   const size_t sm = ((size_t)DC_MAX_NORB * RPAD + (size_t)DC_MAX_NORB * DC_MAX_NORB) * sizeof(T);
   DC_CUDA(dc_set_smem((const void *)k_rotate<T>, sm));
   const T *C = nullptr;

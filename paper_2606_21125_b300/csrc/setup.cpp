@@ -182,6 +182,7 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   c->max_atoms = 0;
   c->max_zlist = 0;
   c->max_plane_ent = 0;
+  c->max_frag_ent = 0;
   for (int d = 0; d < 3; ++d) c->max_E[d] = 0;
   int max_norb = 0;
   for (int f = 0; f < c->nfrag; ++f) {
@@ -277,6 +278,7 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
         c->max_plane_ent = std::max(c->max_plane_ent, (int)(row_ent.size() - plane_start));
       }
       row_beg.push_back((int)row_ent.size());
+      c->max_frag_ent = std::max(c->max_frag_ent, (int)(row_ent.size() - (size_t)row_beg[D.row_off]));
       if (row_ent.size() > (size_t)INT32_MAX / 2) {
         dc_set_error("dc_init: projector row lists too long");
         return DC_ERR_ARG;

@@ -48,7 +48,7 @@ def main():
     if args.all_shapes:
         shapes = [(0, 128, 1), (0, 128, 2), (0, 256, 1), (0, 256, 2), (0, 512, 1), (0, 512, 2), (0, 512, 4),
                   (1, 128, 1), (1, 256, 1), (1, 512, 1), (1, 1024, 1), (1, 256, 2), (1, 512, 2), (2, 128, 1),
-                  (2, 256, 1)]
+                  (2, 256, 1), (3, 256, 1)]
     for shape in shapes:
         if shape is not None and not s.set_tuning(args.dtype, *shape):
             continue
