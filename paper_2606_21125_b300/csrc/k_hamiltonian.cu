@@ -842,12 +842,20 @@ __device__ __forceinline__ void hpair_plane(const HPair<PP> &H, const PairK<ISO>
     {
       const int eb = m.rb[rz + y] - e0, ee = m.rb[rz + y + 1] - e0;
       const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2 + x);
-      for (int e = eb; e < ee; ++e) {
+      int e = eb;
+      for (; e + 1 < ee; e += 2) {
+        const float4 ra = RC[e], rb = RC[e + 1];
+        const float4 ga = g4[__float_as_int(ra.z)], gb = g4[__float_as_int(rb.z)];
+        h0 = fma2(lo2(ra), lo2(ga), h0);
+        h1 = fma2(lo2(ra), hi2(ga), h1);
+        h0 = fma2(lo2(rb), lo2(gb), h0);
+        h1 = fma2(lo2(rb), hi2(gb), h1);
+      }
+      if (e < ee) {
         const float4 rr = RC[e];
         const float4 g = g4[__float_as_int(rr.z)];
-        const float2 u = lo2(rr);
-        h0 = fma2(u, lo2(g), h0);
-        h1 = fma2(u, hi2(g), h1);
+        h0 = fma2(lo2(rr), lo2(g), h0);
+        h1 = fma2(lo2(rr), hi2(g), h1);
       }
     }
     float2 out0 = h0, out1 = h1;
