@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *
 // eigenvalues, and the vectors' ~1e-7 mixing is below the FP32 rounding of the rotation that
 // applies them.
 // ---------------------------------------------------------------------------------------------
-constexpr int SNT = 256;
+constexpr int SNT = 512;
 
 template <typename T>
 __device__ __forceinline__ T block_sum_t(T v, T *red) {
@@ -230,28 +230,29 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, T rel,
         rs[tid] = sn;
       }
       __syncthreads();
-      // rows: A <- J^T A
-      for (int t = tid; t < half * np; t += SNT) {
-        const int k = t / np, j = t - k * np;
-        const T sn = rs[k];
-        if (sn == T(0)) continue;
-        const int p = rp[k], q = rq[k];
-        const T c = rc[k];
-        const T ap = M[p * ld + j], aq = M[q * ld + j];
-        M[p * ld + j] = c * ap - sn * aq;
-        M[q * ld + j] = sn * ap + c * aq;
+      // A <- J^T A J: the round's rotations act on disjoint index pairs, so each 2 x 2 block (row
+      // pair k, column pair l) takes its row rotation and then its column rotation in one pass;
+      // V <- V J on the same pass (V is not read by the block updates)
+      for (int t = tid; t < half * half; t += SNT) {
+        const int k = t / half, l = t - k * half;
+        const T sk = rs[k], sl = rs[l];
+        if (sk == T(0) && sl == T(0)) continue;
+        const int pk = rp[k], qk = rq[k], pl = rp[l], ql = rq[l];
+        const T ck = rc[k], cl = rc[l];
+        const T a = M[pk * ld + pl], b = M[pk * ld + ql], c = M[qk * ld + pl], d = M[qk * ld + ql];
+        const T a1 = ck * a - sk * c, b1 = ck * b - sk * d;
+        const T c1 = sk * a + ck * c, d1 = sk * b + ck * d;
+        M[pk * ld + pl] = cl * a1 - sl * b1;
+        M[pk * ld + ql] = sl * a1 + cl * b1;
+        M[qk * ld + pl] = cl * c1 - sl * d1;
+        M[qk * ld + ql] = sl * c1 + cl * d1;
       }
-      __syncthreads();
-      // columns: A <- A J, V <- V J
       for (int t = tid; t < half * np; t += SNT) {
         const int k = t / np, i = t - k * np;
         const T sn = rs[k];
         if (sn == T(0)) continue;
         const int p = rp[k], q = rq[k];
         const T c = rc[k];
-        const T ap = M[i * ld + p], aq = M[i * ld + q];
-        M[i * ld + p] = c * ap - sn * aq;
-        M[i * ld + q] = sn * ap + c * aq;
         const T vp = V[i * ld + p], vq = V[i * ld + q];
         V[i * ld + p] = c * vp - sn * vq;
         V[i * ld + q] = sn * vp + c * vq;
