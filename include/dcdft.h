@@ -212,6 +212,30 @@ int dc_set_state(dc_ctx *ctx, const void *d_psi, const double *d_eps, void *stre
  * Outputs (device, FP64): d_rho[npts]; d_q[nstates] and d_mu[1] may be NULL. */
 int dc_density(dc_ctx *ctx, double *d_rho, double *d_q, double *d_mu, void *stream);
 
+/* ---- DC-LCFO basis (Sec. 2.3, Eqs. 6-7) -------------------------------------------------- */
+/* Size of the basis output of dc_lcfo_basis: *basis_elems = sum over fragments of n_f |core_f|
+ * (FP64 elements); h_off (host, nfrag entries, may be NULL) receives each fragment's element offset.
+ * Returns DC_ERR_ARG for a NULL context or basis_elems. */
+int dc_lcfo_query(const dc_ctx *ctx, int64_t *basis_elems, int64_t *h_off);
+/* The basis-construction step of DC-LCFO on every fragment.  Orbitals i of fragment f with
+ * eps_i < eps_cut (strict, in orbital order) are projected onto the core (zero outside it, Eq. 3),
+ * their overlap S_ij = <phibar_i|phibar_j> (dV sum over core points, Eq. 6) is diagonalised in FP64,
+ * eigenvectors with eigenvalue s <= lambda_cut are dropped, and the kept ones, in descending order of
+ * s, give the basis lambda_k = sum_i phibar_i U_ik / sqrt(s_k), orthonormal on the core (Eq. 7).
+ *   d_psi     orbital block in the layout of dc_query (device), element type dtype (DC_FP64 or
+ *             DC_FP32; FP32 values are widened to FP64 before any arithmetic).
+ *   d_eps     eigenvalues of those orbitals, nstates FP64 (device), in the block's state order.
+ *   eps_cut   selection energy (Ha), e.g. mu + 0.1 eV; lambda_cut >= 0 the overlap threshold.
+ *   d_basis   (device, FP64, dc_lcfo_query elements) fragment f's row k (k < n_f) at element
+ *             h_off[f] + k |core_f|, core points [c_z][c_y][c_x] with x fastest; rows k >= m_f are 0.
+ *   d_nbasis  (device, int32, nfrag) m_f, the number of kept functions.
+ *   d_s       (device, FP64, nstates, may be NULL) the eigenvalues of S per fragment in descending
+ *             order, 0 past the selected count.
+ * All arguments are caller-owned; the call is stream-ordered on `stream` and writes nothing else.
+ * Errors: DC_ERR_ARG for NULL pointers, a bad dtype or lambda_cut < 0 (nothing is written). */
+int dc_lcfo_basis(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_eps, double eps_cut, double lambda_cut,
+                  double *d_basis, int32_t *d_nbasis, double *d_s, void *stream);
+
 /* Allocation-free chemical potential.  The paper has no counterpart: this is a library variant of
  * the Fermi-level solve inside dc_density (same kernel, same stopping rule), for callers that may
  * not allocate device memory where they need mu (a caller-owned pool or arena holding the device,

@@ -133,6 +133,25 @@ class DCSolver:
         check("dc_hpsi", self.lib.dc_hpsi(self.ctx, _ptr(psi), _ptr(out), dt, _stream(stream)))
         return out
 
+    def lcfo_basis(self, psi, eps, eps_cut, lambda_cut=1e-7, stream=None):
+        """DC-LCFO basis of every fragment (Sec. 2.3, Eqs. 6-7) from the orbital block ``psi`` and its
+        eigenvalues ``eps`` (device tensors in the context's layout).  Returns (basis, nbasis, s,
+        offsets): basis FP64 with fragment f's row k at offsets[f] + k |core_f| (rows k >= nbasis[f]
+        zero), nbasis int32 per fragment, s the overlap eigenvalues per fragment in descending order,
+        offsets a host list."""
+        torch = _torch()
+        nel = C.c_int64(0)
+        offs = (C.c_int64 * self.layout.nfrag)()
+        check("dc_lcfo_query", self.lib.dc_lcfo_query(self.ctx, C.byref(nel), offs))
+        basis = torch.empty(nel.value, dtype=torch.float64, device=psi.device)
+        nbasis = torch.empty(self.layout.nfrag, dtype=torch.int32, device=psi.device)
+        sv = torch.empty(self.layout.nstates, dtype=torch.float64, device=psi.device)
+        dt = DC_FP64 if psi.dtype == torch.float64 else DC_FP32
+        check("dc_lcfo_basis", self.lib.dc_lcfo_basis(self.ctx, _ptr(psi), dt, _ptr(eps), float(eps_cut),
+                                                       float(lambda_cut), _ptr(basis), _ptr(nbasis), _ptr(sv),
+                                                       _stream(stream)))
+        return basis, nbasis, sv, list(offs)
+
     def subspace(self, stream=None):
         check("dc_subspace", self.lib.dc_subspace(self.ctx, _stream(stream)))
 

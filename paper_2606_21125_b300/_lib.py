@@ -79,6 +79,8 @@ PROTOTYPES = {
     "dc_get_state": (C.c_int, [VP, VP, VP, VP]),
     "dc_set_state": (C.c_int, [VP, VP, VP, VP]),
     "dc_density": (C.c_int, [VP, VP, VP, VP, VP]),
+    "dc_lcfo_query": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "dc_lcfo_basis": (C.c_int, [VP, VP, C.c_int, VP, C.c_double, C.c_double, VP, VP, VP, VP]),
     "dc_fermi_level_noalloc": (C.c_int, [VP, VP, C.c_int64, C.c_double, C.c_double, VP, VP, VP]),
     "dc_scf_step": (C.c_int, [VP, VP, C.c_int, C.POINTER(dc_stats_t), VP]),
     "dc_get_rho_out": (C.c_int, [VP, VP, VP]),

@@ -851,6 +851,50 @@ int dc_density(dc_ctx *c, double *d_rho, double *d_q, double *d_mu, void *stream
   return check_flags(c, s);
 }
 
+int dc_lcfo_query(const dc_ctx *c, int64_t *basis_elems, int64_t *h_off) {
+  if (!c || !basis_elems) {
+    dc_set_error("dc_lcfo_query: NULL argument");
+    return DC_ERR_ARG;
+  }
+  int64_t off = 0;
+  for (size_t f = 0; f < c->h_desc.size(); ++f) {
+    const FragDesc &D = c->h_desc[f];
+    if (h_off) h_off[f] = off;
+    off += (int64_t)D.norb * D.c[0] * D.c[1] * D.c[2];
+  }
+  *basis_elems = off;
+  return DC_OK;
+}
+
+int dc_lcfo_basis(dc_ctx *c, const void *d_psi, int dtype, const double *d_eps, double eps_cut, double lambda_cut,
+                  double *d_basis, int32_t *d_nbasis, double *d_s, void *stream) {
+  if (!c || !d_psi || !d_eps || !d_basis || !d_nbasis) {
+    dc_set_error("dc_lcfo_basis: NULL argument");
+    return DC_ERR_ARG;
+  }
+  if (dtype != DC_FP64 && dtype != DC_FP32) {
+    dc_set_error("dc_lcfo_basis: dtype must be DC_FP64 or DC_FP32");
+    return DC_ERR_ARG;
+  }
+  if (!(lambda_cut >= 0.0) || eps_cut != eps_cut) {
+    dc_set_error("dc_lcfo_basis: lambda_cut must be >= 0 and eps_cut a number");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  double *sv = d_s ? d_s : c->d_work;
+  if (!d_s && c->layout.nstates > c->npts) {
+    dc_set_error("dc_lcfo_basis: workspace too small for the eigenvalues");
+    return DC_ERR_ARG;
+  }
+  if (dtype == DC_FP64)
+    DC_TRY(dck::launch_lcfo<double>(c, static_cast<const double *>(d_psi), d_eps, eps_cut, lambda_cut, d_basis,
+                                    reinterpret_cast<int *>(d_nbasis), sv, s));
+  else
+    DC_TRY(dck::launch_lcfo<float>(c, static_cast<const float *>(d_psi), d_eps, eps_cut, lambda_cut, d_basis,
+                                   reinterpret_cast<int *>(d_nbasis), sv, s));
+  return DC_OK;
+}
+
 int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, void *stream) {
   if (!c || !rho) {
     dc_set_error("dc_scf_step: NULL argument");

@@ -265,6 +265,9 @@ int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s);
 int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s);
 int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s);
 template <typename T>
+int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, double lambda_cut, double *basis,
+                int *nbasis, double *s_out, cudaStream_t s);
+template <typename T>
 int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s);
 template <typename T>
 int launch_rotate_proj(dc_ctx *c, const T *cin, T *cout, cudaStream_t s);

@@ -643,6 +643,151 @@ __global__ void __launch_bounds__(256) k_rotate_proj(const FragDesc *desc, const
   }
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// DC-LCFO basis (Sec. 2.3, Eqs. 6-7).  One CTA per fragment: orbitals with eps_i < eps_cut (in
+// orbital order) are projected onto the core, their overlap S_ij = dV sum_core phi_i phi_j is
+// accumulated in FP64 over 64-point core tiles (each thread keeps its upper-triangle entries in
+// registers), S is diagonalised by the FP64 Jacobi above, eigenvalues are ranked in descending order
+// (ties by index), the directions with s > lambda_cut are kept, and the basis
+// lambda_k = sum_i phibar_i U_ik / sqrt(s_k) is written on the core points (x fastest).
+// ---------------------------------------------------------------------------------------------
+constexpr int LCH = 64;                               // core points per tile
+constexpr int LTS = LCH + 1;                          // tile row stride (rows of a warp on different banks)
+constexpr int LTRI = (DC_MAX_NORB * (DC_MAX_NORB + 1) / 2 + SNT - 1) / SNT;  // triangle entries per thread
+
+__device__ __forceinline__ long long core_point(const FragDesc &D, long long cp) {
+  const long long cxy = (long long)D.c[0] * D.c[1];
+  const int cz = (int)(cp / cxy);
+  const long long r = cp - cz * cxy;
+  const int cy = (int)(r / D.c[0]), cx = (int)(r - (long long)cy * D.c[0]);
+  return (long long)(D.b[0] + cx) + (long long)D.E[0] * ((D.b[1] + cy) + (long long)D.E[1] * (D.b[2] + cz));
+}
+
+template <typename T>
+__device__ __forceinline__ void lcfo_tile(const FragDesc &D, const T *psi, long long P, const int *sel, int nsel,
+                                          long long ncore, long long cp0, double *tile) {
+  for (int t = threadIdx.x; t < nsel * LCH; t += SNT) {
+    const int i = t / LCH, p = t - i * LCH;
+    const long long cp = cp0 + p;
+    tile[i * LTS + p] = cp < ncore ? (double)psi[D.psi_off + (long long)sel[i] * P + core_point(D, cp)] : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi, const double *eps, double eps_cut,
+                                              double lambda_cut, double dV, double *basis, int *nbasis,
+                                              double *s_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int LD = DC_MAX_NORB + 1;
+  double *S = reinterpret_cast<double *>(smem_raw);  // [np][LD] overlap -> eigenvalues; then W
+  double *V = S + DC_MAX_NORB * LD;                   // [np][LD] eigenvectors
+  double *tile = V + DC_MAX_NORB * LD;                // [nsel][LTS]
+  __shared__ double red[SNT / 32], rc[32], rs[32], sv[DC_MAX_NORB];
+  __shared__ long long redl[SNT / 32];
+  __shared__ int rp[32], rq[32], sel[DC_MAX_NORB], perm[DC_MAX_NORB], nsel_s;
+  const int f = blockIdx.x, tid = threadIdx.x;
+  const FragDesc D = desc[f];
+  const int n = D.norb;
+  const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
+  const long long ncore = (long long)D.c[0] * D.c[1] * D.c[2];
+
+  // element offset of this fragment's rows: sum over the fragments before it of n |core|
+  long long part = 0;
+  for (int g = tid; g < f; g += SNT) part += (long long)desc[g].norb * desc[g].c[0] * desc[g].c[1] * desc[g].c[2];
+  const long long off = block_sum_t<long long>(part, redl);
+  double *out = basis + off;
+
+  if (tid == 0) {
+    int k = 0;
+    for (int i = 0; i < n; ++i)
+      if (eps[D.st_off + i] < eps_cut) sel[k++] = i;
+    nsel_s = k;
+  }
+  __syncthreads();
+  const int nsel = nsel_s;
+  const int np = nsel + (nsel & 1);  // even size for the round-robin pairing (index nsel is a dummy)
+  const int ntri = nsel * (nsel + 1) / 2;
+
+  // 1. S = dV sum over core points of phibar_i phibar_j (upper triangle)
+  double acc[LTRI];
+#pragma unroll
+  for (int r = 0; r < LTRI; ++r) acc[r] = 0.0;
+  for (long long cp0 = 0; cp0 < ncore && nsel > 0; cp0 += LCH) {
+    lcfo_tile<T>(D, psi, P, sel, nsel, ncore, cp0, tile);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < LTRI; ++r) {
+      const int t = tid + r * SNT;
+      if (t < ntri) {
+        int i, j;
+        tri_ij(t, nsel, i, j);
+        const double *a = tile + i * LTS, *b = tile + j * LTS;
+        double sum = 0.0;
+        for (int p = 0; p < LCH; ++p) sum += a[p] * b[p];
+        acc[r] += sum;
+      }
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < np * np; t += SNT) {
+    const int i = t / np, j = t - i * np;
+    S[i * LD + j] = 0.0;
+    V[i * LD + j] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < LTRI; ++r) {
+    const int t = tid + r * SNT;
+    if (t < ntri) {
+      int i, j;
+      tri_ij(t, nsel, i, j);
+      S[i * LD + j] = dV * acc[r];
+      S[j * LD + i] = dV * acc[r];
+    }
+  }
+  __syncthreads();
+
+  // 2. S = U diag(s) U^T (FP64 Jacobi to convergence)
+  if (np > 0) jacobi_sweeps<double>(S, V, np, LD, 40, 1e-30, 1e-18, red, rc, rs, rp, rq);
+  for (int i = tid; i < nsel; i += SNT) sv[i] = S[i * LD + i];
+  __syncthreads();
+
+  // 3. rank descending (ties by index), keep s > lambda_cut
+  for (int i = tid; i < nsel; i += SNT) {
+    int r = 0;
+    for (int k = 0; k < nsel; ++k) r += (sv[k] > sv[i]) || (sv[k] == sv[i] && k < i);
+    perm[r] = i;
+  }
+  __syncthreads();
+  int m = 0;
+  for (int k = 0; k < nsel; ++k) m += sv[k] > lambda_cut;
+  if (tid == 0) nbasis[f] = m;
+  for (int r = tid; r < n; r += SNT) s_out[D.st_off + r] = r < nsel ? sv[perm[r]] : 0.0;
+  // W[i][k] = U[i][perm k] / sqrt(s_perm k) over the kept directions (into S's space)
+  for (int t = tid; t < nsel * m; t += SNT) {
+    const int i = t / m, k = t - i * m;
+    S[i * LD + k] = V[i * LD + perm[k]] / sqrt(sv[perm[k]]);
+  }
+  __syncthreads();
+
+  // 4. lambda_k on the core points; rows m <= k < n are zero
+  for (long long cp0 = 0; cp0 < ncore; cp0 += LCH) {
+    if (m > 0) lcfo_tile<T>(D, psi, P, sel, nsel, ncore, cp0, tile);
+    __syncthreads();
+    for (int t = tid; t < n * LCH; t += SNT) {
+      const int k = t / LCH, p = t - k * LCH;
+      const long long cp = cp0 + p;
+      if (cp >= ncore) continue;
+      double v = 0.0;
+      if (k < m)
+        for (int i = 0; i < nsel; ++i) v += tile[i * LTS + p] * S[i * LD + k];
+      out[(long long)k * ncore + cp] = v;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 namespace dck {
@@ -723,5 +868,19 @@ template int launch_gram<double>(dc_ctx *, const double *, const double *, cudaS
 template int launch_gram<float>(dc_ctx *, const float *, const float *, cudaStream_t);
 template int launch_rotate<double>(dc_ctx *, const double *, double *, cudaStream_t);
 template int launch_rotate<float>(dc_ctx *, const float *, float *, cudaStream_t);
+
+template <typename T>
+int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, double lambda_cut, double *basis,
+                int *nbasis, double *s_out, cudaStream_t s) {
+  const size_t sm = (2 * (size_t)DC_MAX_NORB * (DC_MAX_NORB + 1) + (size_t)DC_MAX_NORB * LTS) * sizeof(double);
+  DC_CUDA(dc_set_smem((const void *)k_lcfo<T>, sm));
+  k_lcfo<T><<<c->nfrag, SNT, sm, s>>>(c->d_desc, psi, eps, eps_cut, lambda_cut, c->dV, basis, nbasis, s_out);
+  DC_CUDA(cudaGetLastError());
+  return DC_OK;
+}
+template int launch_lcfo<double>(dc_ctx *, const double *, const double *, double, double, double *, int *, double *,
+                                 cudaStream_t);
+template int launch_lcfo<float>(dc_ctx *, const float *, const double *, double, double, double *, int *, double *,
+                                cudaStream_t);
 
 }  // namespace dck

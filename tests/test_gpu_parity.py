@@ -426,3 +426,99 @@ def test_full_size_hpsi_sampled_si512():
         shp = (int(st.norb[f]),) + tuple(int(v) for v in st.frags.extent[f][::-1])
         ref = st.hamiltonian(f, V).apply(xin[f].reshape(shp)).reshape(-1)
         assert np.max(np.abs(got[f] - ref)) <= 2e-6 * np.max(np.abs(ref)), f
+
+
+# ---------------------------------------------------------------------------------------------
+# DC-LCFO basis (Sec. 2.3, Eqs. 6-7).  Inputs come from the oracle's own warmed-up state (or a
+# seeded synthetic block); the CUDA call gets the same values, FP32 inputs rounded once and handed
+# to both sides.  Compared: the kept count (exact; the test asserts that no overlap eigenvalue lies
+# within a factor 3 of lambda_cut, so both FP64 decisions are well separated), the overlap
+# eigenvalues (1e-11 of the largest: FP64 Jacobi against LAPACK), the span projector dV B^T B
+# (1e-8: rounding amplified by at most 1/s_min for s_min >= lambda_cut), orthonormality of the
+# returned functions (1e-9) and zero rows past the kept count.
+# ---------------------------------------------------------------------------------------------
+def _lcfo_reference(st, psi_frags, eps_frags, eps_cut, lam):
+    from oracle import lcfo
+    s_ref, B_ref = {}, {}
+    for f in range(st.frags.nfrag):
+        s_ref[f], B_ref[f] = lcfo.fragment_basis(st.frags, f, psi_frags[f], eps_frags[f], st.grid.dV, eps_cut, lam)
+        for v in s_ref[f]:
+            assert not (lam / 3.0 < v < 3.0 * lam), "an overlap eigenvalue sits at the threshold"
+    return s_ref, B_ref
+
+
+def _lcfo_run(cfg, st, psi_frags, eps_frags, eps_cut, lam, dtype):
+    from oracle import lcfo
+    if dtype == "fp32":
+        psi_frags = {f: v.astype(np.float32).astype(np.float64) for f, v in psi_frags.items()}
+    s_ref, B_ref = _lcfo_reference(st, psi_frags, eps_frags, eps_cut, lam)
+    tdt = torch.float64 if dtype == "fp64" else torch.float32
+    psi = torch.from_numpy(pack(st, psi_frags)).to(tdt).cuda()
+    eps = torch.from_numpy(pack(st, eps_frags)).cuda()
+    dV = st.grid.dV
+    with _solver(cfg) as s:
+        for _ in range(2):  # two calls in a row write the same result
+            basis, nb, sv, offs = s.lcfo_basis(psi, eps, eps_cut, lam)
+            torch.cuda.synchronize()
+            basis, nb, sv = _np(basis), _np(nb), _np(sv)
+            so = 0
+            for f in range(st.frags.nfrag):
+                n = int(st.norb[f])
+                ncore = int(np.prod(st.frags.core[f]))
+                m = B_ref[f].shape[0]
+                assert nb[f] == m, (f, nb[f], m)
+                ns = len(s_ref[f])
+                smax = max(1.0, float(np.max(np.abs(s_ref[f]))) if ns else 1.0)
+                np.testing.assert_allclose(sv[so:so + ns], s_ref[f], rtol=0, atol=1e-11 * smax)
+                assert np.all(sv[so + ns:so + n] == 0.0)
+                rows = basis[offs[f]:offs[f] + n * ncore].reshape(n, ncore)
+                B = rows[:m]
+                assert np.all(rows[m:] == 0.0)
+                if m:
+                    np.testing.assert_allclose(dV * B @ B.T, np.eye(m), rtol=0, atol=1e-9)
+                    np.testing.assert_allclose(lcfo.span_projector(B, dV), lcfo.span_projector(B_ref[f], dV),
+                                               rtol=0, atol=1e-8)
+                so += n
+    return s_ref
+
+
+def _gap_cut(eps_frags):
+    """A cut energy in the widest gap of the middle third of all eigenvalues (no eps near it)."""
+    e = np.sort(np.concatenate(list(eps_frags.values())))
+    lo, hi = len(e) // 3, 2 * len(e) // 3
+    j = lo + int(np.argmax(e[lo + 1:hi + 1] - e[lo:hi]))
+    return 0.5 * (e[j] + e[j + 1])
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["si8", "uneven"])
+def test_lcfo_basis_from_oracle_state(case, dtype):
+    cfg = CASES[case](precision="fp64", n_warmup=2)
+    st = oracle_state(cfg)
+    st.warmup()
+    from oracle import lcfo
+    eps_cut = _gap_cut(st.eps)
+    s_all = [lcfo.fragment_basis(st.frags, f, st.psi[f], st.eps[f], st.grid.dV, eps_cut, 0.0)[0] for f in st.eps]
+    lam = next(v for v in (1e-7, 1e-6, 1e-5, 1e-4, 1e-3) if not any(np.any((s > v / 3) & (s < 3 * v)) for s in s_all))
+    _lcfo_run(cfg, st, st.psi, st.eps, eps_cut, lam, dtype)
+
+
+@pytest.mark.parametrize("dtype", ["fp64", "fp32"])
+def test_lcfo_basis_drops_a_planted_dependence(dtype):
+    """Seeded orbitals where, in fragments 1 and 6, orbital 2's core values are 0.3 phi_0 - 0.7 phi_1:
+    one direction of those overlaps vanishes and is dropped at lambda_cut = 1e-7."""
+    cfg = CASES["uneven"](precision="fp64")
+    st = oracle_state(cfg)
+    r = np.random.default_rng(20260603)
+    psi, eps = {}, {}
+    for f in range(st.frags.nfrag):
+        n = int(st.norb[f])
+        shp = (n,) + tuple(int(v) for v in st.frags.extent[f][::-1])
+        psi[f] = r.standard_normal(shp) * 0.05
+        eps[f] = np.sort(r.uniform(-0.5, 0.5, n))
+        if f in (1, 6):
+            cm = st.frags.core_mask(f)
+            psi[f][2][cm] = 0.3 * psi[f][0][cm] - 0.7 * psi[f][1][cm]
+    s_ref = _lcfo_run(cfg, st, psi, eps, 0.5, 1e-7, dtype)
+    for f in (1, 6):
+        assert abs(s_ref[f][-1]) < 1e-12  # the planted direction
