@@ -183,13 +183,19 @@ __device__ __forceinline__ T block_sum_t(T v, T *red) {
 
 // Cyclic Jacobi on the symmetric np x np matrix M (leading dimension ld), V <- V J, all arithmetic
 // in T.  Before each sweep the off-diagonal and diagonal sums of squares are formed; the solve
-// stops when off <= rel (dia + off) or after max_sweeps sweeps.  A rotation is skipped when
+// stops when off <= rel (dia + off), when off is already below stall (dia + off) and the last sweep
+// failed to cut it fourfold (the rounding floor: quadratic convergence would cut it by orders of
+// magnitude), or after max_sweeps sweeps.  A rotation is skipped when
 // |a_pq| <= skip sqrt|a_pp a_qq|.  rc, rs, red: shared scratch of T.
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
 template <typename T>
-__device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, T rel, T skip, T *red, T *rc, T *rs,
-                              int *rp, int *rq) {
+__device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, T rel, T stall, T skip, T *red, T *rc,
+                              T *rs, int *rp, int *rq) {
   const int tid = threadIdx.x;
   const int half = np / 2;
+  T prev = T(-1);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = T(0), dia = T(0);
     for (int t = tid; t < np * np; t += SNT) {
@@ -201,6 +207,8 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, T rel,
     off = block_sum_t<T>(off, red);
     dia = block_sum_t<T>(dia, red);
     if (!(off > rel * (dia + off))) break;
+    if (prev >= T(0) && off <= stall * (dia + off) && off > T(0.25) * prev) break;
+    prev = off;
     for (int r = 0; r < np - 1; ++r) {
       if (tid < half) {
         int p, q;
@@ -219,9 +227,11 @@ __device__ void jacobi_sweeps(T *M, T *V, int np, int ld, int max_sweeps, T rel,
         const T app = M[p * ld + p], aqq = M[q * ld + q], apq = M[q * ld + p];
         T c = T(1), sn = T(0);
         if (apq != T(0) && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
+          // one division per rotation: sqrt(1 + tau^2) = (1 + tau^2) rsqrt(1 + tau^2), c = rsqrt(1 + t^2)
           const T tau = (aqq - app) / (T(2) * apq);
-          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-          c = T(1) / sqrt(T(1) + t * t);
+          const T w = T(1) + tau * tau;
+          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + w * rsqrt_t(w));
+          c = rsqrt_t(T(1) + t * t);
           sn = t * c;
         }
         rp[tid] = p;
@@ -383,7 +393,7 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
   __syncthreads();
 
   // 5a. FP32 Jacobi to the FP32 rounding floor
-  jacobi_sweeps<float>(Mf, Vf, np, ld, 30, 1e-12f, 1e-9f, redf, rcf, rsf, rp, rq);
+  jacobi_sweeps<float>(Mf, Vf, np, ld, 30, 1e-12f, 0.f, 1e-9f, redf, rcf, rsf, rp, rq);
   // 5b. Q = Q32 (3 I - Q32^T Q32) / 2 in FP64 (orthonormal to FP64 rounding; Q32^T Q32 = I + O(1e-7))
   for (int t = tid; t < np * np; t += SNT) {
     const int i = t / np, j = t - i * np;
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
   }
   __syncthreads();
   // 5d. FP64 Jacobi from there
-  jacobi_sweeps<double>(M2, M0, np, ld, fp64_sweeps, 1e-30, 1e-18, red, rc, rs, rp, rq);
+  jacobi_sweeps<double>(M2, M0, np, ld, fp64_sweeps, 1e-30, 1e-20, 1e-18, red, rc, rs, rp, rq);
 
   // 6. sort ascending (rank by value, ties by index) and C = L^-T V
   __shared__ int rank[DC_MAX_NORB];
@@ -684,6 +694,7 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   double *V = S + DC_MAX_NORB * LD;                   // [np][LD] eigenvectors
   double *tile = V + DC_MAX_NORB * LD;                // [nsel][LTS]
   __shared__ double red[SNT / 32], rc[32], rs[32], sv[DC_MAX_NORB];
+  __shared__ float redf[SNT / 32], rcf[32], rsf[32];
   __shared__ long long redl[SNT / 32];
   __shared__ int rp[32], rq[32], sel[DC_MAX_NORB], perm[DC_MAX_NORB], nsel_s;
   const int f = blockIdx.x, tid = threadIdx.x;
@@ -723,9 +734,15 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
         int i, j;
         tri_ij(t, nsel, i, j);
         const double *a = tile + i * LTS, *b = tile + j * LTS;
-        double sum = 0.0;
-        for (int p = 0; p < LCH; ++p) sum += a[p] * b[p];
-        acc[r] += sum;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;  // four independent FP64 chains
+#pragma unroll 4
+        for (int p = 0; p < LCH; p += 4) {
+          s0 = fma(a[p], b[p], s0);
+          s1 = fma(a[p + 1], b[p + 1], s1);
+          s2 = fma(a[p + 2], b[p + 2], s2);
+          s3 = fma(a[p + 3], b[p + 3], s3);
+        }
+        acc[r] += (s0 + s1) + (s2 + s3);
       }
     }
     __syncthreads();
@@ -748,9 +765,94 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   }
   __syncthreads();
 
-  // 2. S = U diag(s) U^T (FP64 Jacobi to convergence)
-  if (np > 0) jacobi_sweeps<double>(S, V, np, LD, 40, 1e-30, 1e-18, red, rc, rs, rp, rq);
-  for (int i = tid; i < nsel; i += SNT) sv[i] = S[i * LD + i];
+  // 2. S = U diag(s) U^T.  As in the subspace solve: FP32 Jacobi on a float copy to the FP32 floor,
+  // one FP64 Newton-Schulz step makes its vectors Q orthonormal to FP64 rounding, and FP64 Jacobi on
+  // B = Q^T S Q (off-diagonal ~1e-7) converges quadratically, accumulating U = Q J.  The tile's space
+  // is idle here: it holds the float copies, then B.  Every FP64 product goes through registers
+  // (at most RPT entries per thread), a barrier, and an in-place write.
+  if (np > 0) {
+    constexpr int RPT = (DC_MAX_NORB * DC_MAX_NORB + SNT - 1) / SNT;
+    float *Sf = reinterpret_cast<float *>(tile), *Vf = Sf + DC_MAX_NORB * LD;
+    double *B = tile;
+    double r[RPT];
+    for (int t = tid; t < np * np; t += SNT) {
+      const int i = t / np, j = t - i * np;
+      Sf[i * LD + j] = (float)S[i * LD + j];
+      Vf[i * LD + j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_sweeps<float>(Sf, Vf, np, LD, 30, 1e-12f, 0.f, 1e-9f, redf, rcf, rsf, rp, rq);
+    for (int t = tid; t < np * np; t += SNT) {
+      const int i = t / np, j = t - i * np;
+      V[i * LD + j] = (double)Vf[i * LD + j];  // Q32
+    }
+    __syncthreads();
+    // F = (3 I - Q32^T Q32) / 2 into B's space (the float copies are dead)
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      r[q] = 0.0;
+      if (t < np * np) {
+        const int i = t / np, j = t - i * np;
+        double a = 0.0;
+        for (int k = 0; k < np; ++k) a = fma(V[k * LD + i], V[k * LD + j], a);
+        r[q] = 0.5 * ((i == j ? 3.0 : 0.0) - a);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      if (t < np * np) B[(t / np) * LD + t % np] = r[q];
+    }
+    __syncthreads();
+    // Q = Q32 F (into V), W = S Q (into S), B = Q^T W (into B), each through registers
+    for (int stage = 0; stage < 3; ++stage) {
+      const double *X = stage == 0 ? V : (stage == 1 ? S : V);
+      const double *Y = stage == 0 ? B : (stage == 1 ? V : S);
+      double *Z = stage == 0 ? V : (stage == 1 ? S : B);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SNT;
+        r[q] = 0.0;
+        if (t < np * np) {
+          const int i = t / np, j = t - i * np;
+          double a = 0.0;
+          if (stage == 2)
+            for (int k = 0; k < np; ++k) a = fma(X[k * LD + i], Y[k * LD + j], a);  // Q^T W
+          else
+            for (int k = 0; k < np; ++k) a = fma(X[i * LD + k], Y[k * LD + j], a);
+          r[q] = a;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SNT;
+        if (t < np * np) Z[(t / np) * LD + t % np] = r[q];
+      }
+      __syncthreads();
+    }
+    // symmetrise B (equal to Q^T S Q up to rounding)
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      r[q] = 0.0;
+      if (t < np * np) {
+        const int i = t / np, j = t - i * np;
+        r[q] = 0.5 * (B[i * LD + j] + B[j * LD + i]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      if (t < np * np) B[(t / np) * LD + t % np] = r[q];
+    }
+    __syncthreads();
+    jacobi_sweeps<double>(B, V, np, LD, 40, 1e-30, 1e-20, 1e-18, red, rc, rs, rp, rq);
+    for (int i = tid; i < nsel; i += SNT) sv[i] = B[i * LD + i];
+  }
   __syncthreads();
 
   // 3. rank descending (ties by index), keep s > lambda_cut
@@ -775,14 +877,22 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   for (long long cp0 = 0; cp0 < ncore; cp0 += LCH) {
     if (m > 0) lcfo_tile<T>(D, psi, P, sel, nsel, ncore, cp0, tile);
     __syncthreads();
-    for (int t = tid; t < n * LCH; t += SNT) {
+    for (int t = tid; t < m * LCH; t += SNT) {  // kept rows: two independent FP64 chains per output
       const int k = t / LCH, p = t - k * LCH;
       const long long cp = cp0 + p;
-      if (cp >= ncore) continue;
-      double v = 0.0;
-      if (k < m)
-        for (int i = 0; i < nsel; ++i) v += tile[i * LTS + p] * S[i * LD + k];
-      out[(long long)k * ncore + cp] = v;
+      double v0 = 0.0, v1 = 0.0;
+      int i = 0;
+      for (; i + 1 < nsel; i += 2) {
+        v0 = fma(tile[i * LTS + p], S[i * LD + k], v0);
+        v1 = fma(tile[(i + 1) * LTS + p], S[(i + 1) * LD + k], v1);
+      }
+      if (i < nsel) v0 = fma(tile[i * LTS + p], S[i * LD + k], v0);
+      if (cp < ncore) out[(long long)k * ncore + cp] = v0 + v1;
+    }
+    for (int t = m * LCH + tid; t < n * LCH; t += SNT) {  // rows m <= k < n
+      const int k = t / LCH, p = t - k * LCH;
+      const long long cp = cp0 + p;
+      if (cp < ncore) out[(long long)k * ncore + cp] = 0.0;
     }
     __syncthreads();
   }
