@@ -227,6 +227,18 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
+def whole_job(seconds, ws, steps, dist, device):
+    """Replicas timing: the slowest rank's time for the timed steps (max over ranks) and the whole-job
+    throughput ws * steps / that time.  dist is torch.distributed (or None for one rank); the
+    reduction tensor lives on `device` ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    slowest = float(t.item())
+    return slowest, ws * steps / slowest
+
+
 HARTREE_EV = 27.211386245988  # eV per hartree (CODATA 2018)
 FP64_NOMINAL_TFLOPS = 1.25    # B300 FP64 dense, nominal (no measured FP64 peak is available)
 
@@ -318,12 +330,9 @@ def run_ours(args):
     prof = solver.profile_read()
     solver.profile(False)
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max, value = whole_job(ms * 1e-3, ws, args.steps, dist, "cuda")
+    ms_max *= 1e3
     ms_step = ms_max / args.steps
-    value = ws * args.steps / (ms_max / 1e3)
 
     # ---- the same steps in plain FP64: step time and energy difference per atom ----
     compare = None
@@ -361,10 +370,7 @@ def run_ours(args):
         solver.scf_step(hnp)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - w0
-    t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_val = ws * args.steps / float(t.item())
+    _, e2e_val = whole_job(e2e_s, ws, args.steps, dist, "cuda")
     nb = 8 * solver.layout.npts
 
     # ---- the DC-LCFO basis step (Sec. 2.3, Eqs. 6-7) on the final state, after the timed region ----
