@@ -522,3 +522,38 @@ def test_lcfo_basis_drops_a_planted_dependence(dtype):
     s_ref = _lcfo_run(cfg, st, psi, eps, 0.5, 1e-7, dtype)
     for f in (1, 6):
         assert abs(s_ref[f][-1]) < 1e-12  # the planted direction
+
+
+@pytest.mark.parametrize("which", ["none", "all"])
+def test_lcfo_basis_selection_extremes(which):
+    """eps_cut below every eigenvalue keeps nothing (zero rows, zero counts); above every one keeps
+    all orbitals of the periodic case (odd counts take the padded Jacobi)."""
+    cfg = CASES["periodic"](precision="fp64")
+    st = oracle_state(cfg)
+    r = np.random.default_rng(7)
+    psi, eps = {}, {}
+    for f in range(st.frags.nfrag):
+        n = int(st.norb[f])
+        psi[f] = r.standard_normal((n,) + tuple(int(v) for v in st.frags.extent[f][::-1])) * 0.1
+        eps[f] = np.sort(r.uniform(-0.5, 0.5, n))
+    cut = -1.0 if which == "none" else 1.0
+    _lcfo_run(cfg, st, psi, eps, cut, 1e-7, "fp64")
+
+
+def test_lcfo_basis_rejects_bad_arguments_and_writes_nothing():
+    cfg = CASES["wide"](precision="fp64")
+    with _solver(cfg) as s:
+        lib = s.lib
+        psi = torch.zeros(s.layout.psi_elems, dtype=torch.float64, device="cuda")
+        eps = torch.zeros(s.layout.nstates, dtype=torch.float64, device="cuda")
+        basis = torch.full((4096,), 7.0, dtype=torch.float64, device="cuda")
+        nb = torch.full((s.layout.nfrag,), -3, dtype=torch.int32, device="cuda")
+        p = lambda t: t.data_ptr()  # noqa: E731
+        assert lib.dc_lcfo_basis(s.ctx, p(psi), 0, p(eps), 0.0, -1e-7, p(basis), p(nb), None, None) == -1
+        assert b"lambda_cut" in lib.dc_last_error()
+        assert lib.dc_lcfo_basis(s.ctx, p(psi), 7, p(eps), 0.0, 1e-7, p(basis), p(nb), None, None) == -1
+        assert lib.dc_lcfo_basis(s.ctx, None, 0, p(eps), 0.0, 1e-7, p(basis), p(nb), None, None) == -1
+        assert lib.dc_lcfo_basis(s.ctx, p(psi), 0, p(eps), float("nan"), 1e-7, p(basis), p(nb), None, None) == -1
+        torch.cuda.synchronize()
+        assert torch.all(basis == 7.0) and torch.all(nb == -3)
+        assert lib.dc_lcfo_query(None, None, None) == -1
