@@ -212,6 +212,16 @@ int dc_set_state(dc_ctx *ctx, const void *d_psi, const double *d_eps, void *stre
  * Outputs (device, FP64): d_rho[npts]; d_q[nstates] and d_mu[1] may be NULL. */
 int dc_density(dc_ctx *ctx, double *d_rho, double *d_q, double *d_mu, void *stream);
 
+/* ---- failure detection ----------------------------------------------------------------- */
+/* Self-test of the library's bounded device waits; the paper has no counterpart.  It runs the grid
+ * barrier of the Fermi-level kernel on a launch one block short of the arrivals the barrier expects,
+ * so the wait can never complete: each block gives up after its bounded poll count (a fraction of a
+ * second to about a second), records the timeout in the context's device flags and returns.  The
+ * call then reads the flags, clears them and returns DC_ERR_TIMEOUT; the context stays usable.  It
+ * would return DC_OK only if the barrier passed, i.e. if the bound were broken.  DC_ERR_ARG for a
+ * NULL context. */
+int dc_selftest_wait(dc_ctx *ctx, void *stream);
+
 /* ---- DC-LCFO basis (Sec. 2.3, Eqs. 6-7) -------------------------------------------------- */
 /* Size of the basis output of dc_lcfo_basis: *basis_elems = sum over fragments of n_f |core_f|
  * (FP64 elements); h_off (host, nfrag entries, may be NULL) receives each fragment's element offset.

@@ -79,6 +79,7 @@ PROTOTYPES = {
     "dc_get_state": (C.c_int, [VP, VP, VP, VP]),
     "dc_set_state": (C.c_int, [VP, VP, VP, VP]),
     "dc_density": (C.c_int, [VP, VP, VP, VP, VP]),
+    "dc_selftest_wait": (C.c_int, [VP, VP]),
     "dc_lcfo_query": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "dc_lcfo_basis": (C.c_int, [VP, VP, C.c_int, VP, C.c_double, C.c_double, VP, VP, VP, VP]),
     "dc_fermi_level_noalloc": (C.c_int, [VP, VP, C.c_int64, C.c_double, C.c_double, VP, VP, VP]),

@@ -851,6 +851,16 @@ int dc_density(dc_ctx *c, double *d_rho, double *d_q, double *d_mu, void *stream
   return check_flags(c, s);
 }
 
+int dc_selftest_wait(dc_ctx *c, void *stream) {
+  if (!c) {
+    dc_set_error("dc_selftest_wait: NULL context");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  DC_TRY(dck::launch_wait_selftest(c, s));
+  return check_flags(c, s);
+}
+
 int dc_lcfo_query(const dc_ctx *c, int64_t *basis_elems, int64_t *h_off) {
   if (!c || !basis_elems) {
     dc_set_error("dc_lcfo_query: NULL argument");

@@ -276,6 +276,7 @@ int launch_rotate_proj(dc_ctx *c, const T *cin, T *cout, cudaStream_t s);
 template <typename T>
 int launch_core_weights(dc_ctx *c, const T *psi, cudaStream_t s);
 int launch_fermi(dc_ctx *c, cudaStream_t s);
+int launch_wait_selftest(dc_ctx *c, cudaStream_t s);
 template <typename T>
 int launch_density(dc_ctx *c, const T *psi, double *rho, cudaStream_t s);
 

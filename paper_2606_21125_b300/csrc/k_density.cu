@@ -70,6 +70,13 @@ __device__ bool grid_sync(unsigned *count, unsigned *gen, unsigned nblocks, unsi
   return ok != 0;
 }
 
+// Failure-detection self-test: every block arrives at a grid barrier that expects one arrival more
+// than the launch has, so no block can pass; each gives up after its bounded poll count, sets
+// DC_FLAG_TIMEOUT and returns.  Nothing after the barrier runs.
+__global__ void k_wait_selftest(unsigned *bar, unsigned *flags, unsigned nexpect) {
+  if (!grid_sync(bar, bar + 1, nexpect, flags)) return;
+}
+
 __device__ __forceinline__ double fermi_occ(double e, double mu, double kT) {
   return 0.5 * (1.0 - tanh(0.5 * (e - mu) / kT));
 }
@@ -314,6 +321,14 @@ int launch_fermi(dc_ctx *c, cudaStream_t s) {
   double *occ = c->d_occ;
   void *args[] = {&eps, &q, &nst, &ne, &kT, &partials, &bar, &flags, &mu, &occ};
   DC_CUDA(cudaLaunchCooperativeKernel((const void *)k_fermi, dim3(grid), dim3(QNT), args, 0, s));
+  return DC_OK;
+}
+
+int launch_wait_selftest(dc_ctx *c, cudaStream_t s) {
+  DC_CUDA(cudaMemsetAsync(c->d_flags + 1, 0, 2 * sizeof(unsigned), s));
+  k_wait_selftest<<<2, 32, 0, s>>>(c->d_flags + 1, c->d_flags, 3u);  // two blocks, three expected
+  DC_CUDA(cudaGetLastError());
+  DC_CUDA(cudaMemsetAsync(c->d_flags + 1, 0, 2 * sizeof(unsigned), s));
   return DC_OK;
 }
 
