@@ -105,15 +105,22 @@ __device__ __forceinline__ int toff(int r, int k, int kstride) {
   return (k >> 3) * kstride + (r >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// Three-word BF16 split of two values at once: y = h + m + l per lane (paired conversions).
+// Three-word BF16 split of two values at once: y = h + m + l per lane.  Each residual is one paired
+// FMA, y - h = fma(h, -1, y), exact like the scalar subtraction it replaces.
+__device__ __forceinline__ float2 bf2_to_f2(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
 __device__ __forceinline__ void split3x2(float y0, float y1, uint32_t &h, uint32_t &m, uint32_t &l) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 y = make_float2(y0, y1);
   const __nv_bfloat162 hb = __floats2bfloat162_rn(y0, y1);
-  const float r0 = y0 - __low2float(hb), r1 = y1 - __high2float(hb);
-  const __nv_bfloat162 mb = __floats2bfloat162_rn(r0, r1);
-  const float s0 = r0 - __low2float(mb), s1 = r1 - __high2float(mb);
-  const __nv_bfloat162 lb = __floats2bfloat162_rn(s0, s1);
   h = *reinterpret_cast<const uint32_t *>(&hb);
+  const float2 r = __ffma2_rn(bf2_to_f2(h), m1, y);
+  const __nv_bfloat162 mb = __floats2bfloat162_rn(r.x, r.y);
   m = *reinterpret_cast<const uint32_t *>(&mb);
+  const float2 s = __ffma2_rn(bf2_to_f2(m), m1, r);
+  const __nv_bfloat162 lb = __floats2bfloat162_rn(s.x, s.y);
   l = *reinterpret_cast<const uint32_t *>(&lb);
 }
 
