@@ -300,7 +300,10 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   const int stage_max = (2 * nbmax + 128) * TKT * 2 + 3 * nbmax * TKT * 2;
   const int nslots = ((nmax + 7) / 8) * 128;                          // raw float4 slots per array
   float4 *rawring = reinterpret_cast<float4 *>(sm + nstages * stage_max);  // [nraw][2][nslots]
-  float *acc = reinterpret_cast<float *>(rawring + (size_t)nraw * 2 * nslots);  // [5][n][n + 1]
+  // [5][n][n + 1] FP32 item sums.  They share the raw ring's space: the drains write them only after
+  // the item's last tile has been converted (every copy into the ring has landed and been read), and
+  // the next item's first copies start after the barrier that follows their read-out.
+  float *acc = reinterpret_cast<float *>(rawring);
 
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)),
@@ -475,12 +478,13 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
   const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
   const size_t rawslot = 2 * (size_t)((nmax + 7) / 8) * 128 * sizeof(float4);
   const size_t accb = 5 * (size_t)nmax * (nmax + 1) * sizeof(float);
-  // deepest (BF16 stages, raw tiles) pair that fits: two stages keep the MMA and the conversion
-  // overlapped, the raw ring keeps up to three tiles of loads in flight
+  // deepest (BF16 stages, raw tiles) pair that fits: three stages let the conversion run two tiles
+  // ahead of the MMA (which pauses for each drain), the raw ring keeps up to three tiles of loads in
+  // flight; the FP32 item sums share the raw ring's space
   int nstages = 0, nraw = 0;
-  for (int ns : {2, 1}) {
+  for (int ns : {3, 2, 1}) {
     for (int nr : {3, 2, 1})
-      if (ns * stage + nr * rawslot + accb + 1024 <= 227 * 1024) {
+      if (ns * stage + std::max(nr * rawslot, accb) + 1024 <= 227 * 1024) {
         nstages = ns;
         nraw = nr;
         break;
@@ -491,7 +495,7 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     dc_set_error("mixed-precision Gram: tiles exceed shared memory");
     return DC_ERR_ARG;
   }
-  const size_t sm = nstages * stage + nraw * rawslot + accb;
+  const size_t sm = nstages * stage + std::max(nraw * rawslot, accb);
   const int grid = std::min(c->n_gram_items, c->sm_count);
   // column groups per drain warp: nb / 8 groups split over two warps per lane group
   const int ng = (nb / 8 + 1) / 2;
