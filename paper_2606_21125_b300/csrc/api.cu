@@ -527,11 +527,12 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   }
   // work lists for the Gram and rotation kernels
   {
-    // points per Gram partial: each chunk's sums are FP32 (tensor memory or SIMT pairs) and the
-    // chunks are added in FP64; DC_GRAM_CHUNK overrides (multiple of 64, 64..65536).  Tensor-memory
-    // FP32 accumulation carries an error that grows linearly with the chunk length (measured on
-    // B300), so the mixed path uses short chunks.
-    c->gram_chunk = 2048;
+    // points per Gram partial: each chunk's sums are FP32 (tensor memory drained every 256 points
+    // into FP32 registers, or SIMT pairs) and the chunks are added in FP64; DC_GRAM_CHUNK overrides
+    // (multiple of 64, 64..65536).  Tensor-memory FP32 accumulation carries an error that grows with
+    // the accumulated length, hence the 256-point drains; 4096-point chunks left the Si512 mixed-vs-FP64
+    // energy difference where 2048 had it (4.5e-7 Ha/atom) and halve the Gram's item boundaries.
+    c->gram_chunk = 4096;
     if (const char *gc = getenv("DC_GRAM_CHUNK")) {
       const int v = atoi(gc);
       if (v >= 64 && v <= 65536 && v % 64 == 0) c->gram_chunk = v;

@@ -6,7 +6,7 @@
 // FP32 accuracy are accumulated in FP32 in tensor memory:
 //   S = hh + hm + mh + hl + lh + mm            (lh = (hl)^T by symmetry)
 //   A = h.zh + h.zm + m.zh + h.zl + l.zh + m.zm (z = HY split the same way)
-// Persistent CTAs (one per SM, 16 warps) walk the (fragment, 2048-point item) list as a warp-
+// Persistent CTAs (one per SM, 16 warps) walk the (fragment, 4096-point item) list as a warp-
 // specialised pipeline.  Seven converter warps copy 64-point K-tiles of Y and HY into a ring of
 // raw FP32 tiles in shared memory (cp.async, 16 bytes per copy, up to three tiles ahead; each
 // thread later converts exactly the chunks it copied, so a per-thread wait is enough), split them
