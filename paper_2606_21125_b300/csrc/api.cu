@@ -532,7 +532,16 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
     // (multiple of 64, 64..65536).  Tensor-memory FP32 accumulation carries an error that grows with
     // the accumulated length, hence the 256-point drains; 4096-point chunks left the Si512 mixed-vs-FP64
     // energy difference where 2048 had it (4.5e-7 Ha/atom) and halve the Gram's item boundaries.
+    // Fewer than two items per SM leave the persistent Gram CTAs unbalanced, so small cells halve it.
     c->gram_chunk = 4096;
+    {
+      auto items = [&](long long chunk) {
+        long long k = 0;
+        for (const auto &D : c->h_desc) k += ((long long)D.E[0] * D.E[1] * D.E[2] + chunk - 1) / chunk;
+        return k;
+      };
+      while (c->gram_chunk > 512 && items(c->gram_chunk) < 2LL * c->sm_count) c->gram_chunk /= 2;
+    }
     if (const char *gc = getenv("DC_GRAM_CHUNK")) {
       const int v = atoi(gc);
       if (v >= 64 && v <= 65536 && v % 64 == 0) c->gram_chunk = v;
