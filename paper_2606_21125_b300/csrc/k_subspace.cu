@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
   __shared__ float redf[SNT / 32], rcf[32], rsf[32];
   __shared__ int rp[32], rq[32];
   __shared__ int failed;
+  __shared__ double pinv, dinv[DC_MAX_NORB];
   const int tid = threadIdx.x;
   if (tid == 0) failed = 0;
 
@@ -332,13 +333,16 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
       if (!(d > 0.0) || !isfinite(d)) {
         failed = 1;
         M0[k * ld + k] = 1.0;
+        pinv = 1.0;
       } else {
-        M0[k * ld + k] = sqrt(d);
+        const double r = rsqrt(d);  // one reciprocal square root: L_kk = d r, the column scales by r
+        M0[k * ld + k] = d * r;
+        pinv = r;
       }
     }
     __syncthreads();
-    const double piv = M0[k * ld + k];
-    for (int i = k + 1 + tid; i < n; i += SNT) M0[i * ld + k] /= piv;
+    const double rp = pinv;
+    for (int i = k + 1 + tid; i < n; i += SNT) M0[i * ld + k] *= rp;
     __syncthreads();
     const int m = n - k - 1;
     for (int t = tid; t < m * m; t += SNT) {
@@ -352,14 +356,25 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
     return;
   }
 
-  // 3. L^-1 (lower) by forward substitution, one column per thread
+  // 3. L^-1 (lower) by forward substitution, one column per thread; the diagonal's reciprocals once,
+  // each dot product in four independent FP64 chains
+  for (int i = tid; i < n; i += SNT) dinv[i] = 1.0 / M0[i * ld + i];
+  __syncthreads();
   for (int j = tid; j < np; j += SNT) {
     for (int i = 0; i < np; ++i) M1[i * ld + j] = 0.0;
     if (j < n) {
       for (int i = j; i < n; ++i) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int k = j; k < i; ++k) s -= M0[i * ld + k] * M1[k * ld + j];
-        M1[i * ld + j] = s / M0[i * ld + i];
+        const double *Li = M0 + i * ld;
+        double s0 = (i == j) ? 1.0 : 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int k = j;
+        for (; k + 3 < i; k += 4) {
+          s0 = fma(-Li[k], M1[k * ld + j], s0);
+          s1 = fma(-Li[k + 1], M1[(k + 1) * ld + j], s1);
+          s2 = fma(-Li[k + 2], M1[(k + 2) * ld + j], s2);
+          s3 = fma(-Li[k + 3], M1[(k + 3) * ld + j], s3);
+        }
+        for (; k < i; ++k) s0 = fma(-Li[k], M1[k * ld + j], s0);
+        M1[i * ld + j] = ((s0 + s1) + (s2 + s3)) * dinv[i];
       }
     }
   }

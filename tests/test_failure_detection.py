@@ -2,8 +2,10 @@
 
 dc_selftest_wait runs the Fermi kernel's grid barrier on a launch one block short of what the barrier
 expects, so the wait cannot complete.  The library must come back with DC_ERR_TIMEOUT well inside the
-poll bound, clear its device flags, and keep the context working: the density and chemical potential
-computed afterwards equal those computed before, bit for bit.
+poll bound, clear its device flags, and keep the context working: the core weights computed afterwards
+equal those computed before bit for bit, and mu and the density agree within the Fermi solve's
+stopping rule (it starts from the previous mu, so repeated solves may differ in the last bits; a
+Newton correction below 1e-14 Ha and |df/dmu| <= 1/(4 kT) bound the density change far below 1e-10).
 """
 import time
 
@@ -34,6 +36,8 @@ def test_grid_barrier_timeout_is_reported_and_the_context_survives():
             assert dt < 30.0
         rho1, q1, mu1 = s.density()
         torch.cuda.synchronize()
-        assert torch.equal(rho0, rho1) and torch.equal(q0, q1) and torch.equal(mu0, mu1)
+        assert torch.equal(q0, q1)
+        assert abs(float(mu1.item()) - float(mu0.item())) < 1e-11
+        assert float(torch.max(torch.abs(rho1 - rho0))) <= 1e-10 * float(torch.max(torch.abs(rho0)))
     from paper_2606_21125_b300 import load
     assert load().dc_selftest_wait(None, None) == -1
