@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   __syncthreads();
 
   // 2. S = U diag(s) U^T.  As in the subspace solve: FP32 Jacobi on a float copy to the FP32 floor,
-  // one FP64 Newton-Schulz step makes its vectors Q orthonormal to FP64 rounding, and FP64 Jacobi on
+  // two FP64 Newton-Schulz steps make its vectors Q orthonormal to FP64 rounding, and FP64 Jacobi on
   // B = Q^T S Q (off-diagonal ~1e-7) converges quadratically, accumulating U = Q J.  The tile's space
   // is idle here: it holds the float copies, then B.  Every FP64 product goes through registers
   // (at most RPT entries per thread), a barrier, and an in-place write.
@@ -802,30 +802,52 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
       V[i * LD + j] = (double)Vf[i * LD + j];  // Q32
     }
     __syncthreads();
-    // F = (3 I - Q32^T Q32) / 2 into B's space (the float copies are dead)
+    // Two Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2: the FP32 vectors' drift from orthonormality
+    // (up to ~1e-5 after many rotations) is squared twice, to FP64 rounding.  F goes through B's
+    // space (the float copies are dead), every product through registers.
+    for (int it = 0; it < 2; ++it) {
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int t = tid + q * SNT;
-      r[q] = 0.0;
-      if (t < np * np) {
-        const int i = t / np, j = t - i * np;
-        double a = 0.0;
-        for (int k = 0; k < np; ++k) a = fma(V[k * LD + i], V[k * LD + j], a);
-        r[q] = 0.5 * ((i == j ? 3.0 : 0.0) - a);
+      for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SNT;
+        r[q] = 0.0;
+        if (t < np * np) {
+          const int i = t / np, j = t - i * np;
+          double a = 0.0;
+          for (int k = 0; k < np; ++k) a = fma(V[k * LD + i], V[k * LD + j], a);
+          r[q] = 0.5 * ((i == j ? 3.0 : 0.0) - a);
+        }
       }
-    }
-    __syncthreads();
+      __syncthreads();
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int t = tid + q * SNT;
-      if (t < np * np) B[(t / np) * LD + t % np] = r[q];
+      for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SNT;
+        if (t < np * np) B[(t / np) * LD + t % np] = r[q];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SNT;
+        r[q] = 0.0;
+        if (t < np * np) {
+          const int i = t / np, j = t - i * np;
+          double a = 0.0;
+          for (int k = 0; k < np; ++k) a = fma(V[i * LD + k], B[k * LD + j], a);
+          r[q] = a;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int t = tid + q * SNT;
+        if (t < np * np) V[(t / np) * LD + t % np] = r[q];
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // Q = Q32 F (into V), W = S Q (into S), B = Q^T W (into B), each through registers
-    for (int stage = 0; stage < 3; ++stage) {
-      const double *X = stage == 0 ? V : (stage == 1 ? S : V);
-      const double *Y = stage == 0 ? B : (stage == 1 ? V : S);
-      double *Z = stage == 0 ? V : (stage == 1 ? S : B);
+    // W = S Q (into S), B = Q^T W (into B), each through registers
+    for (int stage = 1; stage < 3; ++stage) {
+      const double *X = stage == 1 ? S : V;
+      const double *Y = stage == 1 ? V : S;
+      double *Z = stage == 1 ? S : B;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int t = tid + q * SNT;

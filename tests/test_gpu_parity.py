@@ -557,3 +557,43 @@ def test_lcfo_basis_rejects_bad_arguments_and_writes_nothing():
         torch.cuda.synchronize()
         assert torch.all(basis == 7.0) and torch.all(nb == -3)
         assert lib.dc_lcfo_query(None, None, None) == -1
+
+
+def test_full_size_lcfo_sampled_si512():
+    """The DC-LCFO basis step at Si512 size (512 fragments of 22^3, 10^3 cores, 48 orbitals, FP32
+    block) on a seeded random block with seeded eigenvalues; a few fragments are recomputed by the
+    oracle from the same (FP32-rounded) values, with the tolerances above."""
+    from oracle import lcfo
+    cfg = workloads.make_config("si512", precision="fp32")
+    sample = [0, 301, 511]
+    st = oracle_state(cfg, subset=sample)
+    r = np.random.default_rng(11)
+    with _solver(cfg) as s:
+        host = (0.05 * r.standard_normal(s.layout.psi_elems, dtype=np.float32)).astype(np.float32)
+        eps_h = np.concatenate([np.sort(r.uniform(-0.5, 0.5, int(st.norb[f]))) for f in range(st.frags.nfrag)])
+        psi = torch.from_numpy(host).cuda()
+        eps = torch.from_numpy(eps_h).cuda()
+        basis, nb, sv, offs = s.lcfo_basis(psi, eps, 0.0, 1e-7)
+        torch.cuda.synchronize()
+        nb, sv = _np(nb), _np(sv)
+        poff, soff, p, so = {}, {}, 0, 0
+        for f in range(st.frags.nfrag):
+            n = int(st.norb[f])
+            poff[f], soff[f] = p, so
+            p += n * int(np.prod(st.frags.extent[f]))
+            so += n
+        rows = {f: _np(basis[offs[f]:offs[f] + int(st.norb[f]) * int(np.prod(st.frags.core[f]))]) for f in sample}
+    dV = st.grid.dV
+    for f in sample:
+        n = int(st.norb[f])
+        shp = (n,) + tuple(int(v) for v in st.frags.extent[f][::-1])
+        x = host[poff[f]:poff[f] + int(np.prod(shp))].astype(np.float64).reshape(shp)
+        e = eps_h[soff[f]:soff[f] + n]
+        s_ref, B_ref = lcfo.fragment_basis(st.frags, f, x, e, dV, 0.0, 1e-7)
+        assert not np.any((s_ref > 1e-7 / 3) & (s_ref < 3e-7))
+        m = B_ref.shape[0]
+        assert nb[f] == m
+        np.testing.assert_allclose(sv[soff[f]:soff[f] + len(s_ref)], s_ref, rtol=0, atol=1e-11 * np.max(s_ref))
+        B = rows[f].reshape(n, -1)[:m]
+        np.testing.assert_allclose(dV * B @ B.T, np.eye(m), rtol=0, atol=1e-9)
+        np.testing.assert_allclose(lcfo.span_projector(B, dV), lcfo.span_projector(B_ref, dV), rtol=0, atol=1e-8)
