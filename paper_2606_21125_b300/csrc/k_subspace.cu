@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   double *S = reinterpret_cast<double *>(smem_raw);  // [np][LD] overlap -> eigenvalues; then W
   double *V = S + DC_MAX_NORB * LD;                   // [np][LD] eigenvectors
   double *tile = V + DC_MAX_NORB * LD;                // [nsel][LTS]
-  __shared__ double red[SNT / 32], rc[32], rs[32], sv[DC_MAX_NORB];
+  __shared__ double red[SNT / 32], rc[32], rs[32], sv[DC_MAX_NORB], vn[DC_MAX_NORB];
   __shared__ float redf[SNT / 32], rcf[32], rsf[32];
   __shared__ long long redl[SNT / 32];
   __shared__ int rp[32], rq[32], sel[DC_MAX_NORB], perm[DC_MAX_NORB], nsel_s;
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   __syncthreads();
 
   // 2. S = U diag(s) U^T.  As in the subspace solve: FP32 Jacobi on a float copy to the FP32 floor,
-  // two FP64 Newton-Schulz steps make its vectors Q orthonormal to FP64 rounding, and FP64 Jacobi on
+  // one FP64 Newton-Schulz step makes its vectors Q orthonormal to ~1e-11, and FP64 Jacobi on
   // B = Q^T S Q (off-diagonal ~1e-7) converges quadratically, accumulating U = Q J.  The tile's space
   // is idle here: it holds the float copies, then B.  Every FP64 product goes through registers
   // (at most RPT entries per thread), a barrier, and an in-place write.
@@ -802,47 +802,46 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
       V[i * LD + j] = (double)Vf[i * LD + j];  // Q32
     }
     __syncthreads();
-    // Two Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2: the FP32 vectors' drift from orthonormality
-    // (up to ~1e-5 after many rotations) is squared twice, to FP64 rounding.  F goes through B's
-    // space (the float copies are dead), every product through registers.
-    for (int it = 0; it < 2; ++it) {
+    // One Newton-Schulz step Q <- Q (3 I - Q^T Q) / 2 takes the FP32 vectors' drift from
+    // orthonormality (up to ~1e-5 after many rotations) to ~1e-11; the eigenvalues below are then
+    // Rayleigh quotients normalised by |u_i|^2, which removes that residue to first order.  F goes
+    // through B's space (the float copies are dead), every product through registers.
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int t = tid + q * SNT;
-        r[q] = 0.0;
-        if (t < np * np) {
-          const int i = t / np, j = t - i * np;
-          double a = 0.0;
-          for (int k = 0; k < np; ++k) a = fma(V[k * LD + i], V[k * LD + j], a);
-          r[q] = 0.5 * ((i == j ? 3.0 : 0.0) - a);
-        }
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      r[q] = 0.0;
+      if (t < np * np) {
+        const int i = t / np, j = t - i * np;
+        double a = 0.0;
+        for (int k = 0; k < np; ++k) a = fma(V[k * LD + i], V[k * LD + j], a);
+        r[q] = 0.5 * ((i == j ? 3.0 : 0.0) - a);
       }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int t = tid + q * SNT;
-        if (t < np * np) B[(t / np) * LD + t % np] = r[q];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int t = tid + q * SNT;
-        r[q] = 0.0;
-        if (t < np * np) {
-          const int i = t / np, j = t - i * np;
-          double a = 0.0;
-          for (int k = 0; k < np; ++k) a = fma(V[i * LD + k], B[k * LD + j], a);
-          r[q] = a;
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int t = tid + q * SNT;
-        if (t < np * np) V[(t / np) * LD + t % np] = r[q];
-      }
-      __syncthreads();
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      if (t < np * np) B[(t / np) * LD + t % np] = r[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      r[q] = 0.0;
+      if (t < np * np) {
+        const int i = t / np, j = t - i * np;
+        double a = 0.0;
+        for (int k = 0; k < np; ++k) a = fma(V[i * LD + k], B[k * LD + j], a);
+        r[q] = a;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int t = tid + q * SNT;
+      if (t < np * np) V[(t / np) * LD + t % np] = r[q];
+    }
+    __syncthreads();
     // W = S Q (into S), B = Q^T W (into B), each through registers
     for (int stage = 1; stage < 3; ++stage) {
       const double *X = stage == 1 ? S : V;
@@ -888,7 +887,13 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
     }
     __syncthreads();
     jacobi_sweeps<double>(B, V, np, LD, 40, 1e-30, 1e-20, 1e-18, red, rc, rs, rp, rq);
-    for (int i = tid; i < nsel; i += SNT) sv[i] = B[i * LD + i];
+    // u_i = Q J e_i: B_ii = u_i^T S u_i, and s_i = B_ii / |u_i|^2; the columns are normalised
+    for (int i = tid; i < nsel; i += SNT) {
+      double nrm = 0.0;
+      for (int k = 0; k < np; ++k) nrm = fma(V[k * LD + i], V[k * LD + i], nrm);
+      sv[i] = B[i * LD + i] / nrm;
+      vn[i] = rsqrt(nrm);
+    }
   }
   __syncthreads();
 
@@ -906,7 +911,7 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   // W[i][k] = U[i][perm k] / sqrt(s_perm k) over the kept directions (into S's space)
   for (int t = tid; t < nsel * m; t += SNT) {
     const int i = t / m, k = t - i * m;
-    S[i * LD + k] = V[i * LD + perm[k]] / sqrt(sv[perm[k]]);
+    S[i * LD + k] = V[i * LD + perm[k]] * vn[perm[k]] / sqrt(sv[perm[k]]);
   }
   __syncthreads();
 
