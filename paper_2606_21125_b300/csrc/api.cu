@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots};
+                  c->d_dots, c->d_ig2, c->d_kerkw};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -582,6 +582,8 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(dmalloc(&c->d_rho_out, N));
   DC_TRY(dmalloc(&c->d_work, N));
   DC_TRY(dmalloc(&c->d_rhoiG, N));
+  DC_TRY(dmalloc(&c->d_ig2, N));
+  DC_TRY(dmalloc(&c->d_kerkw, N));
   DC_TRY(dmalloc(&c->d_cplx, N));
   if (cufftPlan3d(&c->plan_z2z, c->grid.n[2], c->grid.n[1], c->grid.n[0], CUFFT_Z2Z) != CUFFT_SUCCESS) {
     dc_set_error("cufftPlan3d failed");

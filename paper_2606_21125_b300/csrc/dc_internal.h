@@ -118,6 +118,8 @@ struct dc_ctx {
   // global grid arrays (FP64)
   double *d_vion = nullptr, *d_rho0 = nullptr, *d_veff = nullptr, *d_rho_out = nullptr, *d_work = nullptr;
   double2 *d_rhoiG = nullptr;  // rho_ion(G), full complex grid
+  double *d_ig2 = nullptr;     // 1/G^2 per grid index (0 at G = 0), set once
+  double *d_kerkw = nullptr;   // Kerker weight alpha G^2/(G^2 + q0^2)/N per grid index, set once
   double2 *d_cplx = nullptr;   // FFT work (full complex grid)
   cufftHandle plan_z2z = 0;
   bool have_plan = false;

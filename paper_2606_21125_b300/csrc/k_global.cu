@@ -42,14 +42,23 @@ __global__ void k_rho_ion_G(long long npts, int nx, int ny, int nz, double Lx, d
 }
 
 // out(G) = scale(G) * in(G) with scale = f/G^2 (0 at G=0)
-__global__ void k_poisson_scale(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz,
-                                const double2 *in, double factor, double2 *out) {
+// The G-dependent factors of the reciprocal-space stages, fixed for a context: 1/G^2 (0 at G = 0)
+// and the Kerker weight alpha G^2/(G^2 + q0^2), divided by N for the unnormalised inverse transform.
+__global__ void k_gtables(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
+                          double q0sq, double *ig2, double *kw) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= npts) return;
   double gx, gy, gz;
   const double g2 = gsq(idx, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
+  ig2[idx] = g2 > 0.0 ? 1.0 / g2 : 0.0;
+  kw[idx] = alpha * g2 / (g2 + q0sq) / (double)npts;
+}
+
+__global__ void k_poisson_scale(long long npts, const double *ig2, const double2 *in, double factor, double2 *out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npts) return;
   const double2 v = in[idx];
-  const double s = g2 > 0.0 ? factor / g2 : 0.0;
+  const double s = factor * ig2[idx];
   out[idx] = make_double2(s * v.x, s * v.y);
 }
 
@@ -219,17 +228,13 @@ struct FnEntropy {
     return -2.0 * q[i] * t;
   }
 };
-struct FnEs {  // 4 pi |rho(G)/N - rho_ion(G)|^2 / G^2 for G != 0
+struct FnEs {  // 4 pi |rho(G)/N - rho_ion(G)|^2 / G^2 for G != 0 (ig2 = 1/G^2, 0 at G = 0)
   const double2 *rG, *iG;
+  const double *ig2;
   double inv_n;
-  int nx, ny, nz;
-  double Lx, Ly, Lz;
   __device__ double operator()(long long i) const {
-    double gx, gy, gz;
-    const double g2 = gsq(i, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
-    if (!(g2 > 0.0)) return 0.0;
     const double re = rG[i].x * inv_n - iG[i].x, im = rG[i].y * inv_n - iG[i].y;
-    return 4.0 * M_PI * (re * re + im * im) / g2;
+    return 4.0 * M_PI * (re * re + im * im) * ig2[i];
   }
 };
 
@@ -251,14 +256,11 @@ __global__ void k_residual_cplx(long long n, const double *rho_out, const double
   if (i < n) out[i] = make_double2(rho_out[i] - rho_in[i], 0.0);
 }
 
-// Kerker weight alpha G^2/(G^2+q0^2), divided by N for the unnormalised inverse transform
-__global__ void k_kerker(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
-                         double q0sq, double2 *c) {
+// Kerker weight (tabulated: alpha G^2/(G^2+q0^2)/N for the unnormalised inverse transform)
+__global__ void k_kerker(long long npts, const double *kw, double2 *c) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= npts) return;
-  double gx, gy, gz;
-  const double g2 = gsq(idx, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
-  const double w = alpha * g2 / (g2 + q0sq) / (double)npts;
+  const double w = kw[idx];
   const double2 v = c[idx];
   c[idx] = make_double2(w * v.x, w * v.y);
 }
@@ -289,11 +291,13 @@ int launch_vion(dc_ctx *c, cudaStream_t s) {
   const int *n = c->grid.n;
   const double *L = c->grid.L;
   DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
+  k_gtables<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->params.mix_alpha,
+                                    c->params.kerker_q0 * c->params.kerker_q0, c->d_ig2, c->d_kerkw);
   k_rho_ion_G<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->natom, c->d_atom_pos,
                                       c->d_atom_species, c->d_species, c->nspecies, c->volume, c->d_rhoiG);
   DC_CUDA(cudaGetLastError());
   // V_loc(G) = -4 pi rho_ion(G)/G^2 ; V_loc(r) = Re sum_G V(G) e^{iG.r}
-  k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->d_rhoiG, -4.0 * M_PI, c->d_cplx);
+  k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, c->d_ig2, c->d_rhoiG, -4.0 * M_PI, c->d_cplx);
   DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   k_cplx_real<<<nblk(N), 256, 0, s>>>(N, c->d_cplx, 1.0, c->d_vion);
   // starting density: max(Re sum_G rho_ion(G) e^{iG.r}, 0) scaled to N_e
@@ -315,7 +319,7 @@ int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s) {
   if (c->params.hxc == DC_HXC_HARTREE_X) {
     k_real_to_cplx<<<nblk(N), 256, 0, s>>>(N, rho, c->d_cplx);
     DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
-    k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->d_cplx, 4.0 * M_PI, c->d_cplx);
+    k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, c->d_ig2, c->d_cplx, 4.0 * M_PI, c->d_cplx);
     DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   }
   k_veff<<<nblk(N), 256, 0, s>>>(N, c->d_vion, c->d_cplx, 1.0 / (double)N, rho, c->params.hxc, c->d_veff);
@@ -357,7 +361,7 @@ int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s) {
     DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
     k_real_to_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, c->d_cplx);
     DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
-    FnEs fe{c->d_cplx, c->d_rhoiG, 1.0 / (double)N, n[0], n[1], n[2], L[0], L[1], L[2]};
+    FnEs fe{c->d_cplx, c->d_rhoiG, c->d_ig2, 1.0 / (double)N};
     DC_TRY(reduce(fe, N, 0.5 * c->volume, sc + 3, c->d_partials, s));
   }
   k_energy_combine<<<1, 1, 0, s>>>(sc, c->params.hxc, c->params.kT);
@@ -378,7 +382,7 @@ int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s) {
   DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
   k_residual_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, rho_in, c->d_cplx);
   DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
-  k_kerker<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->params.mix_alpha, q0 * q0, c->d_cplx);
+  k_kerker<<<nblk(N), 256, 0, s>>>(N, c->d_kerkw, c->d_cplx);
   DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   k_add_real<<<nblk(N), 256, 0, s>>>(N, rho_in, c->d_cplx);
   DC_CUDA(cudaGetLastError());
