@@ -129,10 +129,14 @@ __global__ void __launch_bounds__(QNT) k_fermi(const double *eps, const double *
   // Safeguarded Newton: every iteration evaluates N(mu) and dN/dmu in one pass, shrinks the bracket
   // by the sign of N - N_e, and takes the Newton step when it stays inside the bracket (bisection
   // otherwise).  Starts from the previous mu when that lies in the bracket.  Converged when the
-  // Newton correction is below 1e-14 Ha or the bracket below 1e-13 Ha.
+  // Newton correction is below 1e-14 Ha, the bracket below 1e-13 Ha, or the correction has reached the
+  // rounding floor of the FP64 electron count (~1e-13 Ha for 1e4-1e5 states): below 1e-10 Ha and no
+  // longer at least ten times smaller than the one before (quadratic convergence shrinks it by orders
+  // of magnitude until then).  Every block reads the same sums, so every block takes the same exit.
   double *pacc = partials + 2 * nb;  // [2][2 nb]
   const double guess = __ldcg(mu_out);
   double mu = (guess > lo && guess < hi) ? guess : 0.5 * (lo + hi);
+  double prev = 1e300;  // |Newton correction| of the previous iteration
   for (int itn = 0; itn < 200; ++itn) {
     double s = 0.0, ds = 0.0;
     for (int p = base; p < nst; p += stride) {
@@ -161,21 +165,37 @@ __global__ void __launch_bounds__(QNT) k_fermi(const double *eps, const double *
       pa[2 * blockIdx.x + 1] = dt;
     }
     if (!grid_sync(bar, bar + 1, nb, flags)) return;
-    double tot = 0.0, dtot = 0.0;
-    for (int b = 0; b < nb; ++b) {
-      tot += __ldcg(&pa[2 * b]);
-      dtot += __ldcg(&pa[2 * b + 1]);
+    // every block adds the block partials in the same fixed order: warp 0's lanes stride over the
+    // blocks (independent loads), then a shuffle tree; lane 0's result is shared through red
+    if (threadIdx.x < 32) {
+      double t = 0.0, dt = 0.0;
+      for (int b = threadIdx.x; b < nb; b += 32) {
+        t += __ldcg(&pa[2 * b]);
+        dt += __ldcg(&pa[2 * b + 1]);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+        dt += __shfl_xor_sync(0xffffffffu, dt, o);
+      }
+      if (threadIdx.x == 0) {
+        red[0] = t;
+        red2[0] = dt;
+      }
     }
+    __syncthreads();
+    const double tot = red[0], dtot = red2[0];
     const double r = tot - ne;
     if (r < 0.0) lo = mu;
     else hi = mu;
     const double step = dtot > 0.0 ? r / dtot : 0.0;
     double nm = mu - step;
     const bool newton_ok = dtot > 0.0 && nm > lo && nm < hi;
-    if (r == 0.0 || (newton_ok && fabs(step) < 1e-14) || hi - lo < 1e-13) {
+    const bool floor = dtot > 0.0 && fabs(step) < 1e-10 && fabs(step) > 0.1 * prev;
+    if (r == 0.0 || (newton_ok && fabs(step) < 1e-14) || hi - lo < 1e-13 || floor) {
       if (newton_ok) mu = nm;
       break;
     }
+    prev = dtot > 0.0 ? fabs(step) : 1e300;
     mu = newton_ok ? nm : 0.5 * (lo + hi);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
