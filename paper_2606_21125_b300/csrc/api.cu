@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots, c->d_ig2, c->d_kerkw};
+                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -345,7 +345,8 @@ int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
   const double N8 = 8.0 * (double)c->npts;
   {
     StageScope sc(c, DC_STAGE_POTENTIAL, s, 7.0 * N8, 3);
-    DC_TRY(dck::launch_potential(c, rin, s));
+    // with the Hartree term the input density's spectrum is kept for the Kerker residual below
+    DC_TRY(dck::launch_potential(c, rin, s, c->params.hxc == DC_HXC_HARTREE_X ? c->d_rhoinG : nullptr));
   }
   {
     StageScope sc(c, DC_STAGE_GATHER, s, 24.0 * (double)c->layout.frag_points, 1);
@@ -356,7 +357,7 @@ int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
   {
     StageScope sc(c, DC_STAGE_ENERGY, s, 13.0 * N8, 17);
     DC_TRY(dck::launch_energy(c, rin, s));
-    DC_TRY(dck::launch_mix(c, rin, s));
+    DC_TRY(dck::launch_mix(c, rin, s, c->params.hxc == DC_HXC_HARTREE_X ? c->d_rhoinG : nullptr));
   }
   DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned, c->d_scalar, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned + 20, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -584,6 +585,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(dmalloc(&c->d_rhoiG, N));
   DC_TRY(dmalloc(&c->d_ig2, N));
   DC_TRY(dmalloc(&c->d_kerkw, N));
+  DC_TRY(dmalloc(&c->d_rhoinG, N));
   DC_TRY(dmalloc(&c->d_cplx, N));
   if (cufftPlan3d(&c->plan_z2z, c->grid.n[2], c->grid.n[1], c->grid.n[0], CUFFT_Z2Z) != CUFFT_SUCCESS) {
     dc_set_error("cufftPlan3d failed");

@@ -120,6 +120,7 @@ struct dc_ctx {
   double2 *d_rhoiG = nullptr;  // rho_ion(G), full complex grid
   double *d_ig2 = nullptr;     // 1/G^2 per grid index (0 at G = 0), set once
   double *d_kerkw = nullptr;   // Kerker weight alpha G^2/(G^2 + q0^2)/N per grid index, set once
+  double2 *d_rhoinG = nullptr; // the step's input density in G space (unnormalised forward FFT)
   double2 *d_cplx = nullptr;   // FFT work (full complex grid)
   cufftHandle plan_z2z = 0;
   bool have_plan = false;
@@ -240,11 +241,11 @@ cudaError_t dc_set_smem(const void *func, size_t bytes);
 namespace dck {
 // global stages
 int launch_vion(dc_ctx *c, cudaStream_t s);
-int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s);
+int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG = nullptr);
 int launch_gather(dc_ctx *c, cudaStream_t s);
 int launch_gather_plain(dc_ctx *c, const double *V, double *vf64, float *vf32, cudaStream_t s);
 int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s);
-int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s);
+int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s, const double2 *rho_in_G = nullptr);
 int launch_init_psi(dc_ctx *c, double *psi64, cudaStream_t s);
 int launch_convert(const double *src, float *dst, long long n, cudaStream_t s);
 int launch_convert(const float *src, double *dst, long long n, cudaStream_t s);

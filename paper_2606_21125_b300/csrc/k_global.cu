@@ -265,6 +265,11 @@ __global__ void k_kerker(long long npts, const double *kw, double2 *c) {
   c[idx] = make_double2(w * v.x, w * v.y);
 }
 
+__global__ void k_sub_cplx(long long n, const double2 *b, double2 *a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
+}
+
 __global__ void k_add_real(long long n, double *rho_in, const double2 *d) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) rho_in[i] += d[i].x;
@@ -311,7 +316,7 @@ int launch_vion(dc_ctx *c, cudaStream_t s) {
   return DC_OK;
 }
 
-int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s) {
+int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG) {
   const long long N = c->npts;
   const int *n = c->grid.n;
   const double *L = c->grid.L;
@@ -319,6 +324,7 @@ int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s) {
   if (c->params.hxc == DC_HXC_HARTREE_X) {
     k_real_to_cplx<<<nblk(N), 256, 0, s>>>(N, rho, c->d_cplx);
     DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
+    if (save_rhoG) DC_CUDA(cudaMemcpyAsync(save_rhoG, c->d_cplx, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
     k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, c->d_ig2, c->d_cplx, 4.0 * M_PI, c->d_cplx);
     DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   }
@@ -369,7 +375,10 @@ int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s) {
   return DC_OK;
 }
 
-int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s) {
+// rho_in_G: the spectrum of rho_in from this step's potential stage, with c->d_cplx still holding the
+// energy stage's spectrum of rho_out; the residual's spectrum is then their difference (linearity of
+// the transform) and its forward transform is skipped.  nullptr: transform the residual.
+int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s, const double2 *rho_in_G) {
   const long long N = c->npts;
   const double q0 = c->params.kerker_q0;
   if (!(q0 > 0.0)) {
@@ -380,8 +389,12 @@ int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s) {
   const int *n = c->grid.n;
   const double *L = c->grid.L;
   DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
-  k_residual_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, rho_in, c->d_cplx);
-  DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
+  if (rho_in_G) {
+    k_sub_cplx<<<nblk(N), 256, 0, s>>>(N, rho_in_G, c->d_cplx);
+  } else {
+    k_residual_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, rho_in, c->d_cplx);
+    DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
+  }
   k_kerker<<<nblk(N), 256, 0, s>>>(N, c->d_kerkw, c->d_cplx);
   DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   k_add_real<<<nblk(N), 256, 0, s>>>(N, rho_in, c->d_cplx);
