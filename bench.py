@@ -8,8 +8,10 @@ mixing.  The orbital block (1.05 GB in FP32) is larger than L2, so no L2 flush i
 steps.
 
 Output: one JSON line (rank 0).  ``value`` is SCF steps per second summed over ranks (each rank runs
-its own replica: weak scaling, no collective on the data path).  ``--impl reference`` times the FP64
-CPU oracle on a bounded sample of the same workload (fragments sampled, global stages whole).
+its own replica: weak scaling, no collective on the data path), timed with CUDA events over K steps
+with no per-stage events; a second pass of K steps with per-stage events gives the stage split and the
+stencil's launch durations for the roofline.  ``--impl reference`` times the FP64 CPU oracle on the
+host's cores (fragments in parallel processes) on a bounded, stride-chosen sample of the same workload.
 """
 from __future__ import annotations
 
@@ -55,7 +57,9 @@ def parse():
     p.add_argument("--workload", default="si512", choices=sorted(WORKLOAD_TEXT))
     p.add_argument("--precision", default="mixed", choices=["fp32", "fp64", "mixed"],
                    help="mixed (default): FP32 stencil, 3xBF16 tensor-core Gram, FP64 subspace and Fermi level")
-    p.add_argument("--sample-frags", type=int, default=8, help="fragments in the oracle's timed sample")
+    p.add_argument("--sample-frags", type=int, default=0,
+                   help="fragments in the oracle's timed sample (0: every fragment for cpu_baseline up to 512 "
+                        "fragments, two per host process for --impl reference)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="skip the FP64 comparison run")
     p.add_argument("--shape", default=None,
@@ -145,59 +149,76 @@ def kernel_traffic(kernel_file):
 # ------------------------------------------------------------------------------------------------
 # CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ------------------------------------------------------------------------------------------------
-class OracleSample:
-    """The FP64 oracle timed on `k` stride-chosen fragments plus every global stage.
+class OracleRun:
+    """The FP64 oracle's SCF step on the host's cores.
 
-    One sampled step = V_eff (FFT Poisson + exchange) + one CheFSI pass on the k fragments + their
-    core weights and densities + Fermi level + energy + mixing; the fragment part is scaled by F/k.
+    Fragments are solved by ``oracle.pool.FragmentPool`` (one spawn process per core, one BLAS thread
+    each); the global stages (V_eff by FFT Poisson + exchange, Fermi level, energy, residual, mixing) run
+    in this process.  ``sample=None`` runs every fragment; otherwise ``sample`` stride-chosen fragments
+    run and the fragment-parallel part of the step is scaled by F / sample (labelled extrapolated).
+    The starting Rayleigh-Ritz of each fragment is set-up, not timed.
     """
 
-    def __init__(self, cfg, k):
+    def __init__(self, cfg, sample=None, nproc=None):
         from oracle import scf
+        from oracle.pool import FragmentPool
         self.cfg = cfg
         nf = int(cfg["num_fragment"][0] * cfg["num_fragment"][1] * cfg["num_fragment"][2])
-        k = max(1, min(k, nf))
-        self.sample = sorted(set(int(round(i * nf / k)) % nf for i in range(k)))
         self.nf = nf
-        self.st = scf.DCState(cfg, fragments_subset=self.sample)
-        V = self.st.veff(self.st.rho_in)
-        self.st.initial_rr(V)
+        if sample is None or sample >= nf:
+            self.frags = list(range(nf))
+        else:
+            k = max(1, int(sample))
+            self.frags = sorted(set(int(round(i * nf / k)) % nf for i in range(k)))
+        self.scale = nf / len(self.frags)
+        self.st = scf.DCState(cfg, fragments_subset=[])  # global arrays only
+        self.ne = self.st.ne / self.scale  # electrons of the sampled fragments, so that mu stays in range
+        self.pool = FragmentPool(cfg, self.frags, nproc)
+        self.pool.initial_rr(self.st.veff(self.st.rho_in))
 
     def step(self):
+        import numpy as np
         from oracle import energy, fermi
         st = self.st
         t0 = time.perf_counter()
         V = st.veff(st.rho_in)
         t1 = time.perf_counter()
-        st.solve(V, int(self.cfg["n_pass"]))
+        res = self.pool.solve(V, int(self.cfg["n_pass"]))
         t2 = time.perf_counter()
-        q, mu, occ, rho_part = st.density_stage()
-        import numpy as np
-        eps_all = np.concatenate([st.eps[f] for f in st.active])
-        q_all = np.concatenate([q[f] for f in st.active])
-        occ_all = np.concatenate([occ[f] for f in st.active])
-        eb = energy.band_sum(eps_all, q_all, occ_all)
-        energy.total_energy(st.grid, st.hxc, eb, V, rho_part, st.rhoiG)
-        fermi.entropy(eps_all, q_all, mu, st.kT)
-        energy.residual(st.grid, rho_part, st.rho_in, st.ne)
-        energy.mix(st.rho_in, rho_part, 0.0)
+        eps_all = np.concatenate([res[f][0] for f in self.frags])
+        q_all = np.concatenate([res[f][1] for f in self.frags])
+        mu = fermi.find_mu(eps_all, q_all, self.ne, st.kT)
         t3 = time.perf_counter()
-        frag = (t2 - t1) * self.nf / len(self.sample)
-        return (t1 - t0) + (t3 - t2) + frag
+        dens = self.pool.core_density(mu)
+        t4 = time.perf_counter()
+        rho = np.zeros(st.grid.npts)
+        for f in self.frags:
+            rho[dens[f][0]] = dens[f][1]
+        rho = rho.reshape(st.grid.shape())
+        occ_all = fermi.occupation(eps_all, mu, st.kT)
+        eb = energy.band_sum(eps_all, q_all, occ_all)
+        energy.total_energy(st.grid, st.hxc, eb, V, rho, st.rhoiG)
+        fermi.entropy(eps_all, q_all, mu, st.kT)
+        energy.residual(st.grid, rho, st.rho_in, st.ne)
+        energy.mix(st.rho_in, rho, 0.0)  # alpha 0: the timed input stays the same from step to step
+        t5 = time.perf_counter()
+        return (t1 - t0) + (t3 - t2) + (t5 - t4) + ((t2 - t1) + (t4 - t3)) * self.scale
+
+    @property
+    def cores(self):
+        return self.pool.nproc
 
     def describe(self):
-        return (f"FP64 oracle: CheFSI pass on {len(self.sample)} of {self.nf} fragments (stride-chosen), "
-                f"scaled x{self.nf / len(self.sample):g}, plus the whole global stages (Poisson/exchange, Fermi, "
-                f"density, energy, mixing)")
+        base = (f"FP64 oracle on {self.pool.nproc} host processes (one BLAS thread each; host has {os.cpu_count()} "
+                f"cores): fragments solved in parallel, global stages (Poisson/exchange, Fermi, density assembly, "
+                f"energy, mixing) in the parent")
+        if self.scale == 1.0:
+            return base + f"; whole workload, all {self.nf} fragments"
+        return (base + f"; extrapolated: {len(self.frags)} of {self.nf} fragments (stride-chosen), the fragment-"
+                f"parallel part scaled x{self.scale:g}")
 
-
-def cpu_threads():
-    try:
-        from threadpoolctl import threadpool_info
-        n = max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
-    except Exception:
-        n = 1
-    return n
+    def close(self):
+        self.pool.close()
 
 
 def run_reference(args):
@@ -206,17 +227,20 @@ def run_reference(args):
         return
     import workloads
     cfg = workloads.make_config(args.workload, precision="fp64")
-    samp = OracleSample(cfg, args.sample_frags)
+    nproc = os.cpu_count() or 1
+    # a bounded sample per step (about two fragments per process) keeps K + W steps within minutes
+    samp = OracleRun(cfg, sample=args.sample_frags or 2 * nproc, nproc=nproc)
     for _ in range(args.warmup):
         samp.step()
     ts = [samp.step() for _ in range(args.steps)]
+    samp.close()
     sec = sum(ts) / len(ts)
     val = 1.0 / sec
     line = dict(impl="reference", metric=_metric(), value=val, unit="SCF steps/s", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=sec * 1e3, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=WORKLOAD_TEXT[args.workload], precision="fp64 (oracle)"),
-                cpu_baseline=dict(value=val, unit="SCF steps/s", cores=cpu_threads(), host_cores=os.cpu_count(),
+                cpu_baseline=dict(value=val, unit="SCF steps/s", cores=samp.cores, host_cores=os.cpu_count(),
                                   kind="oracle", sample=samp.describe()),
                 e2e=dict(value=val, unit="SCF steps/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -238,7 +262,7 @@ def whole_job(seconds, ws, steps, dist, device):
 
 
 HARTREE_EV = 27.211386245988  # eV per hartree (CODATA 2018)
-FP64_NOMINAL_TFLOPS = 1.25    # B300 FP64 dense, nominal (no measured FP64 peak is available)
+FP64_NOMINAL_TFLOPS = 1.25    # B300 FP64 dense, nominal; bench replaces it with the measured FMA rate
 
 
 def lcfo_measure(solver, mu, stream, reps=5):
@@ -273,6 +297,57 @@ def lcfo_measure(solver, mu, stream, reps=5):
                 roofline=dict(bound="alu", achieved=tflops, peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s (FP64)",
                               frac=tflops / FP64_NOMINAL_TFLOPS, peak_kind="nominal FP64 (no measured FP64 peak)",
                               fp64_fma_per_launch=fma))
+
+
+def fp64_peak(stream, reps=3):
+    """Measured FP64 FMA rate of this device (TFLOP/s, 2 flops per FMA): the library's FMA-chain probe,
+    one full wave of CTAs, timed with CUDA events on the launching stream (best of ``reps``)."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2606_21125_b300 import _lib, load
+    lib = load()
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fmas = C.c_int64(0)
+    iters = 1 << 16
+    best = float("inf")
+    sptr = C.c_void_p(stream.cuda_stream)
+    _lib.check("dc_fp64_fma_probe", lib.dc_fp64_fma_probe(iters // 16, C.c_void_p(sink.data_ptr()),
+                                                          C.byref(fmas), sptr))
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _lib.check("dc_fp64_fma_probe", lib.dc_fp64_fma_probe(iters, C.c_void_p(sink.data_ptr()), C.byref(fmas),
+                                                              sptr))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return 2.0 * fmas.value / (best * 1e-3) / 1e12
+
+
+def hpsi_measure(solver, stream, reps=10):
+    """dc_hpsi alone (the H-apply of every fragment and orbital of the state block: projections
+    <p|psi>, then the stencil + local + nonlocal kernel), timed with CUDA events over ``reps`` calls.
+    Algorithmic bytes per call: the projection pass reads the block once; the H-apply reads the block
+    and V_f and writes H psi.  The block (1.05 GB on Si512) exceeds L2, so no flush is needed."""
+    import torch
+    psi, _ = solver.get_state()
+    out = torch.empty_like(psi)
+    solver.hpsi(psi, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        solver.hpsi(psi, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    es = psi.element_size()
+    lay = solver.layout
+    by = es * (3.0 * lay.psi_elems + lay.frag_points)
+    return dict(ms=ms, bytes=by, gbs=by / (ms * 1e-3) / 1e9,
+                note="read psi (projections) + read psi, V_f and write H psi (stencil), per call")
 
 
 def run_ours(args):
@@ -310,12 +385,11 @@ def run_ours(args):
         solver.scf_step(rho)
     torch.cuda.synchronize()
 
-    # ---- timed region: K SCF steps with inputs resident in HBM ----
+    # ---- timed region: K SCF steps with inputs resident in HBM, no stage events ----
     sampler = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
     sampler.start()
-    solver.profile(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     stats = None
@@ -325,12 +399,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    prof = solver.profile_read()
-    solver.profile(False)
     ms = ev0.elapsed_time(ev1)
     ms_max, value = whole_job(ms * 1e-3, ws, args.steps, dist, "cuda")
     ms_max *= 1e3
     ms_step = ms_max / args.steps
+
+    # ---- the same K steps again with CUDA events around every stage (stage split and the stencil's
+    # launch durations for the roofline); this pass is not the headline ----
+    solver.profile(True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    pstats = None
+    for _ in range(args.steps):
+        pstats = solver.scf_step(rho)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    prof = solver.profile_read()
+    solver.profile(False)
+    prof_ms_step = p0.elapsed_time(p1) / args.steps
+    steps_done = args.warmup + 2 * args.steps
 
     # ---- the same steps in plain FP64: step time and energy difference per atom ----
     compare = None
@@ -339,7 +426,7 @@ def run_ours(args):
         ref.warmup()
         _, r64 = ref.initial()
         r64 = r64.clone()
-        for _ in range(args.warmup):
+        for _ in range(args.warmup + args.steps):
             ref.scf_step(r64)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,8 +439,8 @@ def run_ours(args):
         natom = len(cfg["pos"])
         compare = dict(precision="fp64", ms_per_step=e0.elapsed_time(e1) / args.steps,
                        speedup=(e0.elapsed_time(e1) / args.steps) / ms_step,
-                       dE_per_atom=abs(stats["E"] - s64["E"]) / natom, dmu=abs(stats["mu"] - s64["mu"]),
-                       steps_compared=args.warmup + args.steps)
+                       dE_per_atom=abs(pstats["E"] - s64["E"]) / natom, dmu=abs(pstats["mu"] - s64["mu"]),
+                       steps_compared=steps_done)
         ref.close()
 
     # ---- end to end through the public API with host buffers (H2D rho_in, D2H rho + stats) ----
@@ -371,16 +458,18 @@ def run_ours(args):
     _, e2e_val = whole_job(e2e_s, ws, args.steps, dist, "cuda")
     nb = 8 * solver.layout.npts
 
-    # ---- the DC-LCFO basis step (Sec. 2.3, Eqs. 6-7) on the final state, after the timed region ----
+    # ---- H psi alone, the DC-LCFO basis step, the measured FP64 rate (after the timed region) ----
+    hpsi_line = hpsi_measure(solver, stream)
     lcfo_line = lcfo_measure(solver, stats["mu"], stream)
+    fp64 = fp64_peak(stream)
+    lcfo_line["roofline"].update(peak=fp64, frac=lcfo_line["roofline"]["achieved"] / fp64,
+                                 peak_kind="measured FP64 FMA rate (dc_fp64_fma_probe, CUDA events)")
 
-    # ---- roofline of the dominant kernel (stencil H-apply, all launches of the timed region) ----
+    # ---- roofline of the dominant kernel (stencil H-apply, its launches in the profiled pass) ----
     peaks, peak_kind = measured_peaks()
     tun = solver.tuning()["fp64" if args.precision == "fp64" else "fp32"]
-    stencil_name = ("k_hpair (orbital-pair FP32 stencil + local + nonlocal H-apply, fused Chebyshev step)"
-                    if tun["kind"] >= 1 else "k_hstep (stencil + local + nonlocal H-apply, fused Chebyshev step)")
+    stencil_name = STENCIL_KINDS.get(tun["kind"], f"kind {tun['kind']}")
     stencil_name += f", {tun['threads']} threads x {tun['pairs']} point pairs"
-    stencil_name += {2: ", register-capped", 3: ", every projector record of a fragment staged once"}.get(tun["kind"], "")
     h = prof["hpsi"]
     achieved = h["bytes"] / (h["ms"] * 1e-3) / 1e9 if h["ms"] > 0 else 0.0
     traffic, traffic_note = kernel_traffic("k_hamiltonian.cu")
@@ -400,22 +489,42 @@ def run_ours(args):
                               frac=achieved / peaks["hbm_gbs"], peak_kind=peak_kind + " (hbm_gbs)",
                               traffic=traffic, traffic_note=traffic_note,
                               algorithmic_bytes_per_launch=per_launch_bytes, launches=h["launches"],
-                              avg_launch_ms=h["ms"] / max(1, h["launches"])),
+                              avg_launch_ms=h["ms"] / max(1, h["launches"]),
+                              timing="CUDA events around each stencil launch in a second pass of the same K "
+                                     "steps (the headline pass runs without events)"),
                 stages_ms_per_step={k: v["ms"] / args.steps for k, v in prof.items()},
+                profiled_pass_ms_per_step=prof_ms_step,
+                hpsi=hpsi_line,
                 e2e=dict(value=e2e_val, unit="SCF steps/s", h2d_bytes_per_step=nb, d2h_bytes_per_step=nb + 8 * 16),
-                gpu_launches=launches, init_s=init_s, fp64_compare=compare, lcfo=lcfo_line,
+                gpu_launches=launches, launches_counted="this library's kernels per profiled pass of K steps",
+                init_s=init_s, fp64_compare=compare, lcfo=lcfo_line,
+                fp64_measured_tflops=fp64,
                 last_step=dict(E_per_atom=stats["E"] / len(cfg["pos"]), mu=stats["mu"], drho=stats["drho"]),
                 clocks=clocks)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        samp = OracleSample(workloads.make_config(args.workload, precision="fp64"), args.sample_frags)
+        ocfg = workloads.make_config(args.workload, precision="fp64")
+        nf = int(np.prod(ocfg["num_fragment"]))
+        nproc = os.cpu_count() or 1
+        sample = args.sample_frags or (None if nf <= 512 else 16 * nproc)
+        samp = OracleRun(ocfg, sample=sample, nproc=nproc)
         sec = samp.step()
-        line["cpu_baseline"] = dict(value=1.0 / sec, unit="SCF steps/s", cores=cpu_threads(),
-                                    host_cores=os.cpu_count(), kind="oracle", sample=samp.describe())
+        line["cpu_baseline"] = dict(value=1.0 / sec, unit="SCF steps/s", cores=samp.cores,
+                                    host_cores=os.cpu_count(), kind="oracle", sample=samp.describe(),
+                                    seconds_per_step=sec)
+        samp.close()
     solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+STENCIL_KINDS = {
+    0: "k_hstep (stencil + local + nonlocal H-apply, fused Chebyshev step)",
+    1: "k_hpair (orbital-pair FP32 stencil + local + nonlocal H-apply, fused Chebyshev step)",
+    2: "k_hpair (orbital-pair FP32 stencil, fused Chebyshev step), register-capped",
+    3: "k_hpair (orbital-pair FP32 stencil, fused Chebyshev step), every projector record of a fragment staged once",
+}
 
 
 def main():

@@ -104,7 +104,13 @@ typedef struct {
  * (Ha, > 0).  mix_alpha: linear mixing weight in [0, 1]; 0 keeps rho_in fixed (the paper's fixed-density
  * DC, Sec. 2.5 use case 3).  seed: initial-orbital seed.  kerker_q0 (bohr^-1, >= 0): 0 gives plain
  * linear mixing; > 0 weights every Fourier component of the density residual by
- * mix_alpha G^2/(G^2 + q0^2) (Kerker preconditioning against long-wavelength charge sloshing). */
+ * mix_alpha G^2/(G^2 + q0^2) (Kerker preconditioning against long-wavelength charge sloshing).
+ * rank, nranks: the context's fragment shard (Sec. 2.5: fragments are distributed over processes).
+ * nranks = 0 or 1: the context solves every fragment.  nranks > 1 (at most the number of fragments):
+ * the context solves only the contiguous fragment range of `rank` (dc_query: frag_lo, frag_hi), chosen
+ * so that every rank's stencil work sum P_f n_f is about 1/nranks of the total; every rank still holds
+ * the global grid, maps and potentials.  The sharded SCF step is dc_step_local / dc_step_density /
+ * dc_step_finish with the caller's exchanges between them. */
 typedef struct {
   int precision;
   int cheb_degree;
@@ -115,6 +121,8 @@ typedef struct {
   double mix_alpha;
   uint64_t seed;
   double kerker_q0;
+  int rank;
+  int nranks;
 } dc_params_t;
 
 /* Sizes of everything a caller allocates for the calls below. */
@@ -128,6 +136,9 @@ typedef struct {
   int64_t natom_frag;  /* sum_f |A_f| (atoms whose projector touches fragment f) */
   int max_norb;        /* max_f n_f */
   int element_bytes;   /* 8 for DC_FP64, 4 otherwise */
+  int frag_lo, frag_hi;        /* fragments [frag_lo, frag_hi) are solved by this context (all of them
+                                  unless nranks > 1) */
+  int64_t state_lo, state_hi;  /* their states in per-state arrays */
 } dc_layout_t;
 
 /* Per-step results (host struct filled by dc_scf_step). */
@@ -149,7 +160,7 @@ typedef struct dc_ctx dc_ctx;
  * projector factors, the ionic potential V_loc and ion charge rho_ion(G) (on the device, via
  * cuFFT), the starting density (band-limited ion charge scaled to N_e) and the random starting
  * orbitals; allocate the orbital state and work blocks.  Synchronous.  On failure *out is NULL
- * and nothing is leaked.  Errors: DC_ERR_ARG (sizes, counts, >= 4096 fragments, n_f outside [1, 64], extents above 64),
+ * and nothing is leaked.  Errors: DC_ERR_ARG (sizes, counts, more than 4096 fragments, n_f outside [1, 64], extents above 64),
  * DC_ERR_OOM, DC_ERR_CUDA. */
 int dc_init(const dc_grid_t *grid, const dc_fragments_t *fragments, const dc_buffers_t *buffers,
             const dc_atoms_t *atoms, const dc_params_t *params, dc_ctx **out);
@@ -190,8 +201,20 @@ int dc_set_potential(dc_ctx *ctx, const double *d_veff, void *stream);
 int dc_hpsi(dc_ctx *ctx, const void *d_psi, void *d_hpsi, int dtype, void *stream);
 
 /* ---- fragment eigensolver (CheFSI) ------------------------------------------------------ */
-/* Rayleigh-Ritz of the current orbital block without filtering (used once on the random start). */
-int dc_subspace(dc_ctx *ctx, void *stream);
+/* Rayleigh-Ritz without filtering (Eq. 1 in the span of a block; Sec. 2.2 "orthonormalization" and
+ * "diagonalization"): per fragment S = <Y|Y> (dV-weighted), S = L L^T (FP64 Cholesky), Hs = L^-1 <Y|H Y> L^-T
+ * = Q diag(eps) Q^T (FP64 results, ascending eps), Y <- Y L^-T Q.  The Gram contractions run in the
+ * context precision (DC_MIXED: 3xBF16 words on tensor cores, FP32 accumulation).
+ *   d_psi == NULL: acts on the context's own orbital state (used once on the random start); d_eps (may
+ *                  be NULL) receives a copy of the Ritz values; dtype is ignored.
+ *   d_psi != NULL: a caller block in the dc_query layout (device), rotated in place, with element type
+ *                  dtype equal to the context's (DC_FP64 for an FP64 context, DC_FP32 otherwise);
+ *                  d_eps[nstates] (device, FP64, required) receives its Ritz values.  The context's own
+ *                  state, eigenvalues, core weights and mu are not changed; its work blocks and projection
+ *                  buffers are used as scratch.
+ * With nranks > 1 only the context's fragment range is processed.  Errors: DC_ERR_ARG (NULL context,
+ * wrong dtype, missing d_eps), DC_ERR_NOCONV (a Gram matrix not positive definite), DC_ERR_CUDA. */
+int dc_subspace(dc_ctx *ctx, void *d_psi, int dtype, double *d_eps, void *stream);
 /* n_pass CheFSI passes on every fragment in the current V_eff: degree-m scaled Chebyshev filter
  * with bounds from the previous Ritz values, Cholesky orthonormalisation of the Gram matrix,
  * Rayleigh-Ritz and rotation (Eq. 1).  Gram/RR in the context precision, subspace solves FP64. */
@@ -206,11 +229,20 @@ int dc_get_state(dc_ctx *ctx, void *d_psi, double *d_eps, void *stream);
 int dc_set_state(dc_ctx *ctx, const void *d_psi, const double *d_eps, void *stream);
 
 /* ---- density -------------------------------------------------------------------------- */
-/* From the current state: core weights q_i^f = <psi_i|1_core|psi_i>, the chemical potential with
- * sum_f sum_i 2 f((eps_i^f - mu)/kT) q_i^f = N_e (FP64 bisection, Sec. 2.2), and the
- * core-projected density rho_out(g) = sum_i 2 f_i^f psi_i^f(j)^2 with f = owner(g) (Eqs. 2-4).
- * Outputs (device, FP64): d_rho[npts]; d_q[nstates] and d_mu[1] may be NULL. */
-int dc_density(dc_ctx *ctx, double *d_rho, double *d_q, double *d_mu, void *stream);
+/* Core weights q_i^f = <psi_i|1_core|psi_i>, the chemical potential with
+ * sum_f sum_i 2 f((eps_i^f - mu)/kT) q_i^f = N_e (FP64 safeguarded Newton in the bisection bracket,
+ * Sec. 2.2), and the core-projected density rho_out(g) = sum_i 2 f_i^f psi_i^f(j)^2 with f = owner(g)
+ * (Eqs. 2-4).
+ *   d_psi == NULL: from the context's own state and eigenvalues (d_eps and dtype ignored); the
+ *                  context keeps q, the occupations and mu for its energy stage.
+ *   d_psi != NULL: from a caller block (dc_query layout, dtype equal to the context's element type) and
+ *                  its eigenvalues d_eps[nstates] (device, FP64, required); the context's own arrays
+ *                  are not changed.  Needs nranks = 1.
+ * Outputs (device, FP64): d_rho[npts] (required); d_q[nstates] and d_mu[1] may be NULL.
+ * Errors: DC_ERR_ARG, DC_ERR_TIMEOUT (the Fermi solve's bounded grid barrier), DC_ERR_NONFINITE,
+ * DC_ERR_CUDA. */
+int dc_density(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_eps, double *d_rho, double *d_q,
+               double *d_mu, void *stream);
 
 /* ---- failure detection ----------------------------------------------------------------- */
 /* Self-test of the library's bounded device waits; the paper has no counterpart.  It runs the grid
@@ -259,7 +291,10 @@ int dc_lcfo_basis(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_eps
  * the bracket; any value is accepted.  Synchronises the stream before returning.
  * Setup: the first call on each device looks up the scratch address (cudaGetSymbolAddress), the SM
  * count and the kernel's residency; a call with nstates = 0 does only that, so do it before any
- * stream capture begins.  Calls on one device share the scratch: calls that overlap in time
+ * stream capture begins.  The looked-up address belongs to the device's current primary context:
+ * after cudaDeviceReset (or any teardown of that context) the first call that meets the stale
+ * address fails with DC_ERR_CUDA and drops it, and the call after it looks the address up again, so
+ * callers that reset a device should repeat the nstates = 0 setup call.  Calls on one device share the scratch: calls that overlap in time
  * (several host threads, or streams not ordered with each other) race and must be serialised by
  * the caller.  Errors: DC_ERR_ARG (nstates outside [0, 2^31 - 1], NULL pointer, bad kT or n_elec),
  * DC_ERR_TIMEOUT, DC_ERR_NONFINITE, DC_ERR_CUDA. */
@@ -271,14 +306,36 @@ int dc_fermi_level_noalloc(const double *d_eps, const double *d_q, int64_t nstat
  * energies, and linear mixing written back: rho_in <- rho_in + alpha (rho_out - rho_in).
  * rho_in_out[npts] FP64 is a device pointer if rho_on_host == 0, else a host pointer (then
  * copied in and out on the stream inside the call).  *h_stats is filled (host); the stream is
- * synchronised.  Requires dc_warmup first (DC_ERR_STATE otherwise). */
+ * synchronised.  Requires dc_warmup first (DC_ERR_STATE otherwise) and nranks = 1 (a shard steps with
+ * the dc_step_* calls below; DC_ERR_ARG otherwise). */
 int dc_scf_step(dc_ctx *ctx, double *rho_in_out, int rho_on_host, dc_stats_t *h_stats, void *stream);
+
+/* ---- fragment-sharded SCF step (Sec. 2.2; Sec. 2.5: fragments distributed over processes) ------ */
+/* One SCF iteration of a context that owns fragments [frag_lo, frag_hi) of nranks, in three calls with
+ * two exchanges that the caller makes between them (e.g. NCCL all-reduce sums; every array below is
+ * zero outside the rank's own part, so a sum over ranks assembles the global array exactly):
+ *   dc_step_local:   V_eff[rho_in] (every rank, identical), the rank's fragments' n_pass CheFSI passes and
+ *                    core weights; writes d_eps[nstates] and d_q[nstates] (device, FP64), the rank's states
+ *                    [state_lo, state_hi) filled and every other entry 0.
+ *   -- caller: sum d_eps and d_q over ranks --
+ *   dc_step_density: mu from all states (the same solve on every rank, from the previous mu), occupations,
+ *                    and d_rho_part[npts] = rho_out on the rank's cores, 0 elsewhere; d_mu[1] may be NULL.
+ *   -- caller: sum d_rho_part over ranks into rho_out --
+ *   dc_step_finish:  energies, residual and mixing from rho_out (d_rho_out[npts], device) into
+ *                    d_rho_in_out[npts] (device), as dc_scf_step; fills *h_stats (host, may be NULL).
+ * With nranks = 1 the three calls equal dc_scf_step bit for bit.  Errors: DC_ERR_ARG (NULL pointers),
+ * DC_ERR_STATE (no warm-up), DC_ERR_NOCONV, DC_ERR_TIMEOUT, DC_ERR_NONFINITE, DC_ERR_CUDA. */
+int dc_step_local(dc_ctx *ctx, const double *d_rho_in, double *d_eps, double *d_q, void *stream);
+int dc_step_density(dc_ctx *ctx, const double *d_eps, const double *d_q, double *d_rho_part, double *d_mu,
+                    void *stream);
+int dc_step_finish(dc_ctx *ctx, double *d_rho_in_out, const double *d_rho_out, dc_stats_t *h_stats, void *stream);
 
 /* rho_out of the last dc_scf_step (device, FP64 [npts]). */
 int dc_get_rho_out(dc_ctx *ctx, double *d_rho, void *stream);
 
 /* ---- band-energy adjoint --------------------------------------------------------------- */
-/* E_b = sum_f sum_i occ_i <psi_i^f|H_f|psi_i^f> for a caller block d_psi (dtype), occupations
+/* Needs nranks = 1 (DC_ERR_ARG otherwise).
+ * E_b = sum_f sum_i occ_i <psi_i^f|H_f|psi_i^f> for a caller block d_psi (dtype), occupations
  * d_occ[nstates] (FP64, any values), potential d_V[npts] and per-atom strengths d_D[natom]
  * (FP64).  Writes h_Eb (host, may be NULL), d_dpsi = 2 occ_i dV H_f psi_i (dtype, may be NULL),
  * d_dV[npts] = dV sum over all fragments covering g of sum_i occ_i psi_i^2 (FP64, unweighted,
@@ -327,6 +384,15 @@ int dc_set_tuning(dc_ctx *ctx, int dtype, int kind, int threads, int pairs);
  * each counted once; host arrays of DC_NSTAGES entries, any may be NULL). */
 int dc_profile(dc_ctx *ctx, int enable);
 int dc_profile_read(dc_ctx *ctx, double *h_ms, int64_t *h_launches, double *h_bytes);
+
+/* ---- measurement helper ------------------------------------------------------------------ */
+/* FP64 issue-rate probe (the paper has no counterpart): launches, on `stream`, one full wave of CTAs on
+ * the current device in which every thread runs eight independent chains of `iters` FP64 FMAs, and
+ * writes the number of FMAs launched to *h_fmas (host).  The caller times the launch (e.g. CUDA events
+ * on the same stream) to get the device's measured FP64 FMA rate.  d_sink: one device double the kernel
+ * may write (it does not for the inputs it uses).  Errors: DC_ERR_ARG (iters < 1, NULL pointer),
+ * DC_ERR_CUDA. */
+int dc_fp64_fma_probe(int64_t iters, double *d_sink, int64_t *h_fmas, void *stream);
 
 #ifdef __cplusplus
 }

@@ -62,7 +62,8 @@ class DCSolver:
         self.precision = PRECISIONS[cfg["precision"]]
         pa = _lib.dc_params_t(self.precision, int(cfg["cheb_degree"]), int(cfg["n_pass"]), int(cfg["n_warmup"]),
                               HXCS[cfg["hxc"]], float(cfg["kT"]), float(cfg["mix_alpha"]), int(cfg["seed"]),
-                              float(cfg.get("kerker_q0", 0.0)))
+                              float(cfg.get("kerker_q0", 0.0)), int(cfg.get("rank", 0)),
+                              int(cfg.get("nranks", 1)))
         ctx = C.c_void_p()
         check("dc_init", lib.dc_init(C.byref(g), C.byref(fr), C.byref(bu), C.byref(at), C.byref(pa), C.byref(ctx)))
         self.ctx = ctx
@@ -152,8 +153,18 @@ class DCSolver:
                                                        _stream(stream)))
         return basis, nbasis, sv, list(offs)
 
-    def subspace(self, stream=None):
-        check("dc_subspace", self.lib.dc_subspace(self.ctx, _stream(stream)))
+    def subspace(self, psi=None, eps=None, stream=None):
+        """Rayleigh-Ritz without filtering.  ``psi=None``: of the context's own state.  Otherwise of the
+        caller block ``psi`` (rotated in place); the Ritz values go to ``eps`` (allocated if None) and
+        are returned."""
+        torch = _torch()
+        if psi is None:
+            check("dc_subspace", self.lib.dc_subspace(self.ctx, None, 0, _ptr(eps), _stream(stream)))
+            return eps
+        eps = torch.empty(self.layout.nstates, dtype=torch.float64, device=psi.device) if eps is None else eps
+        dt = DC_FP64 if psi.dtype == torch.float64 else DC_FP32
+        check("dc_subspace", self.lib.dc_subspace(self.ctx, _ptr(psi), dt, _ptr(eps), _stream(stream)))
+        return eps
 
     def chefsi(self, n_pass=1, stream=None):
         check("dc_chefsi", self.lib.dc_chefsi(self.ctx, int(n_pass), _stream(stream)))
@@ -171,13 +182,31 @@ class DCSolver:
     def set_state(self, psi=None, eps=None, stream=None):
         check("dc_set_state", self.lib.dc_set_state(self.ctx, _ptr(psi), _ptr(eps), _stream(stream)))
 
-    def density(self, stream=None):
+    def density(self, psi=None, eps=None, stream=None):
+        """(rho, q, mu) from the context's own state (``psi=None``) or from a caller block ``psi`` with its
+        eigenvalues ``eps``."""
         torch = _torch()
         rho = self.grid_tensor()
         q = torch.empty(self.layout.nstates, dtype=torch.float64, device="cuda")
         mu = torch.empty(1, dtype=torch.float64, device="cuda")
-        check("dc_density", self.lib.dc_density(self.ctx, _ptr(rho), _ptr(q), _ptr(mu), _stream(stream)))
+        dt = 0 if psi is None else (DC_FP64 if psi.dtype == torch.float64 else DC_FP32)
+        check("dc_density", self.lib.dc_density(self.ctx, _ptr(psi), dt, _ptr(eps), _ptr(rho), _ptr(q), _ptr(mu),
+                                                _stream(stream)))
         return rho, q, mu
+
+    # ---- fragment-sharded step (Sec. 2.5) ----------------------------------------------------
+    def step_local(self, rho_in, eps, q, stream=None):
+        check("dc_step_local", self.lib.dc_step_local(self.ctx, _ptr(rho_in), _ptr(eps), _ptr(q), _stream(stream)))
+
+    def step_density(self, eps, q, rho_part, mu=None, stream=None):
+        check("dc_step_density", self.lib.dc_step_density(self.ctx, _ptr(eps), _ptr(q), _ptr(rho_part), _ptr(mu),
+                                                          _stream(stream)))
+
+    def step_finish(self, rho_in, rho_out, stream=None):
+        st = _lib.dc_stats_t()
+        check("dc_step_finish", self.lib.dc_step_finish(self.ctx, _ptr(rho_in), _ptr(rho_out), C.byref(st),
+                                                        _stream(stream)))
+        return dict(E=st.E, F=st.F, eband=st.eband, mu=st.mu, drho=st.drho, ne=st.ne, step=st.step)
 
     def scf_step(self, rho, stream=None):
         """One SCF step; ``rho`` is a CUDA float64 tensor (updated in place) or a host numpy array."""
@@ -215,6 +244,16 @@ def fermi_level_noalloc(eps, q, n_elec, kT, mu, occ, stream=None):
     """``dc_fermi_level_noalloc``: mu and occupations from eigenvalues ``eps`` and core weights ``q``
     (CUDA float64 tensors of one length) into the caller's tensors ``mu`` (1 element, read as the
     starting guess) and ``occ``.  The library allocates nothing; this wrapper creates no tensors."""
+    torch = _torch()
+    for name, t in (("eps", eps), ("q", q), ("occ", occ), ("mu", mu)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"fermi_level_noalloc: {name} must be a contiguous CUDA float64 tensor")
+    if not (eps.device == q.device == occ.device == mu.device):
+        raise ValueError("fermi_level_noalloc: eps, q, occ and mu must be on one device")
+    if q.numel() != eps.numel() or occ.numel() != eps.numel():
+        raise ValueError("fermi_level_noalloc: eps, q and occ must have the same number of elements")
+    if mu.numel() < 1:
+        raise ValueError("fermi_level_noalloc: mu needs one element")
     lib = load()
     check("dc_fermi_level_noalloc", lib.dc_fermi_level_noalloc(_ptr(eps), _ptr(q), int(eps.numel()), float(n_elec),
                                                                float(kT), _ptr(mu), _ptr(occ), _stream(stream)))

@@ -36,13 +36,14 @@ class dc_atoms_t(C.Structure):
 class dc_params_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("cheb_degree", C.c_int), ("n_pass", C.c_int), ("n_warmup", C.c_int),
                 ("hxc", C.c_int), ("kT", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
-                ("kerker_q0", C.c_double)]
+                ("kerker_q0", C.c_double), ("rank", C.c_int), ("nranks", C.c_int)]
 
 
 class dc_layout_t(C.Structure):
     _fields_ = [("nfrag", C.c_int), ("natom", C.c_int), ("npts", C.c_int64), ("psi_elems", C.c_int64),
                 ("frag_points", C.c_int64), ("nstates", C.c_int64), ("natom_frag", C.c_int64),
-                ("max_norb", C.c_int), ("element_bytes", C.c_int)]
+                ("max_norb", C.c_int), ("element_bytes", C.c_int), ("frag_lo", C.c_int), ("frag_hi", C.c_int),
+                ("state_lo", C.c_int64), ("state_hi", C.c_int64)]
 
 
 class dc_stats_t(C.Structure):
@@ -73,12 +74,15 @@ PROTOTYPES = {
     "dc_potential": (C.c_int, [VP, VP, VP, VP]),
     "dc_set_potential": (C.c_int, [VP, VP, VP]),
     "dc_hpsi": (C.c_int, [VP, VP, VP, C.c_int, VP]),
-    "dc_subspace": (C.c_int, [VP, VP]),
+    "dc_subspace": (C.c_int, [VP, VP, C.c_int, VP, VP]),
     "dc_chefsi": (C.c_int, [VP, C.c_int, VP]),
     "dc_warmup": (C.c_int, [VP, VP]),
     "dc_get_state": (C.c_int, [VP, VP, VP, VP]),
     "dc_set_state": (C.c_int, [VP, VP, VP, VP]),
-    "dc_density": (C.c_int, [VP, VP, VP, VP, VP]),
+    "dc_density": (C.c_int, [VP, VP, C.c_int, VP, VP, VP, VP, VP]),
+    "dc_step_local": (C.c_int, [VP, VP, VP, VP, VP]),
+    "dc_step_density": (C.c_int, [VP, VP, VP, VP, VP, VP]),
+    "dc_step_finish": (C.c_int, [VP, VP, VP, C.POINTER(dc_stats_t), VP]),
     "dc_selftest_wait": (C.c_int, [VP, VP]),
     "dc_lcfo_query": (C.c_int, [VP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "dc_lcfo_basis": (C.c_int, [VP, VP, C.c_int, VP, C.c_double, C.c_double, VP, VP, VP, VP]),
@@ -90,6 +94,7 @@ PROTOTYPES = {
     "dc_set_tuning": (C.c_int, [VP, C.c_int, C.c_int, C.c_int, C.c_int]),
     "dc_profile": (C.c_int, [VP, C.c_int]),
     "dc_profile_read": (C.c_int, [VP, PD, C.POINTER(C.c_int64), PD]),
+    "dc_fp64_fma_probe": (C.c_int, [C.c_int64, VP, C.POINTER(C.c_int64), VP]),
 }
 
 STAGES = ["potential", "gather", "project", "hpsi", "gram", "subspace", "rotate", "density", "energy"]

@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG};
+                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -189,6 +189,43 @@ void destroy_graphs(dc_ctx *c) {
   c->graphs.clear();
 }
 
+// Algorithmic bytes and launches of this library's kernels in the global stages (cuFFT's own launches
+// are not counted; each transform is counted as one read and one write of the complex grid).
+// N = grid points; a complex grid is 16N bytes, a real one 8N.
+struct StageModel {
+  double bytes;
+  int launches;
+};
+StageModel potential_model(const dc_ctx *c, bool save_spectrum) {
+  const double N = (double)c->npts;
+  if (c->params.hxc != DC_HXC_HARTREE_X) return {16.0 * N, 1};  // k_veff: V_loc in, V_eff out
+  // k_real_to_cplx 24N, forward FFT 32N, [spectrum copy 32N], k_poisson_scale 40N, inverse FFT 32N,
+  // k_veff (V_loc, spectrum, rho in; V_eff out) 40N
+  return {(168.0 + (save_spectrum ? 32.0 : 0.0)) * N, 3};
+}
+StageModel energy_model(const dc_ctx *c, bool spectrum_difference) {
+  const double N = (double)c->npts, ns = (double)c->layout.nstates;
+  // band sum (occ, eps, q) and entropy (occ, q) over the states; <V, rho_out>, E_x, |rho_out - rho_in|
+  // and int rho_out over the grid; every reduction is two launches (block partials, final sum)
+  double b = 40.0 * ns + 48.0 * N;
+  int nk = 12 + 1;  // + k_energy_combine
+  if (c->params.hxc == DC_HXC_HARTREE_X) {
+    b += (24.0 + 32.0 + 40.0) * N;  // k_real_to_cplx, forward FFT, E_es reduction (spectra, 1/G^2)
+    nk += 1 + 2;
+  }
+  // mixing
+  if (!(c->params.kerker_q0 > 0.0)) {
+    b += 24.0 * N;  // k_mix
+    nk += 1;
+  } else {
+    // residual spectrum: k_sub_cplx 48N, or k_residual_cplx 32N + forward FFT 32N; then k_kerker 40N,
+    // inverse FFT 32N, k_add_real 32N
+    b += (spectrum_difference ? 48.0 : 64.0) * N + 104.0 * N;
+    nk += 3;
+  }
+  return {b, nk};
+}
+
 double core_elems(const dc_ctx *c) {
   double s = 0.0;
   for (const auto &D : c->h_desc) s += (double)D.norb * D.c[0] * D.c[1] * D.c[2];
@@ -254,7 +291,7 @@ int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
   }
   {
     StageScope sc(c, DC_STAGE_SUBSPACE, s, 8.0 * c->gram_elems, 1);
-    DC_TRY(dck::launch_subspace(c, sizeof(T) == 4 ? 32 : 64, s));
+    DC_TRY(dck::launch_subspace(c, sizeof(T) == 4 ? 32 : 64, c->d_eps, s));
   }
   {
     StageScope sc(c, DC_STAGE_ROTATE, s, 2.0 * blk, 1);
@@ -288,13 +325,13 @@ int density_stage(dc_ctx *c, double *rho, cudaStream_t s) {
   const double es = c->params.precision == DC_FP64 ? 8.0 : 4.0;
   StageScope sc(c, DC_STAGE_DENSITY, s, 2.0 * es * core_elems(c) + 8.0 * c->npts + 32.0 * c->layout.nstates, 3);
   if (c->params.precision == DC_FP64) {
-    DC_TRY(dck::launch_core_weights<double>(c, (const double *)c->blk[c->ib_psi], s));
-    DC_TRY(dck::launch_fermi(c, s));
-    DC_TRY(dck::launch_density<double>(c, (const double *)c->blk[c->ib_psi], rho, s));
+    DC_TRY(dck::launch_core_weights<double>(c, (const double *)c->blk[c->ib_psi], c->d_q, s));
+    DC_TRY(dck::launch_fermi(c, c->d_eps, c->d_q, c->d_scalar, c->d_occ, s));
+    DC_TRY(dck::launch_density<double>(c, (const double *)c->blk[c->ib_psi], c->d_occ, rho, s));
   } else {
-    DC_TRY(dck::launch_core_weights<float>(c, (const float *)c->blk[c->ib_psi], s));
-    DC_TRY(dck::launch_fermi(c, s));
-    DC_TRY(dck::launch_density<float>(c, (const float *)c->blk[c->ib_psi], rho, s));
+    DC_TRY(dck::launch_core_weights<float>(c, (const float *)c->blk[c->ib_psi], c->d_q, s));
+    DC_TRY(dck::launch_fermi(c, c->d_eps, c->d_q, c->d_scalar, c->d_occ, s));
+    DC_TRY(dck::launch_density<float>(c, (const float *)c->blk[c->ib_psi], c->d_occ, rho, s));
   }
   return DC_OK;
 }
@@ -342,11 +379,12 @@ int tune(dc_ctx *c, const T *y, T *out, cudaStream_t s) {
 // step's scalars and device flags land in pinned host memory (flags at slot 20) and the flags are
 // cleared for the next call.
 int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
-  const double N8 = 8.0 * (double)c->npts;
+  const bool keep_spectrum = c->params.hxc == DC_HXC_HARTREE_X;
   {
-    StageScope sc(c, DC_STAGE_POTENTIAL, s, 7.0 * N8, 3);
+    const StageModel pm = potential_model(c, keep_spectrum);
+    StageScope sc(c, DC_STAGE_POTENTIAL, s, pm.bytes, pm.launches);
     // with the Hartree term the input density's spectrum is kept for the Kerker residual below
-    DC_TRY(dck::launch_potential(c, rin, s, c->params.hxc == DC_HXC_HARTREE_X ? c->d_rhoinG : nullptr));
+    DC_TRY(dck::launch_potential(c, rin, s, keep_spectrum ? c->d_rhoinG : nullptr));
   }
   {
     StageScope sc(c, DC_STAGE_GATHER, s, 24.0 * (double)c->layout.frag_points, 1);
@@ -355,9 +393,10 @@ int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
   DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
   DC_TRY(density_stage(c, c->d_rho_out, s));
   {
-    StageScope sc(c, DC_STAGE_ENERGY, s, 13.0 * N8, 17);
+    const StageModel em = energy_model(c, keep_spectrum);
+    StageScope sc(c, DC_STAGE_ENERGY, s, em.bytes, em.launches);
     DC_TRY(dck::launch_energy(c, rin, s));
-    DC_TRY(dck::launch_mix(c, rin, s, c->params.hxc == DC_HXC_HARTREE_X ? c->d_rhoinG : nullptr));
+    DC_TRY(dck::launch_mix(c, rin, s, keep_spectrum ? c->d_rhoinG : nullptr));
   }
   DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned, c->d_scalar, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
   DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned + 20, c->d_flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -407,6 +446,27 @@ int capture_step(dc_ctx *c, double *rin, cudaStream_t s) {
   return (int)c->graphs.size() - 1;
 }
 
+// Rayleigh-Ritz of a caller block Y in place (Y <- Y C), Ritz values into eps.  The context's two work
+// blocks hold H Y and Y C; its own state block, eps, q and mu are left alone.
+template <typename T>
+int subspace_block(dc_ctx *c, T *Y, double *eps, cudaStream_t s) {
+  T *W1 = static_cast<T *>(c->blk[(c->ib_psi + 1) % 3]);
+  T *W2 = static_cast<T *>(c->blk[(c->ib_psi + 2) % 3]);
+  c->proj_ok = 0;  // projection buffer 0 holds the caller block's projections below
+  DC_TRY(dck::launch_project<T>(c, Y, cproj<T>(c, 0), s));
+  DC_TRY(dck::launch_hstep<T>(c, HSTEP_HPSI, 0, Y, nullptr, W1, cproj<T>(c, 0), nullptr, nullptr, nullptr, nullptr,
+                              nullptr, s));
+  if (sizeof(T) == 4 && c->params.precision == DC_MIXED)
+    DC_TRY(dck::launch_gram_tc(c, (const float *)Y, (const float *)W1, s));
+  else
+    DC_TRY(dck::launch_gram<T>(c, Y, W1, s));
+  DC_TRY(dck::launch_subspace(c, sizeof(T) == 4 ? 32 : 64, eps, s));
+  DC_TRY(dck::launch_rotate<T>(c, Y, W2, s));
+  const size_t bytes = sizeof(T) * (size_t)c->layout.psi_elems;
+  DC_CUDA(cudaMemcpyAsync(Y, W2, bytes, cudaMemcpyDeviceToDevice, s));
+  return DC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -450,6 +510,31 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   }
   HostTables ht;
   DC_TRY(dc_build_host(c, atoms, ht));
+  // fragment shard (Sec. 2.5: fragments are distributed over processes): contiguous fragment ids,
+  // balanced by the stencil work P_f n_f of each fragment
+  c->nranks = P.nranks > 0 ? P.nranks : 1;
+  c->rank = P.rank;
+  if (c->rank < 0 || c->rank >= c->nranks || c->nranks > c->nfrag) {
+    dc_set_error("dc_init: need 0 <= rank < nranks <= number of fragments");
+    return DC_ERR_ARG;
+  }
+  {
+    std::vector<long long> cost(c->nfrag);
+    for (int f = 0; f < c->nfrag; ++f) {
+      const FragDesc &D = c->h_desc[f];
+      cost[f] = (long long)D.E[0] * D.E[1] * D.E[2] * D.norb;
+    }
+    int lo = 0, hi = c->nfrag;
+    dc_shard_range(cost.data(), c->nfrag, c->rank, c->nranks, &lo, &hi);
+    c->f_lo = lo;
+    c->f_hi = hi;
+    c->st_lo = c->h_desc[lo].st_off;
+    c->st_hi = hi < c->nfrag ? (long long)c->h_desc[hi].st_off : c->layout.nstates;
+    c->layout.frag_lo = lo;
+    c->layout.frag_hi = hi;
+    c->layout.state_lo = c->st_lo;
+    c->layout.state_hi = c->st_hi;
+  }
   int dev = 0;
   DC_CUDA(cudaGetDevice(&dev));
   DC_CUDA(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev));
@@ -460,7 +545,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(upload(&c->d_items, c->h_items));
   {
     std::vector<int2> it2;
-    for (int f = 0; f < c->nfrag; ++f)
+    for (int f = c->f_lo; f < c->f_hi; ++f)
       for (int i = 0; i < c->h_desc[f].norb; i += 2) it2.push_back(make_int2(f, i));
     c->n_items2 = (int)it2.size();
     DC_TRY(upload(&c->d_items2, it2));
@@ -538,7 +623,9 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
     {
       auto items = [&](long long chunk) {
         long long k = 0;
-        for (const auto &D : c->h_desc) k += ((long long)D.E[0] * D.E[1] * D.E[2] + chunk - 1) / chunk;
+        // counted over the whole system, not the shard: the chunking fixes the Gram's rounding, and a
+      // shard must reproduce the single-context result bit for bit
+      for (const auto &D : c->h_desc) k += ((long long)D.E[0] * D.E[1] * D.E[2] + chunk - 1) / chunk;
         return k;
       };
       while (c->gram_chunk > 512 && items(c->gram_chunk) < 2LL * c->sm_count) c->gram_chunk /= 2;
@@ -558,6 +645,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
       gn[f] = nch;
       goff[f] = off;
       off += (long long)nch * 2 * D.norb * D.norb;
+      if (f < c->f_lo || f >= c->f_hi) continue;  // work items of the context's shard only
       for (int ch = 0; ch < nch; ++ch) gi.push_back(make_int2(f, ch));
       const int nr = (int)((Pf + 127) / 128);
       for (int ch = 0; ch < nr; ++ch) ri.push_back(make_int2(f, ch));
@@ -609,6 +697,9 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(dmalloc(&c->d_q, (size_t)Lo.nstates));
   DC_TRY(dmalloc(&c->d_occ, (size_t)Lo.nstates));
   DC_TRY(dmalloc(&c->d_dots, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_q_x, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_occ_x, (size_t)Lo.nstates));
+  DC_TRY(dmalloc(&c->d_aux, 4));
   DC_TRY(dmalloc(&c->d_bounds, (size_t)c->nfrag * (4 + 2 * P.cheb_degree)));
   DC_CUDA(cudaMemset(c->d_bounds, 0, sizeof(double) * (size_t)c->nfrag * (4 + 2 * P.cheb_degree)));
   DC_TRY(dmalloc(&c->d_flags, 8));
@@ -778,10 +869,28 @@ int dc_hpsi(dc_ctx *c, const void *d_psi, void *d_hpsi, int dtype, void *stream)
   return DC_OK;
 }
 
-int dc_subspace(dc_ctx *c, void *stream) {
-  if (!c) return DC_ERR_ARG;
-  DC_TRY(pass_ctx(c, false, 1, S(stream)));
-  return check_flags(c, S(stream));
+int dc_subspace(dc_ctx *c, void *d_psi, int dtype, double *d_eps, void *stream) {
+  if (!c) {
+    dc_set_error("dc_subspace: NULL context");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  if (!d_psi) {
+    DC_TRY(pass_ctx(c, false, 1, s));
+    DC_TRY(check_flags(c, s));
+    if (d_eps)
+      DC_CUDA(cudaMemcpyAsync(d_eps, c->d_eps, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, s));
+    return DC_OK;
+  }
+  const int ctype = c->params.precision == DC_FP64 ? DC_FP64 : DC_FP32;
+  if (dtype != ctype || !d_eps) {
+    dc_set_error("dc_subspace: a caller block needs the context's element type (DC_FP64 for an FP64 context, "
+                 "DC_FP32 otherwise) and an eps output");
+    return DC_ERR_ARG;
+  }
+  if (ctype == DC_FP64) DC_TRY(subspace_block<double>(c, static_cast<double *>(d_psi), d_eps, s));
+  else DC_TRY(subspace_block<float>(c, static_cast<float *>(d_psi), d_eps, s));
+  return check_flags(c, s);
 }
 
 int dc_chefsi(dc_ctx *c, int n_pass, void *stream) {
@@ -853,15 +962,43 @@ int dc_set_state(dc_ctx *c, const void *d_psi, const double *d_eps, void *stream
   return DC_OK;
 }
 
-int dc_density(dc_ctx *c, double *d_rho, double *d_q, double *d_mu, void *stream) {
+int dc_density(dc_ctx *c, const void *d_psi, int dtype, const double *d_eps, double *d_rho, double *d_q,
+               double *d_mu, void *stream) {
   if (!c || !d_rho) {
     dc_set_error("dc_density: NULL argument");
     return DC_ERR_ARG;
   }
   cudaStream_t s = S(stream);
-  DC_TRY(density_stage(c, d_rho, s));
-  if (d_q) DC_CUDA(cudaMemcpyAsync(d_q, c->d_q, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, s));
-  if (d_mu) DC_CUDA(cudaMemcpyAsync(d_mu, c->d_scalar, 8, cudaMemcpyDeviceToDevice, s));
+  if (!d_psi) {
+    DC_TRY(density_stage(c, d_rho, s));
+    if (d_q) DC_CUDA(cudaMemcpyAsync(d_q, c->d_q, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, s));
+    if (d_mu) DC_CUDA(cudaMemcpyAsync(d_mu, c->d_scalar, 8, cudaMemcpyDeviceToDevice, s));
+    return check_flags(c, s);
+  }
+  const int ctype = c->params.precision == DC_FP64 ? DC_FP64 : DC_FP32;
+  if (dtype != ctype || !d_eps) {
+    dc_set_error("dc_density: a caller block needs the context's element type and its eigenvalues d_eps");
+    return DC_ERR_ARG;
+  }
+  if (c->nranks > 1) {
+    dc_set_error("dc_density: the caller-block form needs every fragment (nranks = 1)");
+    return DC_ERR_ARG;
+  }
+  // the caller block's weights, occupations and mu go to scratch, never to the context's own arrays
+  double *q = d_q ? d_q : c->d_q_x;
+  double *mu = c->d_aux;
+  DC_CUDA(cudaMemsetAsync(mu, 0xff, sizeof(double), s));  // NaN: the solve starts from its bracket
+  StageScope sc(c, DC_STAGE_DENSITY, s, 0.0, 3);
+  if (ctype == DC_FP64) {
+    DC_TRY(dck::launch_core_weights<double>(c, static_cast<const double *>(d_psi), q, s));
+    DC_TRY(dck::launch_fermi(c, d_eps, q, mu, c->d_occ_x, s));
+    DC_TRY(dck::launch_density<double>(c, static_cast<const double *>(d_psi), c->d_occ_x, d_rho, s));
+  } else {
+    DC_TRY(dck::launch_core_weights<float>(c, static_cast<const float *>(d_psi), q, s));
+    DC_TRY(dck::launch_fermi(c, d_eps, q, mu, c->d_occ_x, s));
+    DC_TRY(dck::launch_density<float>(c, static_cast<const float *>(d_psi), c->d_occ_x, d_rho, s));
+  }
+  if (d_mu) DC_CUDA(cudaMemcpyAsync(d_mu, mu, 8, cudaMemcpyDeviceToDevice, s));
   return check_flags(c, s);
 }
 
@@ -928,6 +1065,10 @@ int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, vo
     dc_set_error("dc_scf_step: call dc_warmup (or dc_set_state) first");
     return DC_ERR_STATE;
   }
+  if (c->nranks > 1) {
+    dc_set_error("dc_scf_step: a fragment shard steps with dc_step_local / dc_step_density / dc_step_finish");
+    return DC_ERR_ARG;
+  }
   cudaStream_t s = S(stream);
   const size_t nb = 8 * (size_t)c->npts;
   double *rin = rho;
@@ -992,6 +1133,85 @@ int dc_scf_step(dc_ctx *c, double *rho, int rho_on_host, dc_stats_t *h_stats, vo
   return DC_OK;
 }
 
+// ---- fragment-sharded SCF step (Sec. 2.2 and 2.5) ---------------------------------------------------
+int dc_step_local(dc_ctx *c, const double *d_rho_in, double *d_eps, double *d_q, void *stream) {
+  if (!c || !d_rho_in || !d_eps || !d_q) {
+    dc_set_error("dc_step_local: NULL argument");
+    return DC_ERR_ARG;
+  }
+  if (!c->warmed) {
+    dc_set_error("dc_step_local: call dc_warmup (or dc_set_state) first");
+    return DC_ERR_STATE;
+  }
+  cudaStream_t s = S(stream);
+  const bool keep_spectrum = c->params.hxc == DC_HXC_HARTREE_X;
+  DC_TRY(dck::launch_potential(c, d_rho_in, s, keep_spectrum ? c->d_rhoinG : nullptr));
+  DC_TRY(dck::launch_gather(c, s));
+  DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
+  if (c->params.precision == DC_FP64)
+    DC_TRY(dck::launch_core_weights<double>(c, (const double *)c->blk[c->ib_psi], c->d_q, s));
+  else
+    DC_TRY(dck::launch_core_weights<float>(c, (const float *)c->blk[c->ib_psi], c->d_q, s));
+  const size_t ns = (size_t)c->layout.nstates, lo = (size_t)c->st_lo, cnt = (size_t)(c->st_hi - c->st_lo);
+  DC_CUDA(cudaMemsetAsync(d_eps, 0, 8 * ns, s));
+  DC_CUDA(cudaMemsetAsync(d_q, 0, 8 * ns, s));
+  DC_CUDA(cudaMemcpyAsync(d_eps + lo, c->d_eps + lo, 8 * cnt, cudaMemcpyDeviceToDevice, s));
+  DC_CUDA(cudaMemcpyAsync(d_q + lo, c->d_q + lo, 8 * cnt, cudaMemcpyDeviceToDevice, s));
+  return check_flags(c, s);
+}
+
+int dc_step_density(dc_ctx *c, const double *d_eps, const double *d_q, double *d_rho_part, double *d_mu,
+                    void *stream) {
+  if (!c || !d_eps || !d_q || !d_rho_part) {
+    dc_set_error("dc_step_density: NULL argument");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  const size_t ns = (size_t)c->layout.nstates;
+  if (d_eps != c->d_eps) DC_CUDA(cudaMemcpyAsync(c->d_eps, d_eps, 8 * ns, cudaMemcpyDeviceToDevice, s));
+  if (d_q != c->d_q) DC_CUDA(cudaMemcpyAsync(c->d_q, d_q, 8 * ns, cudaMemcpyDeviceToDevice, s));
+  // mu from every state (the same solve, from the same previous mu, on every rank)
+  DC_TRY(dck::launch_fermi(c, c->d_eps, c->d_q, c->d_scalar, c->d_occ, s));
+  if (c->params.precision == DC_FP64)
+    DC_TRY(dck::launch_density<double>(c, (const double *)c->blk[c->ib_psi], c->d_occ, d_rho_part, s));
+  else
+    DC_TRY(dck::launch_density<float>(c, (const float *)c->blk[c->ib_psi], c->d_occ, d_rho_part, s));
+  if (d_mu) DC_CUDA(cudaMemcpyAsync(d_mu, c->d_scalar, 8, cudaMemcpyDeviceToDevice, s));
+  return check_flags(c, s);
+}
+
+int dc_step_finish(dc_ctx *c, double *d_rho_in_out, const double *d_rho_out, dc_stats_t *h_stats, void *stream) {
+  if (!c || !d_rho_in_out || !d_rho_out) {
+    dc_set_error("dc_step_finish: NULL argument");
+    return DC_ERR_ARG;
+  }
+  cudaStream_t s = S(stream);
+  if (d_rho_out != c->d_rho_out)
+    DC_CUDA(cudaMemcpyAsync(c->d_rho_out, d_rho_out, 8 * (size_t)c->npts, cudaMemcpyDeviceToDevice, s));
+  const bool keep_spectrum = c->params.hxc == DC_HXC_HARTREE_X;
+  DC_TRY(dck::launch_energy(c, d_rho_in_out, s));
+  DC_TRY(dck::launch_mix(c, d_rho_in_out, s, keep_spectrum ? c->d_rhoinG : nullptr));
+  DC_CUDA(cudaMemcpyAsync(c->h_scalar_pinned, c->d_scalar, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DC_TRY(check_flags(c, s));
+  c->steps_done++;
+  const double *v = c->h_scalar_pinned;
+  if (h_stats) {
+    h_stats->mu = v[0];
+    h_stats->eband = v[1];
+    h_stats->drho = v[5];
+    h_stats->ne = v[6];
+    h_stats->E = v[8];
+    h_stats->F = v[9];
+    h_stats->step = c->steps_done;
+    h_stats->status = DC_OK;
+  }
+  if (!(v[8] == v[8]) || !(v[0] == v[0]) || v[8] - v[8] != 0.0) {
+    dc_set_error("dc_step_finish: non-finite energy or mu");
+    return DC_ERR_NONFINITE;
+  }
+  return DC_OK;
+}
+
 int dc_get_rho_out(dc_ctx *c, double *d_rho, void *stream) {
   if (!c || !d_rho) return DC_ERR_ARG;
   DC_CUDA(cudaMemcpyAsync(d_rho, c->d_rho_out, 8 * (size_t)c->npts, cudaMemcpyDeviceToDevice, S(stream)));
@@ -1003,6 +1223,10 @@ int dc_eb_adjoint(dc_ctx *c, const void *d_psi, int dtype, const double *d_occ, 
   if (c) c->proj_ok = 0;  // projection buffer 0 holds the caller block's projections
   if (!c || !d_psi || !d_occ || !d_V || !d_D || (dtype != DC_FP64 && dtype != DC_FP32)) {
     dc_set_error("dc_eb_adjoint: invalid argument");
+    return DC_ERR_ARG;
+  }
+  if (c->nranks > 1) {
+    dc_set_error("dc_eb_adjoint: needs every fragment (nranks = 1)");
     return DC_ERR_ARG;
   }
   cudaStream_t s = S(stream);

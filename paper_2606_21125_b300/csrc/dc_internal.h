@@ -200,6 +200,14 @@ struct dc_ctx {
   int steps_done = 0;
   bool warmed = false;
   int sm_count = 0;
+
+  // fragment shard of this context (rank of nranks, Sec. 2.5): fragments [f_lo, f_hi) and their states
+  // [st_lo, st_hi) are solved here; everything else (maps, potentials, the Fermi level, energies) is global
+  int rank = 0, nranks = 1;
+  int f_lo = 0, f_hi = 0;
+  long long st_lo = 0, st_hi = 0;
+  // scratch of the caller-block forms of dc_subspace/dc_density (so the context's own state is kept)
+  double *d_q_x = nullptr, *d_occ_x = nullptr, *d_aux = nullptr;
 };
 
 // Host-built projector tables, uploaded by dc_init.
@@ -211,6 +219,10 @@ struct HostTables {
   std::vector<int2> row_ent;
 };
 int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out);
+// Fragment range [*lo, *hi) of rank `rank` of `nranks` (1 <= nranks <= nfrag): contiguous ids, each
+// boundary the first fragment whose cost prefix reaches rank/nranks of the total (integer comparison),
+// kept at least one fragment past the previous boundary and room for the ranks after it.
+void dc_shard_range(const long long *cost, int nfrag, int rank, int nranks, int *lo, int *hi);
 void dc_build_cover(const dc_ctx *c, int d, std::vector<int> &beg, std::vector<int2> &items);
 
 // ---------------------------------------------------------------------------------------------
@@ -266,7 +278,7 @@ int launch_bounds(dc_ctx *c, int first, cudaStream_t s);
 template <typename T>
 int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s);
 int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s);
-int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s);
+int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s);
 template <typename T>
 int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, double lambda_cut, double *basis,
                 int *nbasis, double *s_out, cudaStream_t s);
@@ -276,12 +288,15 @@ template <typename T>
 int launch_rotate_proj(dc_ctx *c, const T *cin, T *cout, cudaStream_t s);
 
 // density
+// core weights of the owned fragments' states into q[nstates] (other entries untouched)
 template <typename T>
-int launch_core_weights(dc_ctx *c, const T *psi, cudaStream_t s);
-int launch_fermi(dc_ctx *c, cudaStream_t s);
+int launch_core_weights(dc_ctx *c, const T *psi, double *q, cudaStream_t s);
+// mu (in: starting guess, out: root) and occupations of all nstates states
+int launch_fermi(dc_ctx *c, const double *eps, const double *q, double *mu, double *occ, cudaStream_t s);
 int launch_wait_selftest(dc_ctx *c, cudaStream_t s);
+// rho[npts] on the owned fragments' cores; zero elsewhere when the context owns a shard
 template <typename T>
-int launch_density(dc_ctx *c, const T *psi, double *rho, cudaStream_t s);
+int launch_density(dc_ctx *c, const T *psi, const double *occ, double *rho, cudaStream_t s);
 
 // adjoint
 template <typename T>

@@ -205,12 +205,18 @@ __global__ void __launch_bounds__(QNT) k_fermi(const double *eps, const double *
   for (int p = base; p < nst; p += stride) occ[p] = fermi_occ(eps[p], mu, kT);
 }
 
+// Points whose owner lies outside the fragment range [f_lo, f_hi) get 0 (a rank's share of rho).
 template <typename T>
 __global__ void k_density(const FragDesc *desc, const int32_t *owner, const int32_t *core_local, long long npts,
-                          const T *psi, const double *occ, double *rho) {
+                          const T *psi, const double *occ, double *rho, int f_lo, int f_hi) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= npts) return;
-  const FragDesc D = desc[owner[g]];
+  const int f = owner[g];
+  if (f < f_lo || f >= f_hi) {
+    rho[g] = 0.0;
+    return;
+  }
+  const FragDesc D = desc[f];
   const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
   const T *y = psi + D.psi_off + core_local[g];
   const double *o = occ + D.st_off;
@@ -308,18 +314,20 @@ __global__ void __launch_bounds__(256) k_density32(const FragDesc *desc, const f
 namespace dck {
 
 template <typename T>
-int launch_core_weights(dc_ctx *c, const T *psi, cudaStream_t s) {
+int launch_core_weights(dc_ctx *c, const T *psi, double *q, cudaStream_t s) {
+  const int nf = c->f_hi - c->f_lo;
+  if (nf <= 0) return DC_OK;
   if constexpr (std::is_same<T, float>::value) {
-    const dim3 grid((unsigned)c->nfrag, (unsigned)((c->layout.max_norb + 7) / 8));
-    k_core_weights32<<<grid, 256, 0, s>>>(c->d_desc, psi, c->dV, c->d_q);
+    const dim3 grid((unsigned)nf, (unsigned)((c->layout.max_norb + 7) / 8));
+    k_core_weights32<<<grid, 256, 0, s>>>(c->d_desc + c->f_lo, psi, c->dV, q);
   } else {
-    k_core_weights<T><<<(unsigned)c->layout.nstates, QNT, 0, s>>>(c->d_desc, c->d_items, psi, c->dV, c->d_q);
+    k_core_weights<T><<<(unsigned)(c->st_hi - c->st_lo), QNT, 0, s>>>(c->d_desc, c->d_items + c->st_lo, psi, c->dV, q);
   }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
 
-int launch_fermi(dc_ctx *c, cudaStream_t s) {
+int launch_fermi(dc_ctx *c, const double *eps_in, const double *q_in, double *mu_io, double *occ_out, cudaStream_t s) {
   int nb = 0;
   DC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_fermi, QNT, 0));
   if (nb < 1) {
@@ -330,15 +338,15 @@ int launch_fermi(dc_ctx *c, cudaStream_t s) {
   const int need = (int)((c->layout.nstates + QNT - 1) / QNT);
   if (grid > need) grid = need > 0 ? need : 1;
   DC_CUDA(cudaMemsetAsync(c->d_flags + 1, 0, 2 * sizeof(unsigned), s));
-  const double *eps = c->d_eps;
-  const double *q = c->d_q;
+  const double *eps = eps_in;
+  const double *q = q_in;
   int nst = (int)c->layout.nstates;
   double ne = c->ne, kT = c->params.kT;
   double *partials = c->d_partials;
   unsigned *bar = c->d_flags + 1;
   unsigned *flags = c->d_flags;
-  double *mu = c->d_scalar;  // slot 0
-  double *occ = c->d_occ;
+  double *mu = mu_io;
+  double *occ = occ_out;
   void *args[] = {&eps, &q, &nst, &ne, &kT, &partials, &bar, &flags, &mu, &occ};
   DC_CUDA(cudaLaunchCooperativeKernel((const void *)k_fermi, dim3(grid), dim3(QNT), args, 0, s));
   return DC_OK;
@@ -353,21 +361,26 @@ int launch_wait_selftest(dc_ctx *c, cudaStream_t s) {
 }
 
 template <typename T>
-int launch_density(dc_ctx *c, const T *psi, double *rho, cudaStream_t s) {
+int launch_density(dc_ctx *c, const T *psi, const double *occ, double *rho, cudaStream_t s) {
+  const int nf = c->f_hi - c->f_lo;
   if constexpr (std::is_same<T, float>::value) {
-    k_density32<<<(unsigned)c->nfrag, 256, 0, s>>>(c->d_desc, psi, c->d_occ, c->grid.n[0], c->grid.n[1], rho);
+    // one CTA per owned core writes exactly that core's points; on a shard the rest of rho is zero
+    if (nf < c->nfrag) DC_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * (size_t)c->npts, s));
+    if (nf > 0)
+      k_density32<<<(unsigned)nf, 256, 0, s>>>(c->d_desc + c->f_lo, psi, occ, c->grid.n[0], c->grid.n[1], rho);
   } else {
     const unsigned nb = (unsigned)((c->npts + 255) / 256);
-    k_density<T><<<nb, 256, 0, s>>>(c->d_desc, c->d_owner, c->d_core_local, c->npts, psi, c->d_occ, rho);
+    k_density<T><<<nb, 256, 0, s>>>(c->d_desc, c->d_owner, c->d_core_local, c->npts, psi, occ, rho, c->f_lo,
+                                    c->f_hi);
   }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
 
-template int launch_core_weights<double>(dc_ctx *, const double *, cudaStream_t);
-template int launch_core_weights<float>(dc_ctx *, const float *, cudaStream_t);
-template int launch_density<double>(dc_ctx *, const double *, double *, cudaStream_t);
-template int launch_density<float>(dc_ctx *, const float *, double *, cudaStream_t);
+template int launch_core_weights<double>(dc_ctx *, const double *, double *, cudaStream_t);
+template int launch_core_weights<float>(dc_ctx *, const float *, double *, cudaStream_t);
+template int launch_density<double>(dc_ctx *, const double *, const double *, double *, cudaStream_t);
+template int launch_density<float>(dc_ctx *, const float *, const double *, double *, cudaStream_t);
 
 }  // namespace dck
 
@@ -458,7 +471,12 @@ extern "C" int dc_fermi_level_noalloc(const double *d_eps, const double *d_q, in
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned *words = reinterpret_cast<unsigned *>(dev->scratch);
-  DC_CUDA(cudaMemsetAsync(words, 0, kFermiNoallocHeader, s));
+  if (cudaMemsetAsync(words, 0, kFermiNoallocHeader, s) != cudaSuccess) {
+    const cudaError_t e = cudaGetLastError();
+    std::lock_guard<std::mutex> lock(g_fermi_noalloc_mutex);
+    dev->ready = false;
+    return dc_cuda_status(e, "dc_fermi_level_noalloc: clearing the scratch header");
+  }
   const double *eps = d_eps;
   const double *q = d_q;
   int nst = (int)nstates;
@@ -469,10 +487,17 @@ extern "C" int dc_fermi_level_noalloc(const double *d_eps, const double *d_q, in
   double *mu = d_mu;
   double *occ = d_occ;
   void *args[] = {&eps, &q, &nst, &ne, &t, &partials, &bar, &flags, &mu, &occ};
-  DC_CUDA(cudaLaunchCooperativeKernel((const void *)k_fermi, dim3(grid), dim3(QNT), args, 0, s));
   unsigned fl = 0;
-  DC_CUDA(cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  DC_CUDA(cudaStreamSynchronize(s));
+  cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_fermi, dim3(grid), dim3(QNT), args, 0, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&fl, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    // a device reset or a torn-down primary context leaves the cached scratch address stale: the next
+    // call looks it up again
+    std::lock_guard<std::mutex> lock(g_fermi_noalloc_mutex);
+    dev->ready = false;
+    return dc_cuda_status(e, "dc_fermi_level_noalloc");
+  }
   if (fl & DC_FLAG_TIMEOUT) {
     dc_set_error("dc_fermi_level_noalloc: a bounded device wait ran out (grid barrier)");
     return DC_ERR_TIMEOUT;

@@ -338,8 +338,11 @@ int launch_gather(dc_ctx *c, cudaStream_t s) {
   const double sym = fd[0] + 2.0 * (-fd[1] + fd[2] - fd[3] + fd[4]);
   double kin = 0.0;
   for (int d = 0; d < 3; ++d) kin += -sym / (2.0 * c->h[d] * c->h[d]);
-  k_gather<<<c->nfrag, 256, 0, s>>>(c->d_desc, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32, c->d_nl_bound, kin,
-                                    c->d_bounds, 4 + 2 * c->params.cheb_degree);
+  const int bstride = 4 + 2 * c->params.cheb_degree;
+  const int nf = c->f_hi - c->f_lo;  // the context's fragment shard (all fragments on one rank)
+  if (nf <= 0) return DC_OK;
+  k_gather<<<nf, 256, 0, s>>>(c->d_desc + c->f_lo, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32,
+                              c->d_nl_bound + c->f_lo, kin, c->d_bounds + (long long)c->f_lo * bstride, bstride);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

@@ -1117,7 +1117,7 @@ template <typename T>
 HArgs<T> make_args(dc_ctx *c) {
   HArgs<T> a{};
   a.desc = c->d_desc;
-  a.items = c->d_items;
+  a.items = c->d_items + c->st_lo;  // the states of the context's fragment shard
   a.slots = c->d_slots;
   a.tab = tab_of<T>(c);
   a.zl_beg = c->d_zl_beg;
@@ -1179,7 +1179,8 @@ int run_hstep(dc_ctx *c, HArgs<T> a, cudaStream_t s) {
   }
   DC_CUDA(dc_set_smem((const void *)k_hstep<T, NT, PP, NO>, sm));
   if (NO == 2) a.items = c->d_items2;
-  const unsigned grid = NO == 2 ? (unsigned)c->n_items2 : (unsigned)c->layout.nstates;
+  const unsigned grid = NO == 2 ? (unsigned)c->n_items2 : (unsigned)(c->st_hi - c->st_lo);
+  if (grid == 0) return DC_OK;
   k_hstep<T, NT, PP, NO><<<grid, NT, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
@@ -1397,7 +1398,8 @@ int launch_project(dc_ctx *c, const T *psi, T *cout, cudaStream_t s) {
   }
   const size_t sm = project_smem(c, sizeof(T));
   DC_CUDA(dc_set_smem((const void *)k_project<T, 256>, sm));
-  k_project<T, 256><<<(unsigned)c->layout.nstates, 256, sm, s>>>(a);
+  if (c->st_hi <= c->st_lo) return DC_OK;
+  k_project<T, 256><<<(unsigned)(c->st_hi - c->st_lo), 256, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

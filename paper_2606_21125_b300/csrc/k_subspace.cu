@@ -16,9 +16,10 @@ namespace {
 //   bounds[f] = {a, b_up, aL, c, alpha_0, beta_0, ..., alpha_{m-1}, beta_{m-1}}
 // b_up is written by the potential gather; a and aL come from the fragment's Ritz values.
 // ---------------------------------------------------------------------------------------------
-__global__ void k_bounds(const FragDesc *desc, int nfrag, const double *eps, double *bounds, int m, int stride) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nfrag) return;
+__global__ void k_bounds(const FragDesc *desc, int f_lo, int f_hi, const double *eps, double *bounds, int m,
+                         int stride) {
+  const int f = f_lo + blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= f_hi) return;
   const FragDesc D = desc[f];
   double lo = eps[D.st_off], hi = eps[D.st_off];
   for (int i = 1; i < D.norb; ++i) {
@@ -286,9 +287,9 @@ __device__ __forceinline__ void tri_ij(int t, int np, int &i, int &j) {
 
 __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const long long *goff, const int *gnchunk,
                                                   const double *gram, double dV, double *eps, double *C64,
-                                                  float *C32, unsigned *flags, int fp64_sweeps) {
+                                                  float *C32, unsigned *flags, int fp64_sweeps, int f_lo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int f = blockIdx.x;
+  const int f = f_lo + blockIdx.x;
   const FragDesc D = desc[f];
   const int n = D.norb;
   const int np = n + (n & 1);  // even size for the round-robin pairing (index n is a dummy)
@@ -702,7 +703,7 @@ __device__ __forceinline__ void lcfo_tile(const FragDesc &D, const T *psi, long 
 template <typename T>
 __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi, const double *eps, double eps_cut,
                                               double lambda_cut, double dV, double *basis, int *nbasis,
-                                              double *s_out) {
+                                              double *s_out, int f_lo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int LD = DC_MAX_NORB + 1;
   double *S = reinterpret_cast<double *>(smem_raw);  // [np][LD] overlap -> eigenvalues; then W
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(SNT) k_lcfo(const FragDesc *desc, const T *psi
   __shared__ float redf[SNT / 32], rcf[32], rsf[32];
   __shared__ long long redl[SNT / 32];
   __shared__ int rp[32], rq[32], sel[DC_MAX_NORB], perm[DC_MAX_NORB], nsel_s;
-  const int f = blockIdx.x, tid = threadIdx.x;
+  const int f = f_lo + blockIdx.x, tid = threadIdx.x;
   const FragDesc D = desc[f];
   const int n = D.norb;
   const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
@@ -946,7 +947,9 @@ namespace dck {
 
 int launch_bounds(dc_ctx *c, int, cudaStream_t s) {
   const int m = c->params.cheb_degree;
-  k_bounds<<<(c->nfrag + 127) / 128, 128, 0, s>>>(c->d_desc, c->nfrag, c->d_eps, c->d_bounds, m, 4 + 2 * m);
+  const int nf = c->f_hi - c->f_lo;
+  if (nf <= 0) return DC_OK;
+  k_bounds<<<(nf + 127) / 128, 128, 0, s>>>(c->d_desc, c->f_lo, c->f_hi, c->d_eps, c->d_bounds, m, 4 + 2 * m);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -959,14 +962,15 @@ int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s) {
   return DC_OK;
 }
 
-int launch_subspace(dc_ctx *c, int precision_bits, cudaStream_t s) {
+int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s) {
   const int np = c->layout.max_norb + (c->layout.max_norb & 1);
   const size_t sm = 5 * (size_t)np * (np + 1) * sizeof(double);
   DC_CUDA(dc_set_smem((const void *)k_subspace, sm));
   const int fp64_sweeps = precision_bits == 32 ? 0 : 40;
-  k_subspace<<<c->nfrag, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, c->d_eps,
-                                       c->d_C64, precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags,
-                                       fp64_sweeps);
+  const int nf = c->f_hi - c->f_lo;
+  if (nf <= 0) return DC_OK;
+  k_subspace<<<nf, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, eps, c->d_C64,
+                                 precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags, fp64_sweeps, c->f_lo);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -1009,7 +1013,9 @@ int launch_rotate_proj(dc_ctx *c, const T *cin, T *cout, cudaStream_t s) {
   const T *C = nullptr;
   if (sizeof(T) == 8) C = reinterpret_cast<const T *>(c->d_C64);
   else C = reinterpret_cast<const T *>(c->d_C32);
-  k_rotate_proj<T><<<c->nfrag, 256, 0, s>>>(c->d_desc, C, cin, cout);
+  const int nf = c->f_hi - c->f_lo;
+  if (nf <= 0) return DC_OK;
+  k_rotate_proj<T><<<nf, 256, 0, s>>>(c->d_desc + c->f_lo, C, cin, cout);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -1026,7 +1032,9 @@ int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, doub
                 int *nbasis, double *s_out, cudaStream_t s) {
   const size_t sm = (2 * (size_t)DC_MAX_NORB * (DC_MAX_NORB + 1) + (size_t)DC_MAX_NORB * LTS) * sizeof(double);
   DC_CUDA(dc_set_smem((const void *)k_lcfo<T>, sm));
-  k_lcfo<T><<<c->nfrag, SNT, sm, s>>>(c->d_desc, psi, eps, eps_cut, lambda_cut, c->dV, basis, nbasis, s_out);
+  const int nf = c->f_hi - c->f_lo;
+  if (nf <= 0) return DC_OK;
+  k_lcfo<T><<<nf, SNT, sm, s>>>(c->d_desc, psi, eps, eps_cut, lambda_cut, c->dV, basis, nbasis, s_out, c->f_lo);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

@@ -65,8 +65,8 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   c->volume = c->grid.L[0] * c->grid.L[1] * c->grid.L[2];
   c->npts = (long long)n[0] * n[1] * n[2];
   c->nfrag = F[0] * F[1] * F[2];
-  if (c->nfrag >= 4096) {
-    dc_set_error("dc_init: at most 4095 fragments (initial-orbital counter layout)");
+  if (c->nfrag > 4096) {
+    dc_set_error("dc_init: at most 4096 fragments (the initial-orbital counter holds fragment indices below 4096)");
     return DC_ERR_ARG;
   }
   c->natom = atoms->natom;
@@ -364,3 +364,27 @@ void dc_build_cover(const dc_ctx *c, int d, std::vector<int> &beg, std::vector<i
   beg[N] = (int)items.size();
 }
 
+void dc_shard_range(const long long *cost, int nfrag, int rank, int nranks, int *lo, int *hi) {
+  long long total = 0;
+  for (int f = 0; f < nfrag; ++f) total += cost[f];
+  // boundaries b_0 = 0 < b_1 < ... < b_nranks = nfrag
+  int prev = 0, f = 0;
+  long long prefix = 0;
+  int b_lo = 0, b_hi = nfrag;
+  for (int r = 1; r <= nranks; ++r) {
+    int b = nfrag;
+    if (r < nranks) {
+      // first f with prefix(f) * nranks >= r * total (prefix(f) = cost of fragments before f)
+      while (f < nfrag && prefix * nranks < (long long)r * total) prefix += cost[f++];
+      b = f;
+      if (b < prev + 1) b = prev + 1;
+      if (b > nfrag - (nranks - r)) b = nfrag - (nranks - r);
+    }
+    if (r == rank) b_lo = b;
+    if (r == rank + 1) b_hi = b;
+    prev = b;
+  }
+  if (rank == 0) b_lo = 0;
+  *lo = b_lo;
+  *hi = b_hi;
+}

@@ -268,9 +268,12 @@ def test_mixed_gram_matches_fp32_gram():
     assert d < 1e-5, f"max |eps_mixed - eps_fp32| = {d:.3e} Ha"
 
 
-def test_scf_kerker_mixing_fp64():
-    """SCF steps with Kerker-preconditioned mixing (FFT-weighted residual) against the oracle."""
-    cfg = CASES["uneven"](precision="fp64", n_warmup=3, kerker_q0=0.8)
+@pytest.mark.parametrize("hxc", ["hartree_x", "none"])
+def test_scf_kerker_mixing_fp64(hxc):
+    """SCF steps with Kerker-preconditioned mixing (FFT-weighted residual) against the oracle.  With the
+    Hartree term the residual's spectrum is the difference of the step's two density spectra; without it
+    the library transforms the residual itself: both branches are compared."""
+    cfg = CASES["uneven"](precision="fp64", n_warmup=3, kerker_q0=0.8, hxc=hxc)
     st = oracle_state(cfg)
     st.warmup()
     refs = [st.scf_step() for _ in range(3)]
@@ -597,3 +600,88 @@ def test_full_size_lcfo_sampled_si512():
         B = rows[f].reshape(n, -1)[:m]
         np.testing.assert_allclose(dV * B @ B.T, np.eye(m), rtol=0, atol=1e-9)
         np.testing.assert_allclose(lcfo.span_projector(B, dV), lcfo.span_projector(B_ref, dV), rtol=0, atol=1e-8)
+
+
+def test_maps_and_orbitals_at_4096_fragments():
+    """The largest fragment count the initial-orbital counter holds (16^3 = 4096 fragments, indices up to
+    4095, as in the 4096-atom weak-scaling cell): maps and the starting orbitals of the last fragments
+    bit-exact against the oracle."""
+    cfg = workloads.small_config(n=(32, 32, 32), L=(16.0, 16.0, 16.0), num_fragment=(16, 16, 16),
+                                 buffer=(1, 1, 1), nstate=2, natom=2, seed=4, precision="fp64")
+    sample = [0, 1, 2047, 4094, 4095]
+    st = oracle_state(cfg, subset=sample)
+    fr = st.frags
+    assert fr.nfrag == 4096
+    with _solver(cfg) as s:
+        m = s.maps()
+        psi, _ = s.get_state()
+        got = _np(psi)
+    for f in range(fr.nfrag):
+        assert list(m["frag"][f, 0:3]) == list(fr.origin[f])
+        assert list(m["frag"][f, 3:6]) == list(fr.extent[f])
+        assert list(m["frag"][f, 6:9]) == list(fr.core[f])
+    idx = np.concatenate([fr.idx_map(f) for f in range(fr.nfrag)])
+    assert np.array_equal(m["idx_map"], idx)
+    assert np.array_equal(m["owner"], st.owner)
+    assert np.array_equal(m["core_local"], st.core_local)
+    per = 2 * 4 ** 3
+    for f in sample:
+        assert np.array_equal(got[f * per:(f + 1) * per], st.psi[f].reshape(-1)), f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "mixed"])
+def test_subspace_on_a_caller_block(precision):
+    """dc_subspace on a caller's seeded block (rotated in place, Ritz values out) against the oracle's
+    Rayleigh-Ritz of the same (element-type-rounded) block; the context's own state is left alone."""
+    from oracle import density
+    cfg = CASES["uneven"](precision=precision)
+    st = oracle_state(cfg)
+    V = st.veff(st.rho_in)
+    r = np.random.default_rng(21)
+    with _solver(cfg) as s:
+        _, rho0 = s.initial()
+        s.potential(rho0)
+        own_psi, own_eps = s.get_state()
+        psi = torch.tensor(r.standard_normal(s.layout.psi_elems), dtype=s.dtype, device="cuda")
+        blocks = unpack(st, _np(psi).astype(np.float64))
+        eps = _np(s.subspace(psi))
+        after_psi, after_eps = s.get_state()
+        assert torch.equal(after_psi, own_psi) and torch.equal(after_eps, own_eps)
+        rot = unpack(st, _np(psi).astype(np.float64))
+    ref = {f: chefsi.rayleigh_ritz(st.hamiltonian(f, V), blocks[f]) for f in range(st.frags.nfrag)}
+    ref_eps = pack(st, {f: ref[f][0] for f in ref})
+    tol = 1e-10 if precision == "fp64" else 2e-5
+    assert np.max(np.abs(eps - ref_eps)) <= tol * max(1.0, np.max(np.abs(ref_eps)))
+    # the rotated block's core weights are invariants of the (non-degenerate) Ritz vectors up to sign
+    for f in range(st.frags.nfrag):
+        qg = density.core_weights(st.frags, f, rot[f], st.grid.dV)
+        qr = density.core_weights(st.frags, f, ref[f][1], st.grid.dV)
+        assert np.max(np.abs(qg - qr)) <= (1e-9 if precision == "fp64" else 1e-4) * max(1.0, np.max(qr)), f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_density_on_a_caller_block(precision):
+    """dc_density on a caller's seeded block and eigenvalues against the oracle's core weights, Fermi
+    level and core-projected density of the same (element-type-rounded) input (Eqs. 2-4)."""
+    from oracle import density
+    cfg = CASES["water_auto"](precision=precision)
+    st = oracle_state(cfg)
+    r = np.random.default_rng(22)
+    with _solver(cfg) as s:
+        n = s.layout.psi_elems
+        psi = torch.tensor(0.05 * r.standard_normal(n), dtype=s.dtype, device="cuda")
+        eps = torch.tensor(np.sort(r.uniform(-0.5, 0.5, s.layout.nstates)), dtype=torch.float64, device="cuda")
+        rho, q, mu = s.density(psi, eps)
+        blocks = unpack(st, _np(psi).astype(np.float64))
+        epsf = unpack_states(st, _np(eps))
+        rho, q, mu = _np(rho), _np(q), float(_np(mu)[0])
+    ref_q = pack(st, {f: density.core_weights(st.frags, f, blocks[f], st.grid.dV) for f in range(st.frags.nfrag)})
+    ref_mu = fermi.find_mu(pack(st, epsf), ref_q, st.ne, st.kT)
+    ref_rho = np.zeros(st.grid.npts)
+    for f in range(st.frags.nfrag):
+        g, vals = density.core_density(st.frags, f, blocks[f], fermi.occupation(epsf[f], ref_mu, st.kT))
+        ref_rho[g] = vals
+    tq, tmu, trho = (1e-12, 1e-11, 1e-11) if precision == "fp64" else (1e-6, 1e-9, 1e-6)
+    assert np.max(np.abs(q - ref_q)) <= tq * np.max(ref_q)
+    assert abs(mu - ref_mu) <= tmu
+    assert np.sum(np.abs(rho - ref_rho)) <= trho * np.sum(np.abs(ref_rho))

@@ -441,6 +441,55 @@ def test_fermi_matches_brentq_and_is_monotone():
     assert mus[0] < mus[1] < mus[2]
 
 
+def test_entropy_is_minus_temperature_derivative_of_grand_potential():
+    """The smearing entropy equals -dOmega/dT at fixed mu, Omega(T) = -T sum_i 2 q_i ln(1 + e^{-(eps_i - mu)/T})
+    the grand potential of independent spin-degenerate fermionic levels weighted by q (k_B = 1).  A
+    central difference in T checks the oracle's S, including its factor 2, its q weighting and its sign."""
+    r = np.random.default_rng(11)
+    eps = r.uniform(-0.3, 0.3, 64)
+    q = r.uniform(0.05, 1.0, 64)
+    mu = 0.017
+
+    def omega(T):
+        return -T * float(np.sum(2.0 * q * np.logaddexp(0.0, -(eps - mu) / T)))
+
+    for kT in (0.01, 0.03, 0.1):
+        dT = 1e-5 * kT
+        s_fd = -(omega(kT + dT) - omega(kT - dT)) / (2.0 * dT)
+        s = fermi.entropy(eps, q, mu, kT)
+        assert s > 0.0
+        assert abs(s - s_fd) < 1e-7 * s, (kT, s, s_fd)
+
+
+def test_entropy_closed_forms():
+    """A level at mu is half filled: 2 ln 2 per unit weight; a level far from mu carries none; the
+    entropy of a level at eps - mu = x kT is 2 [ln(1 + e^x) - x e^x/(1 + e^x)] (here x = ln 3, f = 1/4:
+    2 [ln 4 - (3/4) ln 3])."""
+    kT = 0.02
+    assert abs(fermi.entropy(np.array([0.5]), np.array([1.0]), 0.5, kT) - 2.0 * math.log(2.0)) < 1e-15
+    assert abs(fermi.entropy(np.array([0.5]), np.array([0.25]), 0.5, kT) - 0.5 * math.log(2.0)) < 1e-15
+    assert fermi.entropy(np.array([-5.0, 5.0]), np.array([1.0, 1.0]), 0.0, kT) < 1e-100
+    x = math.log(3.0)
+    want = 2.0 * (math.log(4.0) - 0.75 * math.log(3.0))
+    assert abs(fermi.entropy(np.array([x * kT]), np.array([1.0]), 0.0, kT) - want) < 1e-14
+
+
+def test_density_residual_hand_computed():
+    """int |rho_out - rho_in| dV / N_e on a 4x2x2 grid (dV = 0.125 bohr^3, 16 points): half the points
+    differ by +0.3, four by -0.2, four agree, so the integral is 0.125 (8 * 0.3 + 4 * 0.2) = 0.4 and, for
+    N_e = 2, the residual is 0.2 whatever the values of rho_in (Sec. 3.3 convergence measure)."""
+    grid = model.Grid((4, 2, 2), (2.0, 1.0, 1.0))
+    assert grid.dV == 0.125
+    r = np.random.default_rng(3)
+    rho_in = r.uniform(0.5, 2.0, grid.shape())
+    d = np.zeros(16)
+    d[:8] = 0.3
+    d[8:12] = -0.2
+    rho_out = rho_in + r.permutation(d).reshape(grid.shape())
+    assert abs(energy.residual(grid, rho_out, rho_in, 2.0) - 0.2) < 1e-14
+    assert energy.residual(grid, rho_in, rho_in, 2.0) == 0.0
+
+
 def test_electron_count_conserved():
     """P6: int rho_out = N_e after mu is found."""
     cfg = workloads.small_config(natom=3, n_warmup=2)

@@ -70,6 +70,42 @@ def test_many_blocks_against_the_oracle():
         assert abs(float(torch.sum(2.0 * occ * q).item()) - ne) < 1e-7 * ne
 
 
+def test_solves_allocate_nothing(si8):
+    """After the setup call, repeated solves change neither the device's free memory (any cudaMalloc
+    would take at least one 2 MB page) nor the number of torch allocations."""
+    from paper_2606_21125_b300 import fermi_level_noalloc, load
+    cfg, eps, q, _ = si8
+    assert load().dc_fermi_level_noalloc(None, None, 0, 0.0, 0.01, None, None, None) == 0
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    occ = torch.empty_like(eps)
+    fermi_level_noalloc(eps, q, _ne(cfg), cfg["kT"], mu, occ)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    n0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(5):
+        fermi_level_noalloc(eps, q, _ne(cfg), cfg["kT"], mu, occ)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    n1 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    assert free1 == free0
+    assert n1 == n0
+
+
+def test_wrapper_rejects_mismatched_tensors(si8):
+    from paper_2606_21125_b300 import fermi_level_noalloc
+    cfg, eps, q, _ = si8
+    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
+    occ = torch.empty_like(eps)
+    with pytest.raises(ValueError):
+        fermi_level_noalloc(eps, q[:-1], _ne(cfg), cfg["kT"], mu, occ)
+    with pytest.raises(ValueError):
+        fermi_level_noalloc(eps, q.float(), _ne(cfg), cfg["kT"], mu, occ)
+    with pytest.raises(ValueError):
+        fermi_level_noalloc(eps, q, _ne(cfg), cfg["kT"], mu[:0], occ)
+    with pytest.raises(ValueError):
+        fermi_level_noalloc(eps.cpu(), q, _ne(cfg), cfg["kT"], mu, occ)
+
+
 def test_setup_call_and_oversize_rejection():
     from paper_2606_21125_b300 import _lib, load
     lib = load()
