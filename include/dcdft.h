@@ -351,11 +351,14 @@ int dc_eb_adjoint(dc_ctx *ctx, const void *d_psi, int dtype, const double *d_occ
  * per CTA, point pairs per thread); kind 0 pairs x-adjacent points of one orbital (FP32: two
  * orbitals per CTA), kind 1 (FP32 only) interleaves two orbitals at every point, kind 2 is kind 1
  * compiled with registers capped for three 256-thread CTAs per SM, kind 3 is kind 1 with every
- * plane's projector records built once per CTA (only where they fit in shared memory).  With the
+ * plane's projector records built once per CTA (only where they fit in shared memory), kind 4 (FP32
+ * only) is the orbital-pair kernel compiled for one cubic fragment extent (18, 20, 22 or 32 points)
+ * with the zero boundary and equal spacing on the three axes (256 threads up to 22 points, 512 for
+ * 32); it takes Chebyshev steps and plain H-applies, and the adjoint runs the general kernel.  With the
  * environment variable DC_TUNE_CACHE=<file> results are looked up in / appended to that text file
  * (one line per fragment shape, atom and orbital count, type).
  * h_shape[6] = {fp32 kind, threads, pairs, fp64 kind, threads, pairs} (threads 0 = not tuned yet);
- * h_ms[32] (may be NULL) = best time in ms of each of the 16 candidate slots, FP32 then FP64
+ * h_ms[40] (may be NULL) = best time in ms of each of the 20 candidate slots, FP32 then FP64
  * (0 = not tried). */
 int dc_tuning(const dc_ctx *ctx, int *h_shape, float *h_ms);
 

@@ -273,10 +273,10 @@ def _profile_methods():
 
     def tuning(self):
         shp = (C.c_int * 6)()
-        ms = (C.c_float * 32)()
+        ms = (C.c_float * 40)()
         check("dc_tuning", self.lib.dc_tuning(self.ctx, shp, ms))
-        return dict(fp32=dict(kind=shp[0], threads=shp[1], pairs=shp[2], candidates_ms=list(ms[0:16])),
-                    fp64=dict(kind=shp[3], threads=shp[4], pairs=shp[5], candidates_ms=list(ms[16:32])))
+        return dict(fp32=dict(kind=shp[0], threads=shp[1], pairs=shp[2], candidates_ms=list(ms[0:20])),
+                    fp64=dict(kind=shp[3], threads=shp[4], pairs=shp[5], candidates_ms=list(ms[20:40])))
 
     def set_tuning(self, dtype, kind, threads, pairs):
         """Pin the stencil launch shape for ``dtype`` ("fp64" or "fp32"); False if it does not fit."""

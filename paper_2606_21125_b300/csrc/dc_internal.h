@@ -43,7 +43,7 @@ struct ProjSlot {
   double coef;    // (pi sigma^2)^(-3/4)
 };
 
-#define DC_TUNE_SLOTS 16   // candidate launch shapes of the stencil kernels (per element type)
+#define DC_TUNE_SLOTS 20   // candidate launch shapes of the stencil kernels (per element type)
 #define DC_MAX_NORB 64     // subspace kernels hold n x n FP64 matrices in shared memory
 #define DC_MAX_EXTENT 64   // stencil kernels hold padded planes of (E+8)^2 points
 
@@ -128,6 +128,7 @@ struct dc_ctx {
   // per-fragment-point potential
   double *d_vf64 = nullptr;
   float *d_vf32 = nullptr;
+  float2 *d_vf2 = nullptr;  // FP32 (V, V) per point for the specialised orbital-pair kernel
 
   // orbital blocks: 3 rotating blocks of the context precision (index of the state in ib_psi)
   void *blk[3] = {nullptr, nullptr, nullptr};
@@ -272,6 +273,11 @@ int hstep_shape_find(const dc_ctx *c, size_t esz, int kind, int threads, int pai
 template <typename T>
 int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T *yout, const T *cin, T *cout,
                  const double *Datom, const double *occ, double *dots, const T *vf, cudaStream_t s);
+// specialised FP32 kernel (uniform cubic fragments, zero boundary, isotropic spacing): the compiled extent
+// it runs for this context, or 0; and its launch (HSTEP_CHEB / HSTEP_HPSI, input projections required)
+int cheb_extent(const dc_ctx *c);
+int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yprev, float *yout, const float *cin,
+                float *cout, cudaStream_t s);
 
 // subspace
 int launch_bounds(dc_ctx *c, int first, cudaStream_t s);

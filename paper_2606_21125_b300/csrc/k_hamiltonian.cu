@@ -1196,7 +1196,8 @@ struct Shape {
 };
 constexpr Shape kShapes[] = {{0, 128, 1}, {0, 128, 2}, {0, 256, 1}, {0, 256, 2}, {0, 512, 1},
                              {0, 512, 2}, {0, 512, 4}, {1, 128, 1}, {1, 256, 1}, {1, 512, 1},
-                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}, {2, 128, 1}, {2, 256, 1}, {3, 256, 1}};
+                             {1, 1024, 1}, {1, 256, 2}, {1, 512, 2}, {2, 128, 1}, {2, 256, 1}, {3, 256, 1},
+                             {4, 256, 1}, {4, 512, 1}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 static_assert(kNumShapes <= DC_TUNE_SLOTS, "tuning slots");
 
@@ -1276,7 +1277,9 @@ int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
     case 12: return run_hpair<512, 2>(c, a, s);
     case 13: return run_hpair<128, 1, 6>(c, a, s);
     case 14: return run_hpair<256, 1, 3>(c, a, s);
-    default: return run_hpair<256, 1, 2, true>(c, a, s);
+    case 15: return run_hpair<256, 1, 2, true>(c, a, s);
+    default:
+      return dck::launch_cheb(c, a.mode, a.step, a.yin, a.yprev, a.yout, a.cin, a.cout, s);
   }
 }
 
@@ -1285,6 +1288,11 @@ int run_shape<float>(dc_ctx *c, int shape, HArgs<float> a, cudaStream_t s) {
 bool shape_ok(const dc_ctx *c, int shape, size_t esz) {
   if (shape < 0 || shape >= kNumShapes) return false;
   const Shape S = kShapes[shape];
+  if (S.kind == 4) {
+    // the specialised kernel: one CTA of 256 threads for extents up to 22, 512 for 32
+    const int E = esz == sizeof(float) ? dck::cheb_extent(c) : 0;
+    return E > 0 && S.nt == (E <= 22 ? 256 : 512);
+  }
   if (S.kind >= 1 && (esz != sizeof(float) || hpair_smem(c, S.nt, S.pp, S.kind == 3) > 227 * 1024)) return false;
   const int pairs = ((c->max_E[0] + 1) / 2) * c->max_E[1];
   const int cover = S.nt * S.pp;
@@ -1321,6 +1329,10 @@ int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T 
   a.dots = dots;
   int shape = c->hstep_shape[sizeof(T) == 8 ? 1 : 0];
   if (!shape_ok(c, shape, sizeof(T))) shape = default_shape(c, sizeof(T));
+  // the specialised kernel takes Chebyshev steps and plain H-applies with input projections; the
+  // adjoint (and any call without projections) runs the general kernel's default shape
+  if (kShapes[shape].kind == 4 && ((mode != HSTEP_CHEB && mode != HSTEP_HPSI) || !cin || !yout))
+    shape = default_shape(c, sizeof(T));
   return run_shape<T>(c, shape, a, s);
 }
 

@@ -8,7 +8,9 @@ Input: the oracle warms each fragment up (Rayleigh-Ritz of the SplitMix64 start,
 the starting potential), rounds the orbitals to FP32 and hands them, with their Ritz values, to the
 library (set_state); both sides then run one CheFSI pass and the density stage from that same
 FP32-rounded state.  Tolerances are the method's accuracy budget: 1e-5 Ha for eigenvalues and mu,
-1e-5 relative (L1) for core weights and density.
+1e-5 relative (L1) for the density; core weights within 1e-5 of the largest, per state where the state
+is separated from its neighbours by more than 1e-3 Ha and summed over each cluster of nearly
+degenerate states otherwise (their eigenvectors, hence their individual weights, are not unique).
 """
 import numpy as np
 import pytest
@@ -48,6 +50,29 @@ def _gpu_pass(cfg, psi_fp32, eps, V, env=None):
         return s.layout, e1.cpu().numpy(), q.cpu().numpy(), float(mu.item()), rho.cpu().numpy()
 
 
+def _clusters(eps, gap):
+    """Runs of consecutive (ascending) eigenvalues closer than ``gap``: their eigenvectors, and so their
+    individual core weights, are not determined by the Hamiltonian, only the cluster's span is."""
+    out, start = [], 0
+    for i in range(1, len(eps) + 1):
+        if i == len(eps) or eps[i] - eps[i - 1] > gap:
+            out.append((start, i))
+            start = i
+    return out
+
+
+def _assert_core_weights(st, e1, q, ref_e, ref_q, gap=1e-3, frags=None):
+    """Core weights per state where the state is separated from its neighbours by more than ``gap`` Ha,
+    and summed over each cluster of nearly degenerate states otherwise (a sum invariant under rotations
+    inside the cluster), within 1e-5 of the largest weight."""
+    eps_f, q_f = unpack_states(st, ref_e), unpack_states(st, ref_q)
+    got_f = unpack_states(st, q)
+    tol = 1e-5 * np.max(ref_q)
+    for f in (range(st.frags.nfrag) if frags is None else frags):
+        for a, b in _clusters(eps_f[f], gap):
+            assert abs(np.sum(got_f[f][a:b]) - np.sum(q_f[f][a:b])) < tol * (b - a), (f, a, b)
+
+
 def test_mixed_pass_and_density_si_weak64_whole():
     """All 64 fragments of the 64-atom weak-scaling cell (22^3 fragments, 48 orbitals), 4096-point Gram
     items: every eigenvalue, core weight, mu and the whole density against the oracle."""
@@ -68,7 +93,7 @@ def test_mixed_pass_and_density_si_weak64_whole():
     ref_e = pack(st, {f: res[f][0] for f in range(nf)})
     ref_q = pack(st, {f: res[f][1] for f in range(nf)})
     assert np.max(np.abs(e1 - ref_e)) < 1e-5
-    assert np.max(np.abs(q - ref_q)) < 1e-5 * np.max(ref_q)
+    _assert_core_weights(st, e1, q, ref_e, ref_q)
     ref_mu = fermi.find_mu(ref_e, ref_q, st.ne, st.kT)
     assert abs(mu - ref_mu) < 1e-5
     ref_rho = np.zeros(st.grid.npts)
@@ -115,7 +140,9 @@ def test_mixed_pass_si512_sampled_fragments():
         a, b = soff[f], soff[f + 1]
         assert np.max(np.abs(e1[a:b] - st.eps[f])) < 1e-5, f
         ref_q = density.core_weights(st.frags, f, st.psi[f], st.grid.dV)
-        assert np.max(np.abs(q[a:b] - ref_q)) < 1e-5 * np.max(ref_q), f
+        tol = 1e-5 * np.max(ref_q)
+        for ca, cb in _clusters(st.eps[f], 1e-3):
+            assert abs(np.sum(q[a + ca:a + cb]) - np.sum(ref_q[ca:cb])) < tol * (cb - ca), (f, ca, cb)
     # the chemical potential fixes the electron count (Eq. 4) and the density integrates to it
     assert abs(float(np.sum(2.0 * fermi.occupation(e1, mu, st.kT) * q)) - st.ne) < 1e-8 * st.ne
     assert np.min(rho) >= 0.0

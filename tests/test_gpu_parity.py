@@ -107,7 +107,7 @@ def test_starting_orbitals_bit_exact():
 
 def _hpsi_against_oracle(case, dtype, shapes=(None,)):
     """H psi of a seeded random block under each launch shape (None = default), against the oracle."""
-    cfg = CASES[case](precision=dtype)
+    cfg = (CASES[case] if case in CASES else CASES_EXTRA[case])(precision=dtype)
     st = oracle_state(cfg)
     V = _synthetic_potential(st.grid, seed=17)
     r = np.random.default_rng(11)
@@ -140,19 +140,30 @@ def test_hpsi(case, dtype):
 # (kind, threads per CTA, point pairs per thread) of the stencil kernels
 SHAPES = [(0, 128, 1), (0, 128, 2), (0, 256, 1), (0, 256, 2), (0, 512, 1), (0, 512, 2), (0, 512, 4),
           (1, 128, 1), (1, 256, 1), (1, 512, 1), (1, 1024, 1), (1, 256, 2), (1, 512, 2), (2, 128, 1), (2, 256, 1),
-          (3, 256, 1)]
+          (3, 256, 1), (4, 256, 1), (4, 512, 1)]
 
 
-@pytest.mark.parametrize("case", ["si8", "uneven", "periodic", "wide", "water_auto"])
+# cubic 32^3 fragments (16^3 cores + 8-point buffers, the water workload's fragment shape) of a small
+# water-like cell: the 512-thread instance of the specialised kernel
+CASES_EXTRA = {
+    "water32": lambda **kw: workloads.small_config(n=(32, 32, 32), L=(10.93, 10.93, 10.93), num_fragment=(2, 2, 2),
+                                                   buffer=(8, 8, 8), nstate=0, natom=9, seed=12, species=("O", "H"),
+                                                   **kw),
+}
+
+
+@pytest.mark.parametrize("case", ["si8", "uneven", "periodic", "wide", "water_auto", "water32"])
 @pytest.mark.parametrize("dtype", ["fp64", "fp32"])
 def test_hpsi_every_launch_shape(case, dtype):
-    """Every launch shape that fits the case (both kernel kinds in FP32) gives the oracle's H psi."""
+    """Every launch shape that fits the case (every kernel kind in FP32) gives the oracle's H psi."""
     ran = _hpsi_against_oracle(case, dtype, SHAPES)
     assert any(k == 0 for k, _, _ in ran)
     if dtype == "fp32":
         assert any(k == 1 for k, _, _ in ran) and any(k == 2 for k, _, _ in ran)
         if case in ("si8", "uneven"):  # planes large enough for the 256-thread all-records kernel
             assert any(k == 3 for k, _, _ in ran)
+        if case in ("si8", "water_auto", "water32"):  # uniform cubic fragments, zero boundary
+            assert any(k == 4 for k, _, _ in ran)
     else:
         assert all(k == 0 for k, _, _ in ran)
 
@@ -179,11 +190,11 @@ def test_subspace_and_one_chefsi_pass_fp64(case):
     assert np.max(np.abs(e1 - eps_1)) < 1e-9 * max(1.0, np.max(np.abs(eps_1)))
 
 
-@pytest.mark.parametrize("case", ["periodic", "uneven", "water_auto"])
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("case", ["periodic", "uneven", "water_auto", "si8", "water32"])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
 def test_subspace_and_one_chefsi_pass_fp32(case, kind):
-    """FP32 filter steps (with their in-kernel projections) under both stencil kernel kinds."""
-    cfg = CASES[case](precision="fp32")
+    """FP32 filter steps (with their in-kernel projections) under every stencil kernel kind that fits."""
+    cfg = (CASES[case] if case in CASES else CASES_EXTRA[case])(precision="fp32")
     st = oracle_state(cfg)
     V = st.veff(st.rho_in)
     st.initial_rr(V)
@@ -405,15 +416,17 @@ def test_errors_are_status_codes():
         assert np.isfinite(good["E"])
 
 
-def test_full_size_hpsi_sampled_si512():
-    """Si512 at full size (80^3 grid, 512 fragments of 22^3, 48 orbitals), FP32 H-apply as the bench
-    launches it; a few fragments are recomputed by the oracle."""
+@pytest.mark.parametrize("shape", [(3, 256, 1), (4, 256, 1)])
+def test_full_size_hpsi_sampled_si512(shape):
+    """Si512 at full size (80^3 grid, 512 fragments of 22^3, 48 orbitals), FP32 H-apply under the general
+    and the specialised orbital-pair kernels; a few fragments are recomputed by the oracle."""
     cfg = workloads.make_config("si512", precision="fp32")
     sample = [0, 137, 511]
     st = oracle_state(cfg, subset=sample)
     V = _synthetic_potential(st.grid, seed=23)
     r = np.random.default_rng(2)
     with _solver(cfg) as s:
+        assert s.set_tuning("fp32", *shape)
         s.set_potential(torch.tensor(V.reshape(-1), dtype=torch.float64, device="cuda"))
         psi = torch.tensor(r.standard_normal(s.layout.psi_elems), dtype=torch.float32, device="cuda")
         out = s.hpsi(psi)
