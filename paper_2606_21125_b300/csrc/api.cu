@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux, c->d_vf2};
+                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -683,7 +683,6 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   // fragment-point and per-state arrays
   DC_TRY(dmalloc(&c->d_vf64, (size_t)Lo.frag_points));
   DC_TRY(dmalloc(&c->d_vf32, (size_t)Lo.frag_points));
-  if (c->params.precision != DC_FP64) DC_TRY(dmalloc(&c->d_vf2, (size_t)Lo.frag_points));
   long long cn = 0;
   for (auto &D : c->h_desc) cn += (long long)D.natom * D.norb;
   for (int k = 0; k < 2; ++k) {

@@ -128,7 +128,6 @@ struct dc_ctx {
   // per-fragment-point potential
   double *d_vf64 = nullptr;
   float *d_vf32 = nullptr;
-  float2 *d_vf2 = nullptr;  // FP32 (V, V) per point for the specialised orbital-pair kernel
 
   // orbital blocks: 3 rotating blocks of the context precision (index of the state in ib_psi)
   void *blk[3] = {nullptr, nullptr, nullptr};

@@ -11,8 +11,16 @@
 // and the (x, y) of a thread is a division by a constant), the boundary (no wrap-around stores),
 // the isotropic stencil coefficients, the presence of Y_{k-1} and of output projections (template
 // flags), and even extents (every point pair and every orbital row is 8-byte aligned, so each global
-// access is one 8-byte load or store, without predicates).  The potential is read pre-splatted,
-// (V, V) per point, so no lane copies are needed to multiply an orbital pair.
+// access is one 8-byte load or store, without predicates).
+//
+// Data movement: the kernel is bound by memory latency unless several planes are in flight, and
+// register prefetch holds at most one.  So one thread streams, for every plane z, the planes
+// y_in(z + 4), y_prev(z) and V(z) with 1-D bulk asynchronous copies (cp.async.bulk, whole contiguous
+// planes of the orbital-major layout, completion counted in bytes on an mbarrier) into a ring of
+// RING slots in shared memory, RING - 1 planes ahead of their use; the other threads read their points
+// from the ring.  Every wait on a slot is bounded: a thread that gives up sets the error flag and an
+// abort word that every thread reads after the next barrier; the CTA then waits (bounded) for the
+// copies still in flight and returns.
 //
 // Nonlocal term: the fragment's row lists (one entry per (row, projector slot) with gz gy != 0,
 // host-built) are staged in shared memory once per CTA; each plane turns its entries into records
@@ -21,6 +29,8 @@
 // Chebyshev step, are formed one plane behind by one task per record: gz gy sum_x gx[x] out(x, y)
 // into a dense [row][slot] accumulator (one writer per element and plane), rows summed at the end.
 // One barrier per plane.
+#include <stdint.h>
+
 #include <type_traits>
 
 #include "dc_internal.h"
@@ -35,7 +45,8 @@ struct ChebArgs {
   const int *row_beg;     // per (fragment, z, y) start into row_ent
   const int2 *row_ent;    // (slot | y << 16, FP32 bits of gz gy)
   const double *Datom;
-  const float2 *vf2;      // (V, V) per fragment point
+  const float *vf;        // V per fragment point (FP32)
+  unsigned *flags;        // device error flags (DC_FLAG_TIMEOUT)
   const float *yin;
   const float *yprev;
   float *yout;
@@ -68,7 +79,41 @@ struct Geo {
   static constexpr int PPLANE = PITCH * HROWS;       // one haloed plane (float2)
   static constexpr int PLANE = E * E;
   static constexpr int MINB = NT <= 256 ? 2 : 1;
+  static constexpr int RING = 4;                     // plane slots in flight
 };
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(bytes) : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completion counted
+// on `bar`
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   su32(dst)),
+               "l"(src), "r"(bytes), "r"(su32(bar))
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`; false when the poll limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < DC_SPIN_LIMIT; ++it) {
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 // Shared-memory carve (float2 units first, 16-byte aligned blocks).
 template <int E>
@@ -84,22 +129,46 @@ struct ChebSmem {
   int2 *sent;    // [nent]        the fragment's row-list entries
   int2 *box;     // [A]           even-aligned x support
   int *rb;       // [E*E + 1]     row starts (relative to the fragment's first entry)
+  float *ring;   // [RING][NSUB][E*E] y_in(z + 4) (2 orbitals), [y_prev(z) (2 orbitals)], V(z)
+  uint64_t *full;  // [RING] slot barriers
+  volatile int *abort;  // set by a thread whose bounded wait ran out
+  int *issued;          // [RING] uses of each slot so far (producer thread only)
+  struct Hdr {
+    const float *yin, *yprev, *vf;  // the pair's rows (orbital i; i + 1 at + E^3) and V of the fragment
+    int nvalid;                     // 1 or 2 orbitals
+    float2 ksh, al2, be2;           // kc - shift, alpha, beta (splatted)
+  } *hdr;
 };
 
-template <int E>
+// Planes per ring slot: y_in of the pair, y_prev of the pair (with PREV), V.
+template <bool PREV>
+__host__ __device__ constexpr int ring_sub() {
+  return PREV ? 5 : 3;
+}
+
+template <int E, bool PREV>
 __host__ __device__ inline size_t cheb_smem_bytes(int A, int maxent, int nent) {
   using G = Geo<E>;
+  size_t b = (size_t)G::RING * ring_sub<PREV>() * G::PLANE * sizeof(float) + 256;  // ring, barriers, header
   size_t n2 = 2 * (size_t)G::PPLANE + 2 * (size_t)G::PLANE + (size_t)A * E + (size_t)E * A + A;
-  size_t b = (n2 * sizeof(float2) + 15) & ~(size_t)15;
+  b += (n2 * sizeof(float2) + 15) & ~(size_t)15;
   b += 3 * (size_t)maxent * sizeof(float4);
   b += (size_t)nent * sizeof(int2) + (size_t)A * sizeof(int2) + (size_t)(G::PLANE + 1) * sizeof(int);
   return b + 64;
 }
 
-template <int E>
+template <int E, bool PREV>
 __device__ __forceinline__ ChebSmem<E> cheb_carve(unsigned char *raw, int A, int maxent, int nent) {
   using G = Geo<E>;
   ChebSmem<E> m;
+  m.ring = reinterpret_cast<float *>(raw);  // 16-byte aligned slots (E^2 floats are multiples of 16 bytes)
+  unsigned char *after = raw + (size_t)G::RING * ring_sub<PREV>() * G::PLANE * sizeof(float);
+  m.full = reinterpret_cast<uint64_t *>(after);
+  m.abort = reinterpret_cast<volatile int *>(m.full + G::RING);
+  m.issued = reinterpret_cast<int *>(m.full + G::RING) + 1;
+  m.hdr = reinterpret_cast<typename ChebSmem<E>::Hdr *>(after + 64);
+  after += 64 + 128;
+  raw = after + 64;
   m.pin = reinterpret_cast<float2 *>(raw);
   m.pout = m.pin + 2 * G::PPLANE;
   m.gx2 = m.pout + 2 * G::PLANE;
@@ -119,15 +188,45 @@ struct ChebT {
   int px, py;      // owned points (px, py), (px + 1, py)
   bool active;     // owns a point pair
   int t0;          // py E + px
-  float2 ksh;      // centre coefficient minus the filter shift, splatted
-  float2 al2, be2; // alpha, beta splatted
 };
 
-// Plane z.  ZI = z mod 9 names the column registers: q[(ZI + k) % 9] holds plane z - 4 + k.
+// Issue the bulk copies of iteration z (y_in(z + 4), y_prev(z), V(z)) into ring slot z % RING.
+template <int E, bool PREV>
+__device__ __forceinline__ void ring_issue(const ChebSmem<E> &m, int z) {
+  const typename ChebSmem<E>::Hdr &F = *m.hdr;
+  using G = Geo<E>;
+  constexpr uint32_t PB = G::PLANE * sizeof(float);
+  constexpr long long P = (long long)G::PLANE * E;
+  const int s = z % G::RING;
+  float *slot = m.ring + (size_t)s * ring_sub<PREV>() * G::PLANE;
+  uint64_t *bar = m.full + s;
+  const bool has_y = z + 4 < E;
+  uint32_t bytes = PB;  // V
+  if (has_y) bytes += F.nvalid * PB;
+  if (PREV) bytes += F.nvalid * PB;
+  // the slot was last read through ordinary shared loads (ordered before this by the CTA barrier); the
+  // bulk copies write it through the async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  m.issued[s] += 1;
+  mbar_expect_tx(bar, bytes);
+  if (has_y) {
+    const float *src = F.yin + (long long)(z + 4) * G::PLANE;
+    bulk_g2s(slot, src, PB, bar);
+    if (F.nvalid > 1) bulk_g2s(slot + G::PLANE, src + P, PB, bar);
+  }
+  if (PREV) {
+    const float *src = F.yprev + (long long)z * G::PLANE;
+    bulk_g2s(slot + 2 * G::PLANE, src, PB, bar);
+    if (F.nvalid > 1) bulk_g2s(slot + 3 * G::PLANE, src + P, PB, bar);
+  }
+  bulk_g2s(slot + (ring_sub<PREV>() - 1) * G::PLANE, F.vf + (long long)z * G::PLANE, PB, bar);
+}
+
+// Plane z.  ZI = z mod 9 names the column registers: q[(ZI + k) % 9] holds plane z - 4 + k (plane z + 4
+// arrives from the ring during this plane).  Returns false when the CTA aborts.
 template <int E, bool PREV, bool PROJ, int ZI>
-__device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> &m, const ChebT &T, float4 (&q)[9],
-                                           float4 &vv, float4 &pv, int z, int A, int nvalid, const float *yin,
-                                           const float *yprev, float *yout, const float2 *vf2) {
+__device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> &m, const ChebT &T, float4 (&q)[9],
+                                           int z, int A, float *yout) {
   using G = Geo<E>;
   const int slot = z & 1;
   float2 *P0 = m.pin + slot * G::PPLANE;
@@ -146,6 +245,9 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
     }
   }
   __syncthreads();
+  if (*m.abort) return false;
+  // refill the slot that plane z - 1 has finished with, for plane z - 1 + RING
+  if (threadIdx.x == 0 && z >= 1 && z - 1 + G::RING < E) ring_issue<E, PREV>(m, z - 1 + G::RING);
   // projections of the previous output plane
   if (PROJ && z > 0) {
     const int zp = z - 1, ps = zp & 1;
@@ -171,9 +273,24 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
       pa = fma2(f2(w, w), add2(s0, s1), pa);
     }
   }
-  if (!T.active) return;
-  const float4 V = vv;
-  const float4 Y1 = pv;
+  if (!T.active) return true;
+  // this plane's ring slot: y_in(z + 4) completes the column; y_prev(z) and V(z)
+  if (!mbar_wait(m.full + z % G::RING, (uint32_t)((z / G::RING) & 1))) {
+    atomicOr(a.flags, DC_FLAG_TIMEOUT);
+    *m.abort = 1;
+    return true;
+  }
+  const float *rs = m.ring + (size_t)(z % G::RING) * ring_sub<PREV>() * G::PLANE + T.t0;
+  const int nvalid = m.hdr->nvalid;
+  {
+    float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (z + 4 < E) {
+      const float2 u0 = *reinterpret_cast<const float2 *>(rs);
+      const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(rs + G::PLANE) : f2(0.f, 0.f);
+      nxt = make_float4(u0.x, u1.x, u0.y, u1.y);
+    }
+    q[(ZI + 8) % 9] = nxt;  // plane z + 4 replaces plane z - 5
+  }
   // Laplacian in difference form: taps 1, 2 as (y+n - y) + (y-n - y), taps 3, 4 as y+n + y-n with the
   // centre term added once; tap by tap, so each tap's loads die before the next are needed.
   // x neighbours of point 0 (x = px) and point 1 (px + 1): X0 = (px-4, px-3), X1 = (px-2, px-1),
@@ -183,9 +300,8 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   const float2 c0 = lo2(C), c1 = hi2(C);
   const float4 X1 = *reinterpret_cast<const float4 *>(co - 2);
   const float4 X3 = *reinterpret_cast<const float4 *>(co + 2);
-  // H y without alpha: (kc - shift + V) y, the taps, then the nonlocal term
-  float2 h0 = fma2(T.ksh, c0, mul2(lo2(V), c0));
-  float2 h1 = fma2(T.ksh, c1, mul2(hi2(V), c1));
+  // H y without alpha: the taps, (kc - shift + V) y, then the nonlocal term
+  float2 h0, h1;
   float2 t0, t1;
 #define DC_YZ_TAPS(N, DIFF)                                                                                  \
   {                                                                                                        \
@@ -205,8 +321,8 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   t0 = add2(sub2(c1, c0), sub2(hi2(X1), c0));
   t1 = add2(sub2(lo2(X3), c1), sub2(c0, c1));
   DC_YZ_TAPS(1, true)
-  h0 = fma2(f2(a.k1, a.k1), t0, h0);
-  h1 = fma2(f2(a.k1, a.k1), t1, h1);
+  h0 = mul2(f2(a.k1, a.k1), t0);
+  h1 = mul2(f2(a.k1, a.k1), t1);
   // tap 2
   t0 = add2(sub2(lo2(X3), c0), sub2(lo2(X1), c0));
   t1 = add2(sub2(hi2(X3), c1), sub2(hi2(X1), c1));
@@ -227,6 +343,12 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   h0 = fma2(f2(a.k4, a.k4), t0, h0);
   h1 = fma2(f2(a.k4, a.k4), t1, h1);
 #undef DC_YZ_TAPS
+  {
+    const float2 ksh = m.hdr->ksh;
+    const float2 vr = *reinterpret_cast<const float2 *>(rs + (ring_sub<PREV>() - 1) * G::PLANE);
+    h0 = fma2(ksh, c0, fma2(f2(vr.x, vr.x), c0, h0));
+    h1 = fma2(ksh, c1, fma2(f2(vr.y, vr.y), c1, h1));
+  }
   // nonlocal term over the row's records
   {
     const int rz = z * E + T.py;
@@ -250,12 +372,16 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
     }
   }
   float2 o0, o1;
+  const float2 al2 = m.hdr->al2;
   if (PREV) {
-    o0 = fma2(T.al2, h0, mul2(T.be2, lo2(Y1)));
-    o1 = fma2(T.al2, h1, mul2(T.be2, hi2(Y1)));
+    const float2 be2 = m.hdr->be2;
+    const float2 u0 = *reinterpret_cast<const float2 *>(rs + 2 * G::PLANE);
+    const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(rs + 3 * G::PLANE) : f2(0.f, 0.f);
+    o0 = fma2(al2, h0, mul2(be2, f2(u0.x, u1.x)));
+    o1 = fma2(al2, h1, mul2(be2, f2(u0.y, u1.y)));
   } else {
-    o0 = mul2(T.al2, h0);
-    o1 = mul2(T.al2, h1);
+    o0 = mul2(al2, h0);
+    o1 = mul2(al2, h1);
   }
   {
     float *po = yout + z * G::PLANE + T.t0;
@@ -265,28 +391,7 @@ __device__ __forceinline__ void cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   if (PROJ)
     *reinterpret_cast<float4 *>(m.pout + slot * G::PLANE + T.t0) =
         make_float4(o0.x, nvalid > 1 ? o0.y : 0.f, o1.x, nvalid > 1 ? o1.y : 0.f);
-  // loads for later planes, issued once this plane's stencil no longer needs registers: y_in of plane
-  // z + 5 into the column slot of plane z - 4, V and y_prev of plane z + 1
-  {
-    const int zn = z + 5;
-    float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (zn < E) {
-      const float *p = yin + zn * G::PLANE + T.t0;
-      const float2 u0 = *reinterpret_cast<const float2 *>(p);
-      const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(p + E * G::PLANE) : f2(0.f, 0.f);
-      nxt = make_float4(u0.x, u1.x, u0.y, u1.y);
-    }
-    q[ZI % 9] = nxt;
-    if (z + 1 < E) {
-      const int t1 = (z + 1) * G::PLANE + T.t0;
-      vv = *reinterpret_cast<const float4 *>(vf2 + t1);
-      if (PREV) {
-        const float2 u0 = *reinterpret_cast<const float2 *>(yprev + t1);
-        const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(yprev + t1 + E * G::PLANE) : f2(0.f, 0.f);
-        pv = make_float4(u0.x, u1.x, u0.y, u1.y);
-      }
-    }
-  }
+  return true;
 }
 
 template <int E, bool PREV, bool PROJ>
@@ -297,18 +402,39 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
   const int f = fi.x, i0 = fi.y;
   const FragDesc &D = a.desc[f];
   const int A = D.natom;
-  const int nvalid = min(2, D.norb - i0);
   const int r0 = a.row_beg[D.row_off];
   const int nent = a.row_beg[D.row_off + G::PLANE] - r0;
-  const ChebSmem<E> m = cheb_carve<E>(smem_raw, A, a.maxent, nent);
+  const ChebSmem<E> m = cheb_carve<E, PREV>(smem_raw, A, a.maxent, nent);
   const int tabw = tab_width(D);
+  constexpr long long P = (long long)G::PLANE * E;
+  const long long base = D.psi_off + (long long)i0 * P;
+  const int nvalid = min(2, D.norb - i0);
+  float *yout = a.yout + base;
 
-  float alpha = 1.f, beta = 0.f, shift = 0.f;
-  if (a.cheb) {
-    const double *bd = a.bounds + (long long)f * a.bstride;
-    shift = float(bd[3]);
-    alpha = float(bd[4 + 2 * a.step]);
-    beta = float(bd[5 + 2 * a.step]);
+  // the producer starts the first RING planes' copies before the table set-up
+  if (threadIdx.x == 0) {
+    float alpha = 1.f, beta = 0.f, shift = 0.f;
+    if (a.cheb) {
+      const double *bd = a.bounds + (long long)f * a.bstride;
+      shift = float(bd[3]);
+      alpha = float(bd[4 + 2 * a.step]);
+      beta = float(bd[5 + 2 * a.step]);
+    }
+    typename ChebSmem<E>::Hdr &F = *m.hdr;
+    F.yin = a.yin + base;
+    F.yprev = PREV ? a.yprev + base : nullptr;
+    F.vf = a.vf + D.pt_off;
+    F.nvalid = nvalid;
+    F.ksh = f2(a.kc - shift, a.kc - shift);
+    F.al2 = f2(alpha, alpha);
+    F.be2 = f2(beta, beta);
+    for (int k = 0; k < G::RING; ++k) {
+      mbar_init(m.full + k, 1);
+      m.issued[k] = 0;
+    }
+    *m.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int z = 0; z < G::RING && z < E; ++z) ring_issue<E, PREV>(m, z);
   }
   // tables: x factors (splatted), supports, D C <p|y>, row starts, entries; zero halo and accumulators
   for (int t = threadIdx.x; t < A * E; t += G::NT) {
@@ -334,43 +460,25 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
   T.py = T.active ? tid / G::NPX : 0;
   T.px = T.active ? 2 * (tid - T.py * G::NPX) : 0;
   T.t0 = T.py * E + T.px;
-  T.ksh = f2(a.kc - shift, a.kc - shift);
-  T.al2 = f2(alpha, alpha);
-  T.be2 = f2(beta, beta);
 
-  const long long P = (long long)G::PLANE * E;
-  const long long base = D.psi_off + (long long)i0 * P;
-  const float *yin = a.yin + base;
-  const float *yprev = PREV ? a.yprev + base : nullptr;
-  float *yout = a.yout + base;
-  const float2 *vf2 = a.vf2 + D.pt_off;
-  // z column of planes -4..4 (zero outside the fragment), V and y_prev of plane 0
+  // z column: planes -4..-1 are zero, planes 0..3 read directly; plane 4 arrives with plane 0's slot
   float4 q[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (T.active && k >= 4 && k - 4 < E) {
-      const float *p = yin + (k - 4) * G::PLANE + T.t0;
+    if (T.active && k >= 4 && k < 8 && k - 4 < E) {
+      const float *p = a.yin + base + (k - 4) * G::PLANE + T.t0;
       const float2 u0 = *reinterpret_cast<const float2 *>(p);
       const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(p + P) : f2(0.f, 0.f);
       q[k] = make_float4(u0.x, u1.x, u0.y, u1.y);
     }
   }
-  float4 vv = make_float4(0.f, 0.f, 0.f, 0.f), pv = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (T.active) {
-    vv = *reinterpret_cast<const float4 *>(vf2 + T.t0);
-    if (PREV) {
-      const float2 u0 = *reinterpret_cast<const float2 *>(yprev + T.t0);
-      const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(yprev + T.t0 + P) : f2(0.f, 0.f);
-      pv = make_float4(u0.x, u1.x, u0.y, u1.y);
-    }
-  }
   __syncthreads();
 
+  bool ok = true;
 #define DC_CHEB_PLANE(ZI)                                                                                  \
-  if (z0 + ZI < E)                                                                                         \
-    cheb_plane<E, PREV, PROJ, ZI>(a, m, T, q, vv, pv, z0 + ZI, A, nvalid, yin, yprev, yout, vf2);
-  for (int z0 = 0; z0 < E; z0 += 9) {
+  if (ok && z0 + ZI < E) ok = cheb_plane<E, PREV, PROJ, ZI>(a, m, T, q, z0 + ZI, A, yout);
+  for (int z0 = 0; z0 < E && ok; z0 += 9) {
     DC_CHEB_PLANE(0)
     DC_CHEB_PLANE(1)
     DC_CHEB_PLANE(2)
@@ -382,8 +490,16 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
     DC_CHEB_PLANE(8)
   }
 #undef DC_CHEB_PLANE
+  __syncthreads();
+  if (*m.abort) {
+    // a bounded wait ran out: let the copies still in flight land (bounded) before the CTA's shared
+    // memory is released, then return without projections
+    if (threadIdx.x == 0)
+      for (int k = 0; k < G::RING; ++k)
+        if (m.issued[k] > 0) mbar_wait(m.full + k, (uint32_t)((m.issued[k] - 1) & 1));  // its last use
+    return;
+  }
   if (PROJ) {
-    __syncthreads();
     // the last plane's projection tasks
     {
       const int zp = E - 1, ps = zp & 1;
@@ -423,14 +539,14 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
 
 template <int E>
 bool cheb_fits(const dc_ctx *c) {
-  return cheb_smem_bytes<E>(c->max_atoms, std::max(1, c->max_plane_ent), std::max(1, c->max_frag_ent)) <=
+  return cheb_smem_bytes<E, true>(c->max_atoms, std::max(1, c->max_plane_ent), std::max(1, c->max_frag_ent)) <=
          227 * 1024;
 }
 
 template <int E, bool PREV, bool PROJ>
 int run_cheb(const dc_ctx *c, const ChebArgs &a, cudaStream_t s) {
   using G = Geo<E>;
-  const size_t sm = cheb_smem_bytes<E>(c->max_atoms, a.maxent, std::max(1, c->max_frag_ent));
+  const size_t sm = cheb_smem_bytes<E, PREV>(c->max_atoms, a.maxent, std::max(1, c->max_frag_ent));
   DC_CUDA(dc_set_smem((const void *)k_cheb<E, PREV, PROJ>, sm));
   if (c->n_items2 > 0) k_cheb<E, PREV, PROJ><<<(unsigned)c->n_items2, G::NT, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
@@ -481,7 +597,8 @@ int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yp
   a.row_beg = c->d_row_beg;
   a.row_ent = c->d_row_ent;
   a.Datom = c->d_atom_D;
-  a.vf2 = c->d_vf2;
+  a.vf = c->d_vf32;
+  a.flags = c->d_flags;
   a.yin = yin;
   a.yprev = yprev;
   a.yout = yout;

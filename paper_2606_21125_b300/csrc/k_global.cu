@@ -96,7 +96,7 @@ __global__ void k_veff(long long n, const double *vion, const double2 *vh, doubl
 // Per-fragment potential gather and rigorous spectral upper bound of H_f:
 //   b_up = max symbol of -1/2 L8 + max_j V_f(j) + sum_k max(D_k, 0) <p_k|p_k>.
 __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const double *veff, double *vf64, float *vf32,
-                         float2 *vf2, const double *nl_bound, double kin_max, double *bounds, int bstride) {
+                         const double *nl_bound, double kin_max, double *bounds, int bstride) {
   __shared__ double red[8];
   const int f = blockIdx.x;
   const FragDesc D = desc[f];
@@ -106,7 +106,6 @@ __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const dou
     const double v = veff[idx_map[D.pt_off + j]];
     vf64[D.pt_off + j] = v;
     if (vf32) vf32[D.pt_off + j] = (float)v;
-    if (vf2) vf2[D.pt_off + j] = make_float2((float)v, (float)v);
     vmax = fmax(vmax, v);
   }
   for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -342,7 +341,7 @@ int launch_gather(dc_ctx *c, cudaStream_t s) {
   const int bstride = 4 + 2 * c->params.cheb_degree;
   const int nf = c->f_hi - c->f_lo;  // the context's fragment shard (all fragments on one rank)
   if (nf <= 0) return DC_OK;
-  k_gather<<<nf, 256, 0, s>>>(c->d_desc + c->f_lo, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32, c->d_vf2,
+  k_gather<<<nf, 256, 0, s>>>(c->d_desc + c->f_lo, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32,
                               c->d_nl_bound + c->f_lo, kin, c->d_bounds + (long long)c->f_lo * bstride, bstride);
   DC_CUDA(cudaGetLastError());
   return DC_OK;

@@ -159,7 +159,9 @@ def test_hpsi_every_launch_shape(case, dtype):
     ran = _hpsi_against_oracle(case, dtype, SHAPES)
     assert any(k == 0 for k, _, _ in ran)
     if dtype == "fp32":
-        assert any(k == 1 for k, _, _ in ran) and any(k == 2 for k, _, _ in ran)
+        assert any(k == 1 for k, _, _ in ran)
+        if case != "water32":  # 32^3 planes need more than the register-capped kernel's 256 threads
+            assert any(k == 2 for k, _, _ in ran)
         if case in ("si8", "uneven"):  # planes large enough for the 256-thread all-records kernel
             assert any(k == 3 for k, _, _ in ran)
         if case in ("si8", "water_auto", "water32"):  # uniform cubic fragments, zero boundary
