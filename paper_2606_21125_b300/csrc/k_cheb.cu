@@ -69,6 +69,11 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
+// Projection tasks per record.  Splitting each record's x-support into two tasks with two accumulator
+// planes spreads a plane's tasks over every warp, but the second accumulator plane took the shared
+// memory of the second CTA per SM (Si, 22^3 fragments): 269 -> 394 us per launch on the 64-atom cell.
+constexpr int kPSplit = 1;
+
 template <int E>
 struct Geo {
   static constexpr int NPX = E / 2;                  // point pairs per row
@@ -121,7 +126,7 @@ struct ChebSmem {
   float2 *pin;   // [2][PPLANE]   haloed planes of y_in
   float2 *pout;  // [2][E*E]      output planes (projections)
   float2 *gx2;   // [A][E]        x factors, splatted (g, g)
-  float2 *pacc;  // [E][A]        projection accumulators
+  float2 *pacc;  // [kPSplit][E][A] projection accumulators
   float2 *sk2;   // [A]           D C <p|y> of the pair
   float4 *rec;   // [3][maxent]   per-plane records (a plane's records are read by its own stencil and, one
                  //               plane later, by its projection tasks, so three slots keep the writer of
@@ -150,7 +155,7 @@ template <int E, bool PREV>
 __host__ __device__ inline size_t cheb_smem_bytes(int A, int maxent, int nent) {
   using G = Geo<E>;
   size_t b = (size_t)G::RING * ring_sub<PREV>() * G::PLANE * sizeof(float) + 256;  // ring, barriers, header
-  size_t n2 = 2 * (size_t)G::PPLANE + 2 * (size_t)G::PLANE + (size_t)A * E + (size_t)E * A + A;
+  size_t n2 = 2 * (size_t)G::PPLANE + 2 * (size_t)G::PLANE + (size_t)A * E + (size_t)kPSplit * E * A + A;
   b += (n2 * sizeof(float2) + 15) & ~(size_t)15;
   b += 3 * (size_t)maxent * sizeof(float4);
   b += (size_t)nent * sizeof(int2) + (size_t)A * sizeof(int2) + (size_t)(G::PLANE + 1) * sizeof(int);
@@ -173,7 +178,7 @@ __device__ __forceinline__ ChebSmem<E> cheb_carve(unsigned char *raw, int A, int
   m.pout = m.pin + 2 * G::PPLANE;
   m.gx2 = m.pout + 2 * G::PLANE;
   m.pacc = m.gx2 + A * E;
-  m.sk2 = m.pacc + E * A;
+  m.sk2 = m.pacc + kPSplit * E * A;
   size_t off = (size_t)(reinterpret_cast<unsigned char *>(m.sk2 + A) - raw);
   off = (off + 15) & ~(size_t)15;
   m.rec = reinterpret_cast<float4 *>(raw + off);
@@ -222,20 +227,22 @@ __device__ __forceinline__ void ring_issue(const ChebSmem<E> &m, int z) {
   bulk_g2s(slot + (ring_sub<PREV>() - 1) * G::PLANE, F.vf + (long long)z * G::PLANE, PB, bar);
 }
 
-// Plane z.  ZI = z mod 9 names the column registers: q[(ZI + k) % 9] holds plane z - 4 + k (plane z + 4
-// arrives from the ring during this plane).  Returns false when the CTA aborts.
-template <int E, bool PREV, bool PROJ, int ZI>
+// Plane z.  The column registers q[k] hold plane z - 4 + k (q[8], plane z + 4, arrives from the ring
+// during this plane) and are moved down by one plane at the end.  A loop over z with these moves runs
+// faster than a body unrolled nine times that renames the registers instead: the unrolled kernel's
+// instruction footprint stalled the warps on instruction fetch.  Returns false when the CTA aborts.
+template <int E, bool PREV, bool PROJ>
 __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> &m, const ChebT &T, float4 (&q)[9],
                                            int z, int A, float *yout) {
   using G = Geo<E>;
   const int slot = z & 1;
   float2 *P0 = m.pin + slot * G::PPLANE;
   const int c = (T.py + 4) * G::PITCH + T.px + 4;
-  if (T.active) *reinterpret_cast<float4 *>(P0 + c) = q[(ZI + 4) % 9];
+  if (T.active) *reinterpret_cast<float4 *>(P0 + c) = q[4];
   // this plane's records from its row-list entries
   {
     const int e0 = m.rb[z * E], n = m.rb[(z + 1) * E] - e0;
-    float4 *rc = m.rec + (ZI % 3) * a.maxent;
+    float4 *rc = m.rec + (z % 3) * a.maxent;
     for (int t = threadIdx.x; t < n; t += G::NT) {
       const int2 en = m.sent[e0 + t];
       const float w = __int_as_float(en.y);
@@ -252,24 +259,27 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   if (PROJ && z > 0) {
     const int zp = z - 1, ps = zp & 1;
     const int e0 = m.rb[zp * E], n = m.rb[z * E] - e0;
-    const float4 *rc = m.rec + ((ZI + 2) % 3) * a.maxent;
+    const float4 *rc = m.rec + ((z + 2) % 3) * a.maxent;
     const float4 *o4 = reinterpret_cast<const float4 *>(m.pout + ps * G::PLANE);
     const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2);
-    for (int t = threadIdx.x; t < n; t += G::NT) {
-      const int kb = m.sent[e0 + t].x;
+    for (int t = threadIdx.x; t < kPSplit * n; t += G::NT) {
+      const int e = t / kPSplit, part = t - e * kPSplit;
+      const int kb = m.sent[e0 + e].x;
       const int k = kb & 0xffff, y = kb >> 16;
       const int2 bx = m.box[k];
+      const int len = bx.y - bx.x;
+      const int xa = bx.x + (part * len) / kPSplit, xb = bx.x + ((part + 1) * len) / kPSplit;
       const float4 *orow = o4 + y * G::NPX;
       const float4 *grow = g4 + k * G::NPX;
       float2 s0 = f2(0.f, 0.f), s1 = f2(0.f, 0.f);
-      for (int x2 = bx.x; x2 < bx.y; ++x2) {
+      for (int x2 = xa; x2 < xb; ++x2) {
         const float4 o = orow[x2];
         const float4 g = grow[x2];
         s0 = fma2(lo2(o), lo2(g), s0);
         s1 = fma2(hi2(o), hi2(g), s1);
       }
-      const float w = rc[t].w;
-      float2 &pa = m.pacc[y * A + k];
+      const float w = rc[e].w;
+      float2 &pa = m.pacc[(part * E + y) * A + k];
       pa = fma2(f2(w, w), add2(s0, s1), pa);
     }
   }
@@ -289,14 +299,14 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
       const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(rs + G::PLANE) : f2(0.f, 0.f);
       nxt = make_float4(u0.x, u1.x, u0.y, u1.y);
     }
-    q[(ZI + 8) % 9] = nxt;  // plane z + 4 replaces plane z - 5
+    q[8] = nxt;  // plane z + 4
   }
   // Laplacian in difference form: taps 1, 2 as (y+n - y) + (y-n - y), taps 3, 4 as y+n + y-n with the
   // centre term added once; tap by tap, so each tap's loads die before the next are needed.
   // x neighbours of point 0 (x = px) and point 1 (px + 1): X0 = (px-4, px-3), X1 = (px-2, px-1),
   // centre (px, px+1), X3 = (px+2, px+3), X4 = (px+4, px+5), each float2 = the orbital pair
   const float2 *co = P0 + c;
-  const float4 C = q[(ZI + 4) % 9];
+  const float4 C = q[4];
   const float2 c0 = lo2(C), c1 = hi2(C);
   const float4 X1 = *reinterpret_cast<const float4 *>(co - 2);
   const float4 X3 = *reinterpret_cast<const float4 *>(co + 2);
@@ -307,8 +317,8 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   {                                                                                                        \
     const float4 U = *reinterpret_cast<const float4 *>(co + N * G::PITCH);                                 \
     const float4 Dn = *reinterpret_cast<const float4 *>(co - N * G::PITCH);                                \
-    const float4 ZU = q[(ZI + 4 + N) % 9];                                                                 \
-    const float4 ZD = q[(ZI + 4 - N) % 9];                                                                 \
+    const float4 ZU = q[4 + N];                                                                 \
+    const float4 ZD = q[4 - N];                                                                 \
     if (DIFF) {                                                                                            \
       t0 = add2(t0, add2(add2(sub2(lo2(U), c0), sub2(lo2(Dn), c0)), add2(sub2(lo2(ZU), c0), sub2(lo2(ZD), c0)))); \
       t1 = add2(t1, add2(add2(sub2(hi2(U), c1), sub2(hi2(Dn), c1)), add2(sub2(hi2(ZU), c1), sub2(hi2(ZD), c1)))); \
@@ -353,7 +363,7 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   {
     const int rz = z * E + T.py;
     const int eb = m.rb[rz] - m.rb[z * E], ee = m.rb[rz + 1] - m.rb[z * E];
-    const float4 *rc = m.rec + (ZI % 3) * a.maxent;
+    const float4 *rc = m.rec + (z % 3) * a.maxent;
     const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2) + (T.px >> 1);
     int e = eb;
     for (; e + 1 < ee; e += 2) {
@@ -391,6 +401,8 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   if (PROJ)
     *reinterpret_cast<float4 *>(m.pout + slot * G::PLANE + T.t0) =
         make_float4(o0.x, nvalid > 1 ? o0.y : 0.f, o1.x, nvalid > 1 ? o1.y : 0.f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) q[k] = q[k + 1];
   return true;
 }
 
@@ -451,7 +463,7 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
   }
   for (int t = threadIdx.x; t <= G::PLANE; t += G::NT) m.rb[t] = a.row_beg[D.row_off + t] - r0;
   for (int t = threadIdx.x; t < nent; t += G::NT) m.sent[t] = a.row_ent[r0 + t];
-  for (int t = threadIdx.x; t < E * A; t += G::NT) m.pacc[t] = f2(0.f, 0.f);
+  for (int t = threadIdx.x; t < kPSplit * E * A; t += G::NT) m.pacc[t] = f2(0.f, 0.f);
   for (int t = threadIdx.x; t < 2 * G::PPLANE; t += G::NT) m.pin[t] = f2(0.f, 0.f);
 
   ChebT T;
@@ -461,7 +473,8 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
   T.px = T.active ? 2 * (tid - T.py * G::NPX) : 0;
   T.t0 = T.py * E + T.px;
 
-  // z column: planes -4..-1 are zero, planes 0..3 read directly; plane 4 arrives with plane 0's slot
+  // z column q[k] = plane k - 4: planes -4..-1 are zero, planes 0..3 read directly; plane 4 arrives with
+  // plane 0's ring slot
   float4 q[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -476,20 +489,8 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
   __syncthreads();
 
   bool ok = true;
-#define DC_CHEB_PLANE(ZI)                                                                                  \
-  if (ok && z0 + ZI < E) ok = cheb_plane<E, PREV, PROJ, ZI>(a, m, T, q, z0 + ZI, A, yout);
-  for (int z0 = 0; z0 < E && ok; z0 += 9) {
-    DC_CHEB_PLANE(0)
-    DC_CHEB_PLANE(1)
-    DC_CHEB_PLANE(2)
-    DC_CHEB_PLANE(3)
-    DC_CHEB_PLANE(4)
-    DC_CHEB_PLANE(5)
-    DC_CHEB_PLANE(6)
-    DC_CHEB_PLANE(7)
-    DC_CHEB_PLANE(8)
-  }
-#undef DC_CHEB_PLANE
+#pragma unroll 1
+  for (int z = 0; z < E && ok; ++z) ok = cheb_plane<E, PREV, PROJ>(a, m, T, q, z, A, yout);
   __syncthreads();
   if (*m.abort) {
     // a bounded wait ran out: let the copies still in flight land (bounded) before the CTA's shared
@@ -507,19 +508,22 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
       const float4 *rc = m.rec + (zp % 3) * a.maxent;
       const float4 *o4 = reinterpret_cast<const float4 *>(m.pout + ps * G::PLANE);
       const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2);
-      for (int t = threadIdx.x; t < n; t += G::NT) {
-        const int kb = m.sent[e0 + t].x;
+      for (int t = threadIdx.x; t < kPSplit * n; t += G::NT) {
+        const int e = t / kPSplit, part = t - e * kPSplit;
+        const int kb = m.sent[e0 + e].x;
         const int k = kb & 0xffff, y = kb >> 16;
         const int2 bx = m.box[k];
+        const int len = bx.y - bx.x;
+        const int xa = bx.x + (part * len) / kPSplit, xb = bx.x + ((part + 1) * len) / kPSplit;
         float2 s0 = f2(0.f, 0.f), s1 = f2(0.f, 0.f);
-        for (int x2 = bx.x; x2 < bx.y; ++x2) {
+        for (int x2 = xa; x2 < xb; ++x2) {
           const float4 o = o4[y * G::NPX + x2];
           const float4 g = g4[k * G::NPX + x2];
           s0 = fma2(lo2(o), lo2(g), s0);
           s1 = fma2(hi2(o), hi2(g), s1);
         }
-        const float w = rc[t].w;
-        float2 &pa = m.pacc[y * A + k];
+        const float w = rc[e].w;
+        float2 &pa = m.pacc[(part * E + y) * A + k];
         pa = fma2(f2(w, w), add2(s0, s1), pa);
       }
     }
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
     for (int t = threadIdx.x; t < nvalid * A; t += G::NT) {
       const int o = t / A, k = t - o * A;
       float s = 0.f;
-      for (int y = 0; y < E; ++y) {
+      for (int y = 0; y < kPSplit * E; ++y) {
         const float2 v = m.pacc[y * A + k];
         s += o == 0 ? v.x : v.y;
       }
