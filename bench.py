@@ -131,18 +131,24 @@ def measured_peaks():
         return dict(hbm_gbs=6400.0, bf16_tflops=1800.0, bf16_tflops_sustained=1400.0), "fallback"
 
 
-def kernel_traffic(kernel_file):
-    """DRAM traffic per launch of the dominant kernel from a committed ncu summary, if it is current."""
+def kernel_traffic(kernel_file, point_orbitals, extent):
+    """DRAM traffic per launch of the dominant kernel from a committed ncu capture, scaled to this
+    workload's point-orbitals when its fragments have the captured extent; None (with the reason) when
+    the kernel source changed since the capture or the fragment shape differs."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
-            rec = json.load(fh)
+            rec = json.load(fh)[kernel_file]
         src = open(os.path.join(ROOT, "paper_2606_21125_b300", "csrc", kernel_file), "rb").read()
-        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("sha256") != hashlib.sha256(src).hexdigest():
             return None, "kernel changed since the ncu capture"
-        return rec["bytes_per_launch"], rec.get("note", "")
-    except (OSError, KeyError, ValueError):
+        if int(rec["fragment_extent"]) != int(extent):
+            return None, f"captured on {rec['fragment_extent']}^3 fragments, not {extent}^3"
+        scale = point_orbitals / float(rec["point_orbitals_per_launch"])
+        return rec["bytes_per_launch"] * scale, (f"ncu DRAM bytes of one launch on {rec['workload']} "
+                                                 f"({rec['profile']}), scaled x{scale:g} by point-orbitals")
+    except (OSError, KeyError, ValueError, TypeError):
         return None, "no ncu capture"
 
 
@@ -472,7 +478,10 @@ def run_ours(args):
     stencil_name += f", {tun['threads']} threads x {tun['pairs']} point pairs"
     h = prof["hpsi"]
     achieved = h["bytes"] / (h["ms"] * 1e-3) / 1e9 if h["ms"] > 0 else 0.0
-    traffic, traffic_note = kernel_traffic("k_hamiltonian.cu")
+    fr = solver.maps()["frag"]
+    extent = int(fr[0, 3]) if (fr[:, 3:6] == fr[0, 3]).all() else -1
+    traffic, traffic_note = kernel_traffic("k_cheb.cu" if tun["kind"] == 4 else "k_hamiltonian.cu",
+                                           float(solver.layout.psi_elems), extent)
     per_launch_bytes = h["bytes"] / max(1, h["launches"])
     launches = sum(v["launches"] for v in prof.values())
 
@@ -524,6 +533,8 @@ STENCIL_KINDS = {
     1: "k_hpair (orbital-pair FP32 stencil + local + nonlocal H-apply, fused Chebyshev step)",
     2: "k_hpair (orbital-pair FP32 stencil, fused Chebyshev step), register-capped",
     3: "k_hpair (orbital-pair FP32 stencil, fused Chebyshev step), every projector record of a fragment staged once",
+    4: "k_cheb (orbital-pair FP32 stencil compiled for one cubic fragment extent, planes streamed through a "
+       "shared-memory ring by bulk async copies, fused Chebyshev step)",
 }
 
 
