@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux};
+                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux, c->d_frag_order};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -224,6 +224,20 @@ StageModel energy_model(const dc_ctx *c, bool spectrum_difference) {
     nk += 3;
   }
   return {b, nk};
+}
+
+// Longest-first order of a work list whose items name their fragment in .x (stable, so a cell whose
+// fragments all cost the same keeps its order): the block scheduler hands out CTAs roughly in index
+// order, so the costliest items of uneven cells (fragments with more orbitals or points) start first
+// and the short ones fill in at the end instead of one long item finishing alone.
+void longest_first(const dc_ctx *c, std::vector<int2> &items, int power) {
+  auto cost = [&](int f) {
+    const FragDesc &D = c->h_desc[f];
+    double w = (double)D.E[0] * D.E[1] * D.E[2];
+    for (int k = 0; k < power; ++k) w *= D.norb;
+    return w;
+  };
+  std::stable_sort(items.begin(), items.end(), [&](const int2 &a, const int2 &b) { return cost(a.x) > cost(b.x); });
 }
 
 double core_elems(const dc_ctx *c) {
@@ -547,6 +561,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
     std::vector<int2> it2;
     for (int f = c->f_lo; f < c->f_hi; ++f)
       for (int i = 0; i < c->h_desc[f].norb; i += 2) it2.push_back(make_int2(f, i));
+    longest_first(c, it2, 0);  // one orbital pair of a fragment: cost ~ its points
     c->n_items2 = (int)it2.size();
     DC_TRY(upload(&c->d_items2, it2));
   }
@@ -652,6 +667,9 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
       const int nr2 = (int)((Pf + 255) / 256);
       for (int ch = 0; ch < nr2; ++ch) ri2.push_back(make_int2(f, ch));
     }
+    longest_first(c, gi, 2);   // Gram item: points x n^2
+    longest_first(c, ri, 1);   // rotation items: points x n
+    longest_first(c, ri2, 1);
     c->gram_elems = off;
     c->n_gram_items = (int)gi.size();
     c->n_rot_items = (int)ri.size();
@@ -661,6 +679,15 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
     DC_TRY(upload(&c->d_rot2_items, ri2));
     DC_TRY(upload(&c->d_gram_off, goff));
     DC_TRY(upload(&c->d_gram_nchunk, gn));
+    {
+      // the subspace solve (one CTA per fragment, ~n^3 FP64 work) runs its fragments longest first
+      std::vector<int2> fo;
+      for (int f = c->f_lo; f < c->f_hi; ++f) fo.push_back(make_int2(f, 0));
+      longest_first(c, fo, 3);
+      std::vector<int> order(fo.size());
+      for (size_t k = 0; k < fo.size(); ++k) order[k] = fo[k].x;
+      DC_TRY(upload(&c->d_frag_order, order));
+    }
     DC_TRY(dmalloc(&c->d_gram, (size_t)off));
   }
   // global grid arrays

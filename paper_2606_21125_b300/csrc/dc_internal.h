@@ -208,6 +208,7 @@ struct dc_ctx {
   long long st_lo = 0, st_hi = 0;
   // scratch of the caller-block forms of dc_subspace/dc_density (so the context's own state is kept)
   double *d_q_x = nullptr, *d_occ_x = nullptr, *d_aux = nullptr;
+  int *d_frag_order = nullptr;  // the shard's fragments, longest (most orbitals) first
 };
 
 // Host-built projector tables, uploaded by dc_init.

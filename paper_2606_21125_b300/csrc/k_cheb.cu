@@ -57,6 +57,8 @@ struct ChebArgs {
   int step;
   int cheb;               // 0: out = H y; 1: out = alpha (H - shift) y + beta y_prev
   int maxent;             // max entries of one plane
+  int amax, nentmax;      // max projector slots and row-list entries of one fragment (shared-memory carve)
+  int n_items;            // work items (the CTAs are persistent: CTA b takes a contiguous block of items)
   float dV;
   float k1, k2, k3, k4, kc;  // -1/2 c_n / h^2 (n = 1..4) and the centre term -2 (k3 + k4) * 3 axes
 };
@@ -195,14 +197,15 @@ struct ChebT {
   int t0;          // py E + px
 };
 
-// Issue the bulk copies of iteration z (y_in(z + 4), y_prev(z), V(z)) into ring slot z % RING.
+// Issue the bulk copies of plane z of the current item (y_in(z + 4), y_prev(z), V(z)) into ring slot
+// gz % RING, gz = the CTA's running plane count (slots and their barrier phases continue from item to item).
 template <int E, bool PREV>
-__device__ __forceinline__ void ring_issue(const ChebSmem<E> &m, int z) {
+__device__ __forceinline__ void ring_issue(const ChebSmem<E> &m, int z, int gz) {
   const typename ChebSmem<E>::Hdr &F = *m.hdr;
   using G = Geo<E>;
   constexpr uint32_t PB = G::PLANE * sizeof(float);
   constexpr long long P = (long long)G::PLANE * E;
-  const int s = z % G::RING;
+  const int s = gz % G::RING;
   float *slot = m.ring + (size_t)s * ring_sub<PREV>() * G::PLANE;
   uint64_t *bar = m.full + s;
   const bool has_y = z + 4 < E;
@@ -233,7 +236,7 @@ __device__ __forceinline__ void ring_issue(const ChebSmem<E> &m, int z) {
 // instruction footprint stalled the warps on instruction fetch.  Returns false when the CTA aborts.
 template <int E, bool PREV, bool PROJ>
 __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> &m, const ChebT &T, float4 (&q)[9],
-                                           int z, int A, float *yout) {
+                                           int z, int gbase, int A, float *yout) {
   using G = Geo<E>;
   const int slot = z & 1;
   float2 *P0 = m.pin + slot * G::PPLANE;
@@ -254,7 +257,7 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   __syncthreads();
   if (*m.abort) return false;
   // refill the slot that plane z - 1 has finished with, for plane z - 1 + RING
-  if (threadIdx.x == 0 && z >= 1 && z - 1 + G::RING < E) ring_issue<E, PREV>(m, z - 1 + G::RING);
+  if (threadIdx.x == 0 && z >= 1 && z - 1 + G::RING < E) ring_issue<E, PREV>(m, z - 1 + G::RING, gbase + z - 1 + G::RING);
   // projections of the previous output plane
   if (PROJ && z > 0) {
     const int zp = z - 1, ps = zp & 1;
@@ -285,12 +288,13 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   }
   if (!T.active) return true;
   // this plane's ring slot: y_in(z + 4) completes the column; y_prev(z) and V(z)
-  if (!mbar_wait(m.full + z % G::RING, (uint32_t)((z / G::RING) & 1))) {
+  const int gz = gbase + z;
+  if (!mbar_wait(m.full + gz % G::RING, (uint32_t)((gz / G::RING) & 1))) {
     atomicOr(a.flags, DC_FLAG_TIMEOUT);
     *m.abort = 1;
     return true;
   }
-  const float *rs = m.ring + (size_t)(z % G::RING) * ring_sub<PREV>() * G::PLANE + T.t0;
+  const float *rs = m.ring + (size_t)(gz % G::RING) * ring_sub<PREV>() * G::PLANE + T.t0;
   const int nvalid = m.hdr->nvalid;
   {
     float4 nxt = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -406,65 +410,18 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   return true;
 }
 
+// Persistent CTAs: CTA b runs the contiguous block of work items [b n / G, (b + 1) n / G) (all items cost
+// the same: one orbital pair of an E^3 fragment).  Consecutive items are mostly the same fragment, whose
+// tables (x factors, supports, row lists) stay in shared memory; only the pair's projections are read
+// again.  The ring's slots and barrier phases run on across items.
 template <int E, bool PREV, bool PROJ>
 __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_constant__ ChebArgs a) {
   using G = Geo<E>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 fi = a.items[blockIdx.x];
-  const int f = fi.x, i0 = fi.y;
-  const FragDesc &D = a.desc[f];
-  const int A = D.natom;
-  const int r0 = a.row_beg[D.row_off];
-  const int nent = a.row_beg[D.row_off + G::PLANE] - r0;
-  const ChebSmem<E> m = cheb_carve<E, PREV>(smem_raw, A, a.maxent, nent);
-  const int tabw = tab_width(D);
+  const ChebSmem<E> m = cheb_carve<E, PREV>(smem_raw, a.amax, a.maxent, a.nentmax);
   constexpr long long P = (long long)G::PLANE * E;
-  const long long base = D.psi_off + (long long)i0 * P;
-  const int nvalid = min(2, D.norb - i0);
-  float *yout = a.yout + base;
-
-  // the producer starts the first RING planes' copies before the table set-up
-  if (threadIdx.x == 0) {
-    float alpha = 1.f, beta = 0.f, shift = 0.f;
-    if (a.cheb) {
-      const double *bd = a.bounds + (long long)f * a.bstride;
-      shift = float(bd[3]);
-      alpha = float(bd[4 + 2 * a.step]);
-      beta = float(bd[5 + 2 * a.step]);
-    }
-    typename ChebSmem<E>::Hdr &F = *m.hdr;
-    F.yin = a.yin + base;
-    F.yprev = PREV ? a.yprev + base : nullptr;
-    F.vf = a.vf + D.pt_off;
-    F.nvalid = nvalid;
-    F.ksh = f2(a.kc - shift, a.kc - shift);
-    F.al2 = f2(alpha, alpha);
-    F.be2 = f2(beta, beta);
-    for (int k = 0; k < G::RING; ++k) {
-      mbar_init(m.full + k, 1);
-      m.issued[k] = 0;
-    }
-    *m.abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    for (int z = 0; z < G::RING && z < E; ++z) ring_issue<E, PREV>(m, z);
-  }
-  // tables: x factors (splatted), supports, D C <p|y>, row starts, entries; zero halo and accumulators
-  for (int t = threadIdx.x; t < A * E; t += G::NT) {
-    const int k = t / E, x = t - k * E;
-    const float g = a.tab[D.tab_off + (long long)k * tabw + x];
-    m.gx2[t] = f2(g, g);
-  }
-  for (int k = threadIdx.x; k < A; k += G::NT) {
-    const ProjSlot S = a.slots[D.at_off + k];
-    m.box[k] = make_int2(S.lo[0] >> 1, min((S.hi[0] + 1) >> 1, G::NPX));
-    const float ds = float(a.Datom[S.atom] * S.coef);
-    const float *ci = a.cin + D.c_off + (long long)i0 * A + k;
-    m.sk2[k] = f2(ds * ci[0], nvalid > 1 ? ds * ci[A] : 0.f);
-  }
-  for (int t = threadIdx.x; t <= G::PLANE; t += G::NT) m.rb[t] = a.row_beg[D.row_off + t] - r0;
-  for (int t = threadIdx.x; t < nent; t += G::NT) m.sent[t] = a.row_ent[r0 + t];
-  for (int t = threadIdx.x; t < kPSplit * E * A; t += G::NT) m.pacc[t] = f2(0.f, 0.f);
-  for (int t = threadIdx.x; t < 2 * G::PPLANE; t += G::NT) m.pin[t] = f2(0.f, 0.f);
+  const int it0 = (int)(((long long)blockIdx.x * a.n_items) / gridDim.x);
+  const int it1 = (int)(((long long)(blockIdx.x + 1) * a.n_items) / gridDim.x);
 
   ChebT T;
   const int tid = threadIdx.x;
@@ -473,71 +430,139 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
   T.px = T.active ? 2 * (tid - T.py * G::NPX) : 0;
   T.t0 = T.py * E + T.px;
 
-  // z column q[k] = plane k - 4: planes -4..-1 are zero, planes 0..3 read directly; plane 4 arrives with
-  // plane 0's ring slot
-  float4 q[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (T.active && k >= 4 && k < 8 && k - 4 < E) {
-      const float *p = a.yin + base + (k - 4) * G::PLANE + T.t0;
-      const float2 u0 = *reinterpret_cast<const float2 *>(p);
-      const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(p + P) : f2(0.f, 0.f);
-      q[k] = make_float4(u0.x, u1.x, u0.y, u1.y);
+  if (tid == 0) {
+    for (int k = 0; k < G::RING; ++k) {
+      mbar_init(m.full + k, 1);
+      m.issued[k] = 0;
     }
+    *m.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
+  for (int t = tid; t < 2 * G::PPLANE; t += G::NT) m.pin[t] = f2(0.f, 0.f);  // the halo stays zero
 
-  bool ok = true;
-#pragma unroll 1
-  for (int z = 0; z < E && ok; ++z) ok = cheb_plane<E, PREV, PROJ>(a, m, T, q, z, A, yout);
-  __syncthreads();
-  if (*m.abort) {
-    // a bounded wait ran out: let the copies still in flight land (bounded) before the CTA's shared
-    // memory is released, then return without projections
-    if (threadIdx.x == 0)
-      for (int k = 0; k < G::RING; ++k)
-        if (m.issued[k] > 0) mbar_wait(m.full + k, (uint32_t)((m.issued[k] - 1) & 1));  // its last use
-    return;
-  }
-  if (PROJ) {
-    // the last plane's projection tasks
-    {
-      const int zp = E - 1, ps = zp & 1;
-      const int e0 = m.rb[zp * E], n = m.rb[E * E] - e0;
-      const float4 *rc = m.rec + (zp % 3) * a.maxent;
-      const float4 *o4 = reinterpret_cast<const float4 *>(m.pout + ps * G::PLANE);
-      const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2);
-      for (int t = threadIdx.x; t < kPSplit * n; t += G::NT) {
-        const int e = t / kPSplit, part = t - e * kPSplit;
-        const int kb = m.sent[e0 + e].x;
-        const int k = kb & 0xffff, y = kb >> 16;
-        const int2 bx = m.box[k];
-        const int len = bx.y - bx.x;
-        const int xa = bx.x + (part * len) / kPSplit, xb = bx.x + ((part + 1) * len) / kPSplit;
-        float2 s0 = f2(0.f, 0.f), s1 = f2(0.f, 0.f);
-        for (int x2 = xa; x2 < xb; ++x2) {
-          const float4 o = o4[y * G::NPX + x2];
-          const float4 g = g4[k * G::NPX + x2];
-          s0 = fma2(lo2(o), lo2(g), s0);
-          s1 = fma2(hi2(o), hi2(g), s1);
-        }
-        const float w = rc[e].w;
-        float2 &pa = m.pacc[(part * E + y) * A + k];
-        pa = fma2(f2(w, w), add2(s0, s1), pa);
+  int prev_f = -1;
+  int gbase = 0;  // running plane count of this CTA
+  for (int item = it0; item < it1; ++item) {
+    const int2 fi = a.items[item];
+    const int f = fi.x, i0 = fi.y;
+    const FragDesc &D = a.desc[f];
+    const int A = D.natom;
+    const long long base = D.psi_off + (long long)i0 * P;
+    const int nvalid = min(2, D.norb - i0);
+    float *yout = a.yout + base;
+    __syncthreads();  // the previous item no longer reads the header, tables or ring
+    if (tid == 0) {
+      float alpha = 1.f, beta = 0.f, shift = 0.f;
+      if (a.cheb) {
+        const double *bd = a.bounds + (long long)f * a.bstride;
+        shift = float(bd[3]);
+        alpha = float(bd[4 + 2 * a.step]);
+        beta = float(bd[5 + 2 * a.step]);
+      }
+      typename ChebSmem<E>::Hdr &F = *m.hdr;
+      F.yin = a.yin + base;
+      F.yprev = PREV ? a.yprev + base : nullptr;
+      F.vf = a.vf + D.pt_off;
+      F.nvalid = nvalid;
+      F.ksh = f2(a.kc - shift, a.kc - shift);
+      F.al2 = f2(alpha, alpha);
+      F.be2 = f2(beta, beta);
+      for (int z = 0; z < G::RING && z < E; ++z) ring_issue<E, PREV>(m, z, gbase + z);
+    }
+    if (f != prev_f) {
+      // the fragment's tables: x factors (splatted), supports, row starts and entries
+      const int tabw = tab_width(D);
+      const int r0 = a.row_beg[D.row_off];
+      const int nent = a.row_beg[D.row_off + G::PLANE] - r0;
+      for (int t = tid; t < A * E; t += G::NT) {
+        const int k = t / E, x = t - k * E;
+        const float g = a.tab[D.tab_off + (long long)k * tabw + x];
+        m.gx2[t] = f2(g, g);
+      }
+      for (int k = tid; k < A; k += G::NT) {
+        const ProjSlot S = a.slots[D.at_off + k];
+        m.box[k] = make_int2(S.lo[0] >> 1, min((S.hi[0] + 1) >> 1, G::NPX));
+      }
+      for (int t = tid; t <= G::PLANE; t += G::NT) m.rb[t] = a.row_beg[D.row_off + t] - r0;
+      for (int t = tid; t < nent; t += G::NT) m.sent[t] = a.row_ent[r0 + t];
+      prev_f = f;
+    }
+    // the pair's D C <p|y>, zeroed accumulators
+    for (int k = tid; k < A; k += G::NT) {
+      const ProjSlot S = a.slots[D.at_off + k];
+      const float ds = float(a.Datom[S.atom] * S.coef);
+      const float *ci = a.cin + D.c_off + (long long)i0 * A + k;
+      m.sk2[k] = f2(ds * ci[0], nvalid > 1 ? ds * ci[A] : 0.f);
+    }
+    for (int t = tid; t < kPSplit * E * A; t += G::NT) m.pacc[t] = f2(0.f, 0.f);
+
+    // z column q[k] = plane k - 4: planes -4..-1 are zero, planes 0..3 read directly; plane 4 arrives
+    // with plane 0's ring slot
+    float4 q[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      q[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (T.active && k >= 4 && k < 8 && k - 4 < E) {
+        const float *p = a.yin + base + (k - 4) * G::PLANE + T.t0;
+        const float2 u0 = *reinterpret_cast<const float2 *>(p);
+        const float2 u1 = nvalid > 1 ? *reinterpret_cast<const float2 *>(p + P) : f2(0.f, 0.f);
+        q[k] = make_float4(u0.x, u1.x, u0.y, u1.y);
       }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nvalid * A; t += G::NT) {
-      const int o = t / A, k = t - o * A;
-      float s = 0.f;
-      for (int y = 0; y < kPSplit * E; ++y) {
-        const float2 v = m.pacc[y * A + k];
-        s += o == 0 ? v.x : v.y;
+
+    bool ok = true;
+#pragma unroll 1
+    for (int z = 0; z < E && ok; ++z) ok = cheb_plane<E, PREV, PROJ>(a, m, T, q, z, gbase, A, yout);
+    __syncthreads();
+    if (*m.abort) break;
+    gbase += E;
+    if (PROJ) {
+      // the last plane's projection tasks
+      {
+        const int zp = E - 1, ps = zp & 1;
+        const int e0 = m.rb[zp * E], n = m.rb[E * E] - e0;
+        const float4 *rc = m.rec + (zp % 3) * a.maxent;
+        const float4 *o4 = reinterpret_cast<const float4 *>(m.pout + ps * G::PLANE);
+        const float4 *g4 = reinterpret_cast<const float4 *>(m.gx2);
+        for (int t = tid; t < kPSplit * n; t += G::NT) {
+          const int e = t / kPSplit, part = t - e * kPSplit;
+          const int kb = m.sent[e0 + e].x;
+          const int k = kb & 0xffff, y = kb >> 16;
+          const int2 bx = m.box[k];
+          const int len = bx.y - bx.x;
+          const int xa = bx.x + (part * len) / kPSplit, xb = bx.x + ((part + 1) * len) / kPSplit;
+          float2 s0 = f2(0.f, 0.f), s1 = f2(0.f, 0.f);
+          for (int x2 = xa; x2 < xb; ++x2) {
+            const float4 o = o4[y * G::NPX + x2];
+            const float4 g = g4[k * G::NPX + x2];
+            s0 = fma2(lo2(o), lo2(g), s0);
+            s1 = fma2(hi2(o), hi2(g), s1);
+          }
+          const float w = rc[e].w;
+          float2 &pa = m.pacc[(part * E + y) * A + k];
+          pa = fma2(f2(w, w), add2(s0, s1), pa);
+        }
       }
-      const ProjSlot S = a.slots[D.at_off + k];
-      a.cout[D.c_off + (long long)(i0 + o) * A + k] = float(S.coef * a.dV) * s;
+      __syncthreads();
+      for (int t = tid; t < nvalid * A; t += G::NT) {
+        const int o = t / A, k = t - o * A;
+        float s = 0.f;
+        for (int y = 0; y < kPSplit * E; ++y) {
+          const float2 v = m.pacc[y * A + k];
+          s += o == 0 ? v.x : v.y;
+        }
+        const ProjSlot S = a.slots[D.at_off + k];
+        a.cout[D.c_off + (long long)(i0 + o) * A + k] = float(S.coef * a.dV) * s;
+      }
     }
+  }
+  if (*m.abort) {
+    // a bounded wait ran out: let the copies still in flight land (bounded) before the CTA's shared
+    // memory is released, then return
+    if (tid == 0)
+      for (int k = 0; k < G::RING; ++k)
+        if (m.issued[k] > 0) mbar_wait(m.full + k, (uint32_t)((m.issued[k] - 1) & 1));  // its last use
   }
 }
 
@@ -550,9 +575,12 @@ bool cheb_fits(const dc_ctx *c) {
 template <int E, bool PREV, bool PROJ>
 int run_cheb(const dc_ctx *c, const ChebArgs &a, cudaStream_t s) {
   using G = Geo<E>;
-  const size_t sm = cheb_smem_bytes<E, PREV>(c->max_atoms, a.maxent, std::max(1, c->max_frag_ent));
+  const size_t sm = cheb_smem_bytes<E, PREV>(a.amax, a.maxent, a.nentmax);
   DC_CUDA(dc_set_smem((const void *)k_cheb<E, PREV, PROJ>, sm));
-  if (c->n_items2 > 0) k_cheb<E, PREV, PROJ><<<(unsigned)c->n_items2, G::NT, sm, s>>>(a);
+  int per_sm = 0;
+  DC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb<E, PREV, PROJ>, G::NT, sm));
+  const int grid = std::min(c->n_items2, std::max(1, per_sm) * c->sm_count);
+  if (grid > 0) k_cheb<E, PREV, PROJ><<<(unsigned)grid, G::NT, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -613,6 +641,9 @@ int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yp
   a.step = step;
   a.cheb = mode == HSTEP_CHEB ? 1 : 0;
   a.maxent = std::max(1, c->max_plane_ent);
+  a.amax = std::max(1, c->max_atoms);
+  a.nentmax = std::max(1, c->max_frag_ent);
+  a.n_items = c->n_items2;
   a.dV = (float)c->dV;
   const double fd[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
   const double h2 = c->h[0] * c->h[0];

@@ -287,9 +287,10 @@ __device__ __forceinline__ void tri_ij(int t, int np, int &i, int &j) {
 
 __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const long long *goff, const int *gnchunk,
                                                   const double *gram, double dV, double *eps, double *C64,
-                                                  float *C32, unsigned *flags, int fp64_sweeps, int f_lo) {
+                                                  float *C32, unsigned *flags, int fp64_sweeps,
+                                                  const int *order) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int f = f_lo + blockIdx.x;
+  const int f = order[blockIdx.x];
   const FragDesc D = desc[f];
   const int n = D.norb;
   const int np = n + (n & 1);  // even size for the round-robin pairing (index n is a dummy)
@@ -970,7 +971,7 @@ int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s) 
   const int nf = c->f_hi - c->f_lo;
   if (nf <= 0) return DC_OK;
   k_subspace<<<nf, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, eps, c->d_C64,
-                                 precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags, fp64_sweeps, c->f_lo);
+                                 precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags, fp64_sweeps, c->d_frag_order);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
