@@ -110,7 +110,14 @@ typedef struct {
  * the context solves only the contiguous fragment range of `rank` (dc_query: frag_lo, frag_hi), chosen
  * so that every rank's stencil work sum P_f n_f is about 1/nranks of the total; every rank still holds
  * the global grid, maps and potentials.  The sharded SCF step is dc_step_local / dc_step_density /
- * dc_step_finish with the caller's exchanges between them. */
+ * dc_step_finish with the caller's exchanges between them.
+ * xc_fragment (0 or 1) and xi (>= 0): Eq. 5's per-fragment terms.  0 (default): one global V_eff with the
+ * exchange of rho_in.  1 (needs DC_HXC_HARTREE_X and nranks <= 1): fragment f's potential on its point j
+ * (global point g) is V_loc(g) + V_H[rho_in](g) + v_x(rho_f(j)) + (rho_f(j) - rho_in(g))/xi (the last term
+ * only for xi > 0, the density-template potential), rho_f = sum_i 2 f_i |psi_i|^2 on every point of the
+ * fragment (Eq. 3 before the core projection) from the orbitals and occupations the previous step ended
+ * with (after dc_warmup or dc_set_state with psi and eps: of that state at its own Fermi level); the
+ * energy's double counting uses the potential of the fragment owning each core point. */
 typedef struct {
   int precision;
   int cheb_degree;
@@ -123,6 +130,8 @@ typedef struct {
   double kerker_q0;
   int rank;
   int nranks;
+  int xc_fragment;
+  double xi;
 } dc_params_t;
 
 /* Sizes of everything a caller allocates for the calls below. */

@@ -268,14 +268,19 @@ class FragmentProjectors:
 class FragmentHamiltonian:
     """H_f psi = -1/2 L8 psi + V_f psi + sum_a D_a p_a <p_a|psi>, <u|v> = dV sum u v (Eq. 5, model)."""
 
-    def __init__(self, frags, f, grid: Grid, V_global, proj: FragmentProjectors, bc, D=None):
+    def __init__(self, frags, f, grid: Grid, V_global, proj: FragmentProjectors, bc, D=None, V_frag=None):
+        """V_global: the global potential, restricted to the fragment; or V_frag: the fragment's own
+        potential on its points ([Ez][Ey][Ex], Eq. 5 with per-fragment terms)."""
         self.f = f
         self.shape = (int(frags.extent[f, 2]), int(frags.extent[f, 1]), int(frags.extent[f, 0]))
         self.h = grid.h
         self.dV = grid.dV
         self.bc = bc
-        idx = frags.idx_map(f)
-        self.V = V_global.reshape(-1)[idx].reshape(self.shape)
+        if V_frag is not None:
+            self.V = np.asarray(V_frag, dtype=np.float64).reshape(self.shape)
+        else:
+            idx = frags.idx_map(f)
+            self.V = V_global.reshape(-1)[idx].reshape(self.shape)
         self.P = proj.dense()
         self.D = proj.D.copy() if D is None else np.asarray(D, dtype=np.float64)
 

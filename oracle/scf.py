@@ -10,6 +10,24 @@ exchange-correlation potentials from rho_tot (Eq. 5) and mixes.  Readings:
   bounds; ``n_warmup`` CheFSI passes in the starting potential precede step 1;
 * each SCF step runs ``n_pass`` CheFSI passes per fragment, then the core
   weights, mu, rho_out, the energy and linear mixing.
+
+Per-fragment exchange-correlation and the density-template potential (Eq. 5:
+V_xc[rho_alpha] and V^alpha = (rho_alpha - rho_tot)/xi), switched on with
+``xc_fragment`` (and ``xi`` > 0).  The paper leaves open which fragment
+density enters a step; readings:
+
+* rho_alpha is the whole-fragment density sum_i 2 f_i |phi_i^alpha|^2 (Eq. 3
+  before the core projection) of the orbitals and occupations that the
+  previous step ended with (after the warm-up: of the warm state and its own
+  Fermi level); it is not mixed;
+* the fragment potential on fragment point j (global point g) is
+  V_loc(g) + V_H[rho_in](g) + v_x(rho_alpha(j)) + (rho_alpha(j) - rho_in(g))/xi,
+  the last term only for xi > 0 (the paper's default is V^alpha = 0);
+* the energy removes the double counting with the potential each core point
+  felt, that of the fragment owning it:
+  E = sum 2 f eps q - int V_core rho_out + E_es[rho_out] + E_x[rho_out].
+  For one fragment spanning the cell this is the Kohn-Sham energy of the
+  output orbitals, as with the global potential.
 """
 from __future__ import annotations
 
@@ -47,6 +65,11 @@ class DCState:
             self.psi[f] = rng.orbital_block(int(cfg["seed"]), f, shp[0], int(np.prod(shp[1:]))).reshape(shp)
         self.eps = {}
         self.step_index = 0
+        self.xc_fragment = bool(cfg.get("xc_fragment", False))
+        self.xi = float(cfg.get("xi", 0.0))
+        if self.xc_fragment and self.hxc != "hartree_x":
+            raise ValueError("per-fragment exchange needs hxc = hartree_x")
+        self.rho_frag = {}
 
     # -- potentials -------------------------------------------------------------------------------
     def veff(self, rho_in):
@@ -55,8 +78,33 @@ class DCState:
             return self.vion.copy()
         return self.vion + model.hartree(self.grid, rho_in) + model.vx(rho_in)
 
-    def hamiltonian(self, f, V):
-        return model.FragmentHamiltonian(self.frags, f, self.grid, V, self.proj[f], self.bc)
+    def hamiltonian(self, f, V, Vf=None):
+        return model.FragmentHamiltonian(self.frags, f, self.grid, V, self.proj[f], self.bc, V_frag=Vf)
+
+    # -- per-fragment potential (xc_fragment) -------------------------------------------------------
+    def fragment_density(self, f, occ_f):
+        """rho_alpha on every point of fragment f: sum_i 2 f_i psi_i^2 (Eq. 3 without the core projection)."""
+        return np.einsum("i,i...->...", 2.0 * occ_f, self.psi[f] ** 2)
+
+    def fragment_potentials(self, rho_in):
+        """V_alpha on every fragment point: V_loc + V_H[rho_in] restricted to the fragment, plus v_x of the
+        fragment density and, for xi > 0, the density-template term (rho_alpha - rho_in)/xi (Eq. 5)."""
+        Vg = (self.vion + model.hartree(self.grid, rho_in)).reshape(-1)
+        rin = rho_in.reshape(-1)
+        out = {}
+        for f in self.active:
+            idx = self.frags.idx_map(f)
+            shp = self.psi[f].shape[1:]
+            rf = self.rho_frag[f]
+            Vf = Vg[idx].reshape(shp) + model.vx(rf)
+            if self.xi > 0.0:
+                Vf = Vf + (rf - rin[idx].reshape(shp)) / self.xi
+            out[f] = Vf
+        return out
+
+    def update_fragment_densities(self, occ):
+        for f in self.active:
+            self.rho_frag[f] = self.fragment_density(f, occ[f])
 
     # -- fragment solves --------------------------------------------------------------------------
     def initial_rr(self, V):
@@ -64,9 +112,9 @@ class DCState:
             eps, psi, _ = chefsi.rayleigh_ritz(self.hamiltonian(f, V), self.psi[f])
             self.eps[f], self.psi[f] = eps, psi
 
-    def solve(self, V, n_pass):
+    def solve(self, V, n_pass, Vfrag=None):
         for f in self.active:
-            H = self.hamiltonian(f, V)
+            H = self.hamiltonian(f, V, None if Vfrag is None else Vfrag[f])
             for _ in range(n_pass):
                 eps, psi, _ = chefsi.chefsi_pass(H, self.psi[f], self.m, self.eps[f])
                 self.eps[f], self.psi[f] = eps, psi
@@ -75,6 +123,9 @@ class DCState:
         V = self.veff(self.rho_in)
         self.initial_rr(V)
         self.solve(V, int(self.cfg["n_warmup"]))
+        if self.xc_fragment:
+            _, _, occ, _ = self.density_stage()
+            self.update_fragment_densities(occ)
 
     # -- density stage ----------------------------------------------------------------------------
     def density_stage(self):
@@ -92,13 +143,26 @@ class DCState:
 
     # -- one SCF step -----------------------------------------------------------------------------
     def scf_step(self):
-        V = self.veff(self.rho_in)
-        self.solve(V, int(self.cfg["n_pass"]))
+        Vfrag = None
+        if self.xc_fragment:
+            Vfrag = self.fragment_potentials(self.rho_in)
+            V = None
+        else:
+            V = self.veff(self.rho_in)
+        self.solve(V, int(self.cfg["n_pass"]), Vfrag)
         q, mu, occ, rho_out = self.density_stage()
         eps_all = np.concatenate([self.eps[f] for f in self.active])
         q_all = np.concatenate([q[f] for f in self.active])
         occ_all = np.concatenate([occ[f] for f in self.active])
         eband = energy.band_sum(eps_all, q_all, occ_all)
+        if self.xc_fragment:
+            # the input potential each core point felt: that of its owner fragment
+            Vcore = np.zeros(self.grid.npts)
+            for f in self.active:
+                cm = self.frags.core_mask(f)
+                Vcore[self.frags.idx_map(f)[cm.reshape(-1)]] = Vfrag[f][cm]
+            V = Vcore.reshape(self.grid.shape())
+            self.update_fragment_densities(occ)
         E = energy.total_energy(self.grid, self.hxc, eband, V, rho_out, self.rhoiG)
         S = fermi.entropy(eps_all, q_all, mu, self.kT)
         drho = energy.residual(self.grid, rho_out, self.rho_in, self.ne)

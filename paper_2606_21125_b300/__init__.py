@@ -63,7 +63,8 @@ class DCSolver:
         pa = _lib.dc_params_t(self.precision, int(cfg["cheb_degree"]), int(cfg["n_pass"]), int(cfg["n_warmup"]),
                               HXCS[cfg["hxc"]], float(cfg["kT"]), float(cfg["mix_alpha"]), int(cfg["seed"]),
                               float(cfg.get("kerker_q0", 0.0)), int(cfg.get("rank", 0)),
-                              int(cfg.get("nranks", 1)))
+                              int(cfg.get("nranks", 1)), int(bool(cfg.get("xc_fragment", False))),
+                              float(cfg.get("xi", 0.0)))
         ctx = C.c_void_p()
         check("dc_init", lib.dc_init(C.byref(g), C.byref(fr), C.byref(bu), C.byref(at), C.byref(pa), C.byref(ctx)))
         self.ctx = ctx

@@ -36,7 +36,8 @@ class dc_atoms_t(C.Structure):
 class dc_params_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("cheb_degree", C.c_int), ("n_pass", C.c_int), ("n_warmup", C.c_int),
                 ("hxc", C.c_int), ("kT", C.c_double), ("mix_alpha", C.c_double), ("seed", C.c_uint64),
-                ("kerker_q0", C.c_double), ("rank", C.c_int), ("nranks", C.c_int)]
+                ("kerker_q0", C.c_double), ("rank", C.c_int), ("nranks", C.c_int),
+                ("xc_fragment", C.c_int), ("xi", C.c_double)]
 
 
 class dc_layout_t(C.Structure):

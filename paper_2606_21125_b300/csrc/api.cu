@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux, c->d_frag_order};
+                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux, c->d_frag_order, c->d_rhof, c->d_vcore};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -350,6 +350,17 @@ int density_stage(dc_ctx *c, double *rho, cudaStream_t s) {
   return DC_OK;
 }
 
+// Per-fragment exchange: the fragment densities of the current state and occupations (Eq. 3 before the
+// core projection), the input of the next step's fragment potentials.
+int fragment_density(dc_ctx *c, cudaStream_t s) {
+  if (!c->params.xc_fragment) return DC_OK;
+  const double es = c->params.precision == DC_FP64 ? 8.0 : 4.0;
+  StageScope sc(c, DC_STAGE_DENSITY, s, es * (double)c->layout.psi_elems + 8.0 * c->layout.frag_points, 1);
+  if (c->params.precision == DC_FP64)
+    return dck::launch_frag_density<double>(c, (const double *)c->blk[c->ib_psi], c->d_occ, c->d_rhof, s, true);
+  return dck::launch_frag_density<float>(c, (const float *)c->blk[c->ib_psi], c->d_occ, c->d_rhof, s, true);
+}
+
 inline cudaStream_t S(void *p) { return reinterpret_cast<cudaStream_t>(p); }
 
 // Autotune the stencil launch shape for element type T on block y (scratch block `out`).  With
@@ -398,14 +409,17 @@ int step_body(dc_ctx *c, double *rin, cudaStream_t s) {
     const StageModel pm = potential_model(c, keep_spectrum);
     StageScope sc(c, DC_STAGE_POTENTIAL, s, pm.bytes, pm.launches);
     // with the Hartree term the input density's spectrum is kept for the Kerker residual below
-    DC_TRY(dck::launch_potential(c, rin, s, keep_spectrum ? c->d_rhoinG : nullptr));
+    DC_TRY(dck::launch_potential(c, rin, s, keep_spectrum ? c->d_rhoinG : nullptr, true));
   }
   {
-    StageScope sc(c, DC_STAGE_GATHER, s, 24.0 * (double)c->layout.frag_points, 1);
-    DC_TRY(dck::launch_gather(c, s));
+    const bool fx = c->params.xc_fragment != 0;
+    StageScope sc(c, DC_STAGE_GATHER, s, (fx ? 40.0 : 24.0) * (double)c->layout.frag_points + (fx ? 28.0 : 0.0) * c->npts,
+                  fx ? 2 : 1);
+    DC_TRY(dck::launch_gather(c, s, fx ? rin : nullptr));
   }
   DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
   DC_TRY(density_stage(c, c->d_rho_out, s));
+  DC_TRY(fragment_density(c, s));
   {
     const StageModel em = energy_model(c, keep_spectrum);
     StageScope sc(c, DC_STAGE_ENERGY, s, em.bytes, em.launches);
@@ -510,8 +524,13 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   const dc_params_t &P = c->params;
   if (P.precision < DC_FP64 || P.precision > DC_MIXED || P.cheb_degree < 1 || P.cheb_degree > 64 || P.n_pass < 1 ||
       P.n_warmup < 0 || !(P.kT > 0.0) || !(P.mix_alpha >= 0.0) || P.mix_alpha > 1.0 || !(P.kerker_q0 >= 0.0) ||
-      (P.hxc != DC_HXC_NONE && P.hxc != DC_HXC_HARTREE_X)) {
+      (P.hxc != DC_HXC_NONE && P.hxc != DC_HXC_HARTREE_X) || (P.xc_fragment != 0 && P.xc_fragment != 1) ||
+      !(P.xi >= 0.0)) {
     dc_set_error("dc_init: invalid parameters");
+    return DC_ERR_ARG;
+  }
+  if (P.xc_fragment && (P.hxc != DC_HXC_HARTREE_X || P.nranks > 1)) {
+    dc_set_error("dc_init: per-fragment exchange needs hxc = DC_HXC_HARTREE_X and every fragment (nranks <= 1)");
     return DC_ERR_ARG;
   }
   if (atoms->natom > 0 && (!atoms->pos || !atoms->species)) {
@@ -727,6 +746,10 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(dmalloc(&c->d_q_x, (size_t)Lo.nstates));
   DC_TRY(dmalloc(&c->d_occ_x, (size_t)Lo.nstates));
   DC_TRY(dmalloc(&c->d_aux, 4));
+  if (P.xc_fragment) {
+    DC_TRY(dmalloc(&c->d_rhof, (size_t)Lo.frag_points));
+    DC_TRY(dmalloc(&c->d_vcore, (size_t)c->npts));
+  }
   DC_TRY(dmalloc(&c->d_bounds, (size_t)c->nfrag * (4 + 2 * P.cheb_degree)));
   DC_CUDA(cudaMemset(c->d_bounds, 0, sizeof(double) * (size_t)c->nfrag * (4 + 2 * P.cheb_degree)));
   DC_TRY(dmalloc(&c->d_flags, 8));
@@ -963,6 +986,11 @@ int dc_warmup(dc_ctx *c, void *stream) {
     c->ib_psi = 0;
     if (c->hstep_shape[0] < 0) DC_TRY(tune<float>(c, (float *)c->blk[0], (float *)c->blk[1], s));
   }
+  if (c->params.xc_fragment) {
+    // the first step's fragment densities: the warm state with its own Fermi level
+    DC_TRY(density_stage(c, c->d_rho_out, s));
+    DC_TRY(fragment_density(c, s));
+  }
   DC_TRY(check_flags(c, s));
   c->warmed = true;
   c->steps_done = 0;
@@ -985,6 +1013,12 @@ int dc_set_state(dc_ctx *c, const void *d_psi, const double *d_eps, void *stream
                             cudaMemcpyDeviceToDevice, S(stream)));
   if (d_eps) DC_CUDA(cudaMemcpyAsync(c->d_eps, d_eps, 8 * (size_t)c->layout.nstates, cudaMemcpyDeviceToDevice, S(stream)));
   if (d_psi) c->proj_ok = 0;
+  if (c->params.xc_fragment && d_psi && d_eps) {
+    // the next step's fragment densities: this state with its own Fermi level
+    DC_TRY(density_stage(c, c->d_rho_out, S(stream)));
+    DC_TRY(fragment_density(c, S(stream)));
+    DC_TRY(check_flags(c, S(stream)));
+  }
   c->warmed = true;
   return DC_OK;
 }
@@ -1172,8 +1206,8 @@ int dc_step_local(dc_ctx *c, const double *d_rho_in, double *d_eps, double *d_q,
   }
   cudaStream_t s = S(stream);
   const bool keep_spectrum = c->params.hxc == DC_HXC_HARTREE_X;
-  DC_TRY(dck::launch_potential(c, d_rho_in, s, keep_spectrum ? c->d_rhoinG : nullptr));
-  DC_TRY(dck::launch_gather(c, s));
+  DC_TRY(dck::launch_potential(c, d_rho_in, s, keep_spectrum ? c->d_rhoinG : nullptr, true));
+  DC_TRY(dck::launch_gather(c, s, c->params.xc_fragment ? d_rho_in : nullptr));
   DC_TRY(pass_ctx(c, true, c->params.n_pass, s));
   if (c->params.precision == DC_FP64)
     DC_TRY(dck::launch_core_weights<double>(c, (const double *)c->blk[c->ib_psi], c->d_q, s));
@@ -1203,6 +1237,7 @@ int dc_step_density(dc_ctx *c, const double *d_eps, const double *d_q, double *d
     DC_TRY(dck::launch_density<double>(c, (const double *)c->blk[c->ib_psi], c->d_occ, d_rho_part, s));
   else
     DC_TRY(dck::launch_density<float>(c, (const float *)c->blk[c->ib_psi], c->d_occ, d_rho_part, s));
+  DC_TRY(fragment_density(c, s));
   if (d_mu) DC_CUDA(cudaMemcpyAsync(d_mu, c->d_scalar, 8, cudaMemcpyDeviceToDevice, s));
   return check_flags(c, s);
 }

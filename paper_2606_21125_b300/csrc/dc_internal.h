@@ -209,6 +209,9 @@ struct dc_ctx {
   // scratch of the caller-block forms of dc_subspace/dc_density (so the context's own state is kept)
   double *d_q_x = nullptr, *d_occ_x = nullptr, *d_aux = nullptr;
   int *d_frag_order = nullptr;  // the shard's fragments, longest (most orbitals) first
+  // per-fragment exchange (params.xc_fragment): sum_i f_i psi_i^2 on every fragment point (the fragment
+  // density is twice this) and the potential each core point felt
+  double *d_rhof = nullptr, *d_vcore = nullptr;
 };
 
 // Host-built projector tables, uploaded by dc_init.
@@ -254,8 +257,13 @@ cudaError_t dc_set_smem(const void *func, size_t bytes);
 namespace dck {
 // global stages
 int launch_vion(dc_ctx *c, cudaStream_t s);
-int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG = nullptr);
-int launch_gather(dc_ctx *c, cudaStream_t s);
+// with_fragment_xc: a context with per-fragment exchange leaves v_x to the gather (the SCF step); the
+// warm-up and dc_potential keep the global exchange
+int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG = nullptr,
+                     bool with_fragment_xc = false);
+// rho_in != nullptr: per-fragment exchange and density-template terms from d_rhof (and rho_in), and the
+// core-point potential d_vcore for the energy
+int launch_gather(dc_ctx *c, cudaStream_t s, const double *rho_in = nullptr);
 int launch_gather_plain(dc_ctx *c, const double *V, double *vf64, float *vf32, cudaStream_t s);
 int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s);
 int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s, const double2 *rho_in_G = nullptr);
@@ -306,7 +314,8 @@ int launch_density(dc_ctx *c, const T *psi, const double *occ, double *rho, cuda
 
 // adjoint
 template <typename T>
-int launch_frag_density(dc_ctx *c, const T *psi, const double *occ, double *fd, cudaStream_t s);
+int launch_frag_density(dc_ctx *c, const T *psi, const double *occ, double *fd, cudaStream_t s,
+                        bool shard_only = false);
 int launch_gather_dV(dc_ctx *c, const double *fd, double *dV, cudaStream_t s);
 int launch_dD(dc_ctx *c, const double *cproj64, const float *cproj32, const double *occ, double *dD, cudaStream_t s);
 int launch_sum(const double *x, long long n, double *out, double *partials, int npart, cudaStream_t s);

@@ -12,9 +12,9 @@ namespace {
 
 template <typename T>
 __global__ void k_frag_density(const FragDesc *desc, int nfrag, const T *psi, const double *occ, double *fd,
-                               long long total) {
-  // one thread per fragment point; the fragment of a point is found by bisection on pt_off
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+                               long long t0, long long total) {
+  // one thread per fragment point in [t0, total); the fragment of a point is found by bisection on pt_off
+  const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   int lo = 0, hi = nfrag - 1;
   while (lo < hi) {
@@ -81,9 +81,14 @@ __global__ void k_atom_sum(int natom, const int *beg, const int *slots, const do
 namespace dck {
 
 template <typename T>
-int launch_frag_density(dc_ctx *c, const T *psi, const double *occ, double *fd, cudaStream_t s) {
-  const long long total = c->layout.frag_points;
-  k_frag_density<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(c->d_desc, c->nfrag, psi, occ, fd, total);
+int launch_frag_density(dc_ctx *c, const T *psi, const double *occ, double *fd, cudaStream_t s, bool shard_only) {
+  long long t0 = 0, total = c->layout.frag_points;
+  if (shard_only) {
+    t0 = c->h_desc[c->f_lo].pt_off;
+    total = c->f_hi < c->nfrag ? c->h_desc[c->f_hi].pt_off : c->layout.frag_points;
+  }
+  if (total <= t0) return DC_OK;
+  k_frag_density<T><<<(unsigned)((total - t0 + 255) / 256), 256, 0, s>>>(c->d_desc, c->nfrag, psi, occ, fd, t0, total);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -106,7 +111,7 @@ int launch_dD(dc_ctx *c, const double *cproj64, const float *cproj32, const doub
   return DC_OK;
 }
 
-template int launch_frag_density<double>(dc_ctx *, const double *, const double *, double *, cudaStream_t);
-template int launch_frag_density<float>(dc_ctx *, const float *, const double *, double *, cudaStream_t);
+template int launch_frag_density<double>(dc_ctx *, const double *, const double *, double *, cudaStream_t, bool);
+template int launch_frag_density<float>(dc_ctx *, const float *, const double *, double *, cudaStream_t, bool);
 
 }  // namespace dck

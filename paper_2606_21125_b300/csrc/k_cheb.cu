@@ -75,6 +75,9 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 // planes spreads a plane's tasks over every warp, but the second accumulator plane took the shared
 // memory of the second CTA per SM (Si, 22^3 fragments): 269 -> 394 us per launch on the 64-atom cell.
 constexpr int kPSplit = 1;
+// Task t runs on thread t, so a plane's ~110 tasks fill the first warps.  Spreading them one lane per
+// warp per round (all warps then run the task loop) was slower: 270 -> 295 us per launch on the
+// 64-atom cell (more issue slots outweighed the shorter barrier waits).
 
 template <int E>
 struct Geo {

@@ -83,27 +83,40 @@ __global__ void k_scale(long long n, double *x, const double *num, double den_sc
   if (i < n) x[i] *= den_scale / num[0];
 }
 
-// V_eff = V_loc + V_H + v_x[rho]  (vh holds the unnormalised inverse transform, scaled by 1/N)
+// V_eff = V_loc + V_H + v_x[rho]  (vh holds the unnormalised inverse transform, scaled by 1/N); with
+// with_x = 0 the exchange is left to the per-fragment gather (Eq. 5, V_xc[rho_alpha])
 __global__ void k_veff(long long n, const double *vion, const double2 *vh, double inv_n, const double *rho, int hxc,
-                       double *veff) {
+                       int with_x, double *veff) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v = vion[i];
-  if (hxc == DC_HXC_HARTREE_X) v += vh[i].x * inv_n - cbrt(3.0 * fmax(rho[i], 0.0) / M_PI);
+  if (hxc == DC_HXC_HARTREE_X) {
+    v += vh[i].x * inv_n;
+    if (with_x) v -= cbrt(3.0 * fmax(rho[i], 0.0) / M_PI);
+  }
   veff[i] = v;
 }
 
 // Per-fragment potential gather and rigorous spectral upper bound of H_f:
 //   b_up = max symbol of -1/2 L8 + max_j V_f(j) + sum_k max(D_k, 0) <p_k|p_k>.
+// With rhof != nullptr (per-fragment exchange, Eq. 5): V_f(j) = V(g) + v_x(rho_alpha(j)) [+ (rho_alpha(j) -
+// rho_in(g)) / xi for xi > 0], rho_alpha = 2 rhof (rhof holds sum_i f_i psi_i^2 over every fragment point).
 __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const double *veff, double *vf64, float *vf32,
-                         const double *nl_bound, double kin_max, double *bounds, int bstride) {
+                         const double *nl_bound, double kin_max, double *bounds, int bstride, const double *rhof,
+                         const double *rho_in, double inv_xi) {
   __shared__ double red[8];
   const int f = blockIdx.x;
   const FragDesc D = desc[f];
   const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
   double vmax = -1e300;
   for (long long j = threadIdx.x; j < P; j += blockDim.x) {
-    const double v = veff[idx_map[D.pt_off + j]];
+    const int32_t g = idx_map[D.pt_off + j];
+    double v = veff[g];
+    if (rhof) {
+      const double ra = 2.0 * rhof[D.pt_off + j];
+      v -= cbrt(3.0 * fmax(ra, 0.0) / M_PI);
+      if (inv_xi > 0.0) v += (ra - rho_in[g]) * inv_xi;
+    }
     vf64[D.pt_off + j] = v;
     if (vf32) vf32[D.pt_off + j] = (float)v;
     vmax = fmax(vmax, v);
@@ -116,6 +129,13 @@ __global__ void k_gather(const FragDesc *desc, const int32_t *idx_map, const dou
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
     bounds[(long long)f * bstride + 1] = kin_max + m + nl_bound[f];
   }
+}
+
+__global__ void k_vcore(long long npts, const FragDesc *desc, const int32_t *owner, const int32_t *core_local,
+                        const double *vf64, double *vcore) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= npts) return;
+  vcore[g] = vf64[desc[owner[g]].pt_off + core_local[g]];
 }
 
 __global__ void k_gather_plain(long long total, const int32_t *idx_map, const double *V, double *vf64, float *vf32) {
@@ -316,7 +336,7 @@ int launch_vion(dc_ctx *c, cudaStream_t s) {
   return DC_OK;
 }
 
-int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG) {
+int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG, bool with_fragment_xc) {
   const long long N = c->npts;
   const int *n = c->grid.n;
   const double *L = c->grid.L;
@@ -328,12 +348,13 @@ int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save
     k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, c->d_ig2, c->d_cplx, 4.0 * M_PI, c->d_cplx);
     DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   }
-  k_veff<<<nblk(N), 256, 0, s>>>(N, c->d_vion, c->d_cplx, 1.0 / (double)N, rho, c->params.hxc, c->d_veff);
+  const int with_x = c->params.xc_fragment && with_fragment_xc ? 0 : 1;
+  k_veff<<<nblk(N), 256, 0, s>>>(N, c->d_vion, c->d_cplx, 1.0 / (double)N, rho, c->params.hxc, with_x, c->d_veff);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
 
-int launch_gather(dc_ctx *c, cudaStream_t s) {
+int launch_gather(dc_ctx *c, cudaStream_t s, const double *rho_in) {
   const double fd[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
   const double sym = fd[0] + 2.0 * (-fd[1] + fd[2] - fd[3] + fd[4]);
   double kin = 0.0;
@@ -341,8 +362,14 @@ int launch_gather(dc_ctx *c, cudaStream_t s) {
   const int bstride = 4 + 2 * c->params.cheb_degree;
   const int nf = c->f_hi - c->f_lo;  // the context's fragment shard (all fragments on one rank)
   if (nf <= 0) return DC_OK;
+  const bool frag_xc = rho_in != nullptr;
   k_gather<<<nf, 256, 0, s>>>(c->d_desc + c->f_lo, c->d_idx_map, c->d_veff, c->d_vf64, c->d_vf32,
-                              c->d_nl_bound + c->f_lo, kin, c->d_bounds + (long long)c->f_lo * bstride, bstride);
+                              c->d_nl_bound + c->f_lo, kin, c->d_bounds + (long long)c->f_lo * bstride, bstride,
+                              frag_xc ? c->d_rhof : nullptr, rho_in, c->params.xi > 0.0 ? 1.0 / c->params.xi : 0.0);
+  if (frag_xc) {
+    // the potential each core point feels (its owner fragment's), for the energy's double counting
+    k_vcore<<<nblk(c->npts), 256, 0, s>>>(c->npts, c->d_desc, c->d_owner, c->d_core_local, c->d_vf64, c->d_vcore);
+  }
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -362,7 +389,8 @@ int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s) {
   const long long ns = c->layout.nstates;
   DC_TRY(reduce(FnBand{c->d_occ, c->d_eps, c->d_q}, ns, 1.0, sc + 1, c->d_partials, s));
   DC_TRY(reduce(FnEntropy{c->d_occ, c->d_q}, ns, 1.0, sc + 7, c->d_partials, s));
-  DC_TRY(reduce(FnDot{c->d_veff, c->d_rho_out}, N, c->dV, sc + 2, c->d_partials, s));
+  DC_TRY(reduce(FnDot{c->params.xc_fragment ? c->d_vcore : c->d_veff, c->d_rho_out}, N, c->dV, sc + 2,
+                 c->d_partials, s));
   DC_TRY(reduce(FnEx{c->d_rho_out}, N, -0.75 * cbrt(3.0 / M_PI) * c->dV, sc + 4, c->d_partials, s));
   DC_TRY(reduce(FnAbsDiff{c->d_rho_out, rho_in}, N, c->dV / c->ne, sc + 5, c->d_partials, s));
   DC_TRY(reduce(FnSum{c->d_rho_out}, N, c->dV, sc + 6, c->d_partials, s));

@@ -66,7 +66,8 @@ def _structs(n=(10, 10, 10), F=(2, 2, 2), b=(2, 2, 2), prec=0, kT=0.01, cheb=8):
     return g, fr, bu, at, pa, keep
 
 
-@pytest.mark.parametrize("bad", ["null", "kT", "precision", "fragments", "cheb"])
+@pytest.mark.parametrize("bad", ["null", "kT", "precision", "fragments", "cheb", "xc_fragment_no_hxc", "xi",
+                                 "xc_fragment_value", "rank", "nranks"])
 def test_invalid_configuration_is_rejected_before_device_work(lib, bad):
     """dc_init validates its arguments on the host and returns DC_ERR_ARG with a message."""
     kw = {}
@@ -79,6 +80,16 @@ def test_invalid_configuration_is_rejected_before_device_work(lib, bad):
     elif bad == "cheb":
         kw["cheb"] = 0
     g, fr, bu, at, pa, keep = _structs(**kw)
+    if bad == "xc_fragment_no_hxc":
+        pa.xc_fragment, pa.hxc = 1, 0
+    elif bad == "xi":
+        pa.xi = -1.0
+    elif bad == "xc_fragment_value":
+        pa.xc_fragment = 2
+    elif bad == "rank":
+        pa.rank, pa.nranks = 2, 2
+    elif bad == "nranks":
+        pa.nranks = 9  # more ranks than the 8 fragments
     ctx = C.c_void_p(123)
     if bad == "null":
         st = lib.dc_init(C.byref(g), None, C.byref(bu), C.byref(at), C.byref(pa), C.byref(ctx))

@@ -503,12 +503,18 @@ def test_electron_count_conserved():
 # Single fragment = conventional DFT
 # ---------------------------------------------------------------------------------------------
 
-def test_single_fragment_equals_conventional_dft():
-    """P5: F=1, b=0, periodic DC reduces to a dense-diagonalisation Kohn-Sham SCF (per-step energies)."""
+@pytest.mark.parametrize("xc_fragment,xi", [(False, 0.0), (True, 0.0), (True, 0.7)])
+def test_single_fragment_equals_conventional_dft(xc_fragment, xi):
+    """P5: F=1, b=0, periodic DC reduces to a dense-diagonalisation Kohn-Sham SCF (per-step energies).
+
+    With the per-fragment exchange-correlation and density-template potential (Eq. 5), the one fragment's
+    density is the previous step's output density, so the reference SCF takes v_x of the previous output
+    density (of the starting potential's eigenstates before step 1) and, for xi > 0, adds
+    (rho_prev_out - rho_in)/xi; its energy is still the direct Kohn-Sham energy of the output orbitals."""
     natom, nst = 2, 8
     cfg = workloads.small_config(n=(10, 10, 10), L=(6.0, 6.0, 6.0), num_fragment=(1, 1, 1), buffer=(0, 0, 0),
                                  nstate=nst, natom=natom, bc="periodic", cheb_degree=14, n_pass=25, n_warmup=40,
-                                 seed=11)
+                                 seed=11, xc_fragment=xc_fragment, xi=xi)
     st = scf.DCState(cfg)
     st.warmup()
     dc = [st.scf_step() for _ in range(3)]
@@ -530,18 +536,28 @@ def test_single_fragment_equals_conventional_dft():
     rhoiG = model.rho_ion_G(grid, cfg["pos"], cfg["species"], cfg["spec"])
     rho_in = model.initial_density(grid, cfg["pos"], cfg["species"], cfg["spec"])
     ne = float(np.sum(cfg["spec"]["Z"][cfg["species"]]))
-    for step in range(3):
-        V = vion + model.hartree(grid, rho_in) + model.vx(rho_in)
+
+    def solve(V):
         H = -0.5 * Lap + np.diag(V.reshape(-1)) + grid.dV * (P.T * D) @ P
         w, U = np.linalg.eigh(H)
         w, U = w[:nst], U[:, :nst] / math.sqrt(grid.dV)
         mu = brentq(lambda m: np.sum(2 * 0.5 * (1 - np.tanh(0.5 * (w - m) / cfg["kT"]))) - ne, -5, 5, xtol=1e-15)
         occ = 0.5 * (1 - np.tanh(0.5 * (w - mu) / cfg["kT"]))
-        rho_out = (U * U) @ (2 * occ)
+        return w, U, mu, occ, ((U * U) @ (2 * occ)).reshape(grid.shape())
+
+    rho_prev = solve(vion + model.hartree(grid, rho_in) + model.vx(rho_in))[4]  # the warm state's density
+    for step in range(3):
+        if xc_fragment:
+            V = vion + model.hartree(grid, rho_in) + model.vx(rho_prev)
+            if xi > 0.0:
+                V = V + (rho_prev - rho_in) / xi
+        else:
+            V = vion + model.hartree(grid, rho_in) + model.vx(rho_in)
+        w, U, mu, occ, rho_out = solve(V)
+        rho_prev = rho_out
         T = np.sum(2 * occ * np.einsum("pi,pq,qi->i", U, -0.5 * Lap, U)) * grid.dV
         c = grid.dV * P @ U
         Enl = np.sum(2 * occ[None, :] * D[:, None] * c * c)
-        rho_out = rho_out.reshape(grid.shape())
         Etot = T + Enl + model.es_energy(grid, rho_out, rhoiG) + model.ex_energy(grid, rho_out)
         assert abs(dc[step]["E"] - Etot) / natom < 1e-10, (step, dc[step]["E"], Etot)
         assert abs(dc[step]["mu"] - mu) < 1e-9
