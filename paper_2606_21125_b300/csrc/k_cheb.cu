@@ -88,6 +88,8 @@ struct Geo {
   static constexpr int HROWS = E + 8;
   static constexpr int PPLANE = PITCH * HROWS;       // one haloed plane (float2)
   static constexpr int PLANE = E * E;
+  // Two 256-thread CTAs per SM.  Three (80 registers, two ring slots, the row-list entries read from
+  // global memory to fit the shared memory) ran 311 us per launch on the 64-atom cell against 271.
   static constexpr int MINB = NT <= 256 ? 2 : 1;
   static constexpr int RING = 4;                     // plane slots in flight
 };
