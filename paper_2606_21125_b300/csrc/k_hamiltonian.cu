@@ -344,7 +344,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? (NO == 2 ? 2 : 3) : 1) k_hstep
       for (int o = 0; o < NO; ++o) {
         const T *co = c0 + o * pplane;
         const V cv = q[r][o][4];
-        V h1 = Op::splat(T(0)), h2 = Op::splat(T(0));
         T xv[10];
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
@@ -352,21 +351,40 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? (NO == 2 ? 2 : 3) : 1) k_hstep
           xv[2 * j] = v.x;
           xv[2 * j + 1] = v.y;
         }
+        if constexpr (std::is_same<T, double>::value) {
+          // FP64: direct form, sum_n k_n (y+n + y-n) per axis plus (V + k_0) y at the centre (k_0 summed over
+          // the axes): ~35 FP64 operations per point against ~60 for the difference form, whose rounding
+          // advantage matters only in FP32.  On this part FP64 runs at 1/64 of the FP32 rate, so the
+          // operation count is the kernel's cost.
+          V h = Op::mul(Op::add(vv, Op::splat(a.kx[0] + a.ky[0] + a.kz[0])), cv);
 #pragma unroll
-        for (int n = 1; n <= 4; ++n) {
-          const V pa = Op::mk(xv[4 + n], xv[5 + n]);
-          const V pb = Op::mk(xv[4 - n], xv[5 - n]);
-          h1 = Op::fma(Op::splat(a.kx[n]), Op::add(Op::sub(pa, cv), Op::sub(pb, cv)), h1);
-          const V up = ld2(co + n * pitch);
-          const V dn = ld2(co - n * pitch);
-          h2 = Op::fma(Op::splat(a.ky[n]), Op::add(Op::sub(up, cv), Op::sub(dn, cv)), h2);
+          for (int n = 1; n <= 4; ++n) {
+            const V sx = Op::add(Op::mk(xv[4 + n], xv[5 + n]), Op::mk(xv[4 - n], xv[5 - n]));
+            const V sy = Op::add(ld2(co + n * pitch), ld2(co - n * pitch));
+            const V sz = Op::add(q[r][o][4 + n], q[r][o][4 - n]);
+            h = Op::fma(Op::splat(a.kx[n]), sx, Op::fma(Op::splat(a.ky[n]), sy, Op::fma(Op::splat(a.kz[n]), sz, h)));
+          }
+          hxy[o] = h;
+        } else {
+          // FP32: difference form (each tap as (y+n - y) + (y-n - y)), which keeps the cancellation against
+          // the centre out of the rounding
+          V h1 = Op::splat(T(0)), h2 = Op::splat(T(0));
+#pragma unroll
+          for (int n = 1; n <= 4; ++n) {
+            const V pa = Op::mk(xv[4 + n], xv[5 + n]);
+            const V pb = Op::mk(xv[4 - n], xv[5 - n]);
+            h1 = Op::fma(Op::splat(a.kx[n]), Op::add(Op::sub(pa, cv), Op::sub(pb, cv)), h1);
+            const V up = ld2(co + n * pitch);
+            const V dn = ld2(co - n * pitch);
+            h2 = Op::fma(Op::splat(a.ky[n]), Op::add(Op::sub(up, cv), Op::sub(dn, cv)), h2);
+          }
+          V h3 = Op::mul(vv, cv);
+#pragma unroll
+          for (int n = 1; n <= 4; ++n)
+            h3 = Op::fma(Op::splat(a.kz[n]), Op::add(Op::sub(q[r][o][4 + n], cv), Op::sub(q[r][o][4 - n], cv)), h3);
+          hxy[o] = Op::add(h1, h2);
+          hz[o] = h3;
         }
-        V h3 = Op::mul(vv, cv);
-#pragma unroll
-        for (int n = 1; n <= 4; ++n)
-          h3 = Op::fma(Op::splat(a.kz[n]), Op::add(Op::sub(q[r][o][4 + n], cv), Op::sub(q[r][o][4 - n], cv)), h3);
-        hxy[o] = Op::add(h1, h2);
-        hz[o] = h3;
         hn[o] = Op::splat(T(0));
       }
       const int cnt = RN[y];
@@ -383,7 +401,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? (NO == 2 ? 2 : 3) : 1) k_hstep
       for (int o = 0; o < NO; ++o) {
         if (o >= nvalid) continue;
         const V cv = q[r][o][4];
-        const V hv = Op::add(Op::add(hxy[o], hz[o]), hn[o]);
+        V hv;
+        if constexpr (std::is_same<T, double>::value)
+          hv = Op::add(hxy[o], hn[o]);
+        else
+          hv = Op::add(Op::add(hxy[o], hz[o]), hn[o]);
         V out;
         if (a.mode == HSTEP_CHEB) {
           out = Op::mul(Op::splat(alpha), Op::fma(Op::splat(-shift), cv, hv));

@@ -76,6 +76,12 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
   lo += err;
 }
 
+// Gram partials S = Y^T Y and A = Y^T HY of one (fragment, point chunk) item.  Tiles of 4 x 4 elements,
+// one per thread.  When the fragment's tiles fit one per thread (n <= 48: T(T+1)/2 upper-triangle tiles
+// of S and T^2 tiles of A, T = ceil(n / 4)), only those are computed and S is mirrored (a_i a_j and
+// a_j a_i are the same products in the same order, so the mirror is exact); otherwise a fixed 16 x 16
+// grid of tile pairs covers n <= 64.  The FP32 form accumulates each 32-point chunk in FP32 and the
+// chunks with a compensated (two-sum) FP32 pair; the FP64 form in FP64.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *gitems, const long long *goff,
                                               int chunk, const T *Y, const T *HY, double *out) {
@@ -90,7 +96,34 @@ __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *
   const long long p1 = min(P, p0 + chunk);
   const T *Yf = Y + D.psi_off;
   const T *Hf = HY ? HY + D.psi_off : nullptr;
-  const int ti = threadIdx.x >> 4, tj = threadIdx.x & 15;
+  // tile assignment
+  const int TT = (n + 3) >> 2;
+  const int nS = TT * (TT + 1) / 2;
+  const bool tiled = nS + TT * TT <= 256;
+  int ti, tj;
+  bool isA = false, act = true;
+  if (tiled) {
+    int t = threadIdx.x;
+    act = t < nS + TT * TT;
+    if (t < nS) {  // upper triangle, row by row: row ti holds tiles ti .. TT - 1
+      ti = 0;
+      while (t >= TT - ti) {
+        t -= TT - ti;
+        ++ti;
+      }
+      tj = ti + t;
+    } else if (act) {
+      t -= nS;
+      isA = true;
+      ti = t / TT;
+      tj = t - ti * TT;
+    } else {
+      ti = tj = 0;
+    }
+  } else {
+    ti = threadIdx.x >> 4;
+    tj = threadIdx.x & 15;
+  }
   for (int t = threadIdx.x; t < GKT * GPAD; t += 256) {
     (&sY[0][0])[t] = T(0);
     (&sH[0][0])[t] = T(0);
@@ -114,32 +147,48 @@ __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *
     T ps[16], pa[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) ps[e] = pa[e] = T(0);
+    if (tiled) {
+      if (act) {
+        const T(*sB)[GPAD] = isA ? sH : sY;
 #pragma unroll 4
-    for (int p = 0; p < GKT; ++p) {
-      const Vec4<T> a = ld4(&sY[p][4 * ti]);
-      const Vec4<T> b = ld4(&sY[p][4 * tj]);
-      const Vec4<T> h = ld4(&sH[p][4 * tj]);
+        for (int p = 0; p < GKT; ++p) {
+          const Vec4<T> a = ld4(&sY[p][4 * ti]);
+          const Vec4<T> b = ld4(&sB[p][4 * tj]);
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+          for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          ps[4 * r + cc] += a.v[r] * b.v[cc];
-          pa[4 * r + cc] += a.v[r] * h.v[cc];
+            for (int cc = 0; cc < 4; ++cc) ps[4 * r + cc] += a.v[r] * b.v[cc];
         }
+      }
+    } else {
+#pragma unroll 4
+      for (int p = 0; p < GKT; ++p) {
+        const Vec4<T> a = ld4(&sY[p][4 * ti]);
+        const Vec4<T> b = ld4(&sY[p][4 * tj]);
+        const Vec4<T> h = ld4(&sH[p][4 * tj]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            ps[4 * r + cc] += a.v[r] * b.v[cc];
+            pa[4 * r + cc] += a.v[r] * h.v[cc];
+          }
+      }
     }
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       if (sizeof(T) == 4) {
         two_sum_acc(shi[e], slo[e], (float)ps[e]);
-        two_sum_acc(ahi[e], alo[e], (float)pa[e]);
+        if (!tiled) two_sum_acc(ahi[e], alo[e], (float)pa[e]);
       } else {
         sd[e] += (double)ps[e];
-        ad[e] += (double)pa[e];
+        if (!tiled) ad[e] += (double)pa[e];
       }
     }
     __syncthreads();
   }
   double *o = out + goff[f] + (long long)ch * 2 * n * n;
+  if (!act) return;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -148,9 +197,18 @@ __global__ void __launch_bounds__(256) k_gram(const FragDesc *desc, const int2 *
       if (i < n && j < n) {
         const int e = 4 * r + cc;
         const double sv = sizeof(T) == 4 ? (double)shi[e] + (double)slo[e] : sd[e];
-        const double av = sizeof(T) == 4 ? (double)ahi[e] + (double)alo[e] : ad[e];
-        o[i * n + j] = sv;
-        o[n * n + i * n + j] = av;
+        if (tiled) {
+          if (isA) {
+            o[n * n + i * n + j] = sv;
+          } else {
+            o[i * n + j] = sv;
+            o[j * n + i] = sv;
+          }
+        } else {
+          const double av = sizeof(T) == 4 ? (double)ahi[e] + (double)alo[e] : ad[e];
+          o[i * n + j] = sv;
+          o[n * n + i * n + j] = av;
+        }
       }
     }
 }
