@@ -86,6 +86,7 @@ struct dc_ctx {
   int max_zlist;      // max over f of total per-plane list length
   int max_plane_ent;  // max over f and z of the row-list entries of one plane
   int max_frag_ent;   // max over f of the row-list entries of the whole fragment
+  bool core_pairs;    // every fragment's core rows start at an even x with an even length, E_x even
 
   // host copies of maps (for dc_get_maps and launch planning)
   std::vector<FragDesc> h_desc;

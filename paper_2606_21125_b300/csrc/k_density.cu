@@ -241,8 +241,9 @@ __device__ __forceinline__ void dw_add(float &hi, float &lo, float a) {
   lo += e;
 }
 
+// Scalar forms of the two kernels below, for cells whose core rows do not split into point pairs.
 // q_i = dV sum_core psi_i^2: CTA = (fragment, 8 orbitals), one warp per orbital.
-__global__ void __launch_bounds__(256) k_core_weights32(const FragDesc *desc, const float *psi, double dV,
+__global__ void __launch_bounds__(256) k_core_weights32s(const FragDesc *desc, const float *psi, double dV,
                                                         double *q) {
   const FragDesc D = desc[blockIdx.x];
   const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(256) k_core_weights32(const FragDesc *desc, co
 // point is owned by exactly one fragment, so every global point is written once.  The occupations
 // are carried as FP32 pairs (2 f = oh + ol) and every term is formed with exact products, so the
 // density integrates to sum 2 f q = N_e to ~1e-12 (an FP32-rounded 2 f would break that at 1e-8).
-__global__ void __launch_bounds__(256) k_density32(const FragDesc *desc, const float *psi, const double *occ, int Nx,
+__global__ void __launch_bounds__(256) k_density32s(const FragDesc *desc, const float *psi, const double *occ, int Nx,
                                                    int Ny, double *rho) {
   __shared__ float occh[DC_MAX_NORB], occl[DC_MAX_NORB];
   const FragDesc D = desc[blockIdx.x];
@@ -309,6 +310,112 @@ __global__ void __launch_bounds__(256) k_density32(const FragDesc *desc, const f
   }
 }
 
+// Core points are read as x-adjacent pairs (one 8-byte load) when every fragment's core rows start at an
+// even x and have an even length and its rows an even length (dc_ctx::core_pairs).  A core row is
+// c_x of the fragment's E_x points, so the sectors a warp touches carry buffer points too; the loads
+// are unrolled so that several are in flight per thread.
+
+// q_i = dV sum_core psi_i^2: CTA = (fragment, 8 orbitals), one warp per orbital.
+__global__ void __launch_bounds__(256) k_core_weights32(const FragDesc *desc, const float *psi, double dV,
+                                                        double *q) {
+  const FragDesc D = desc[blockIdx.x];
+  const int i = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (i >= D.norb) return;
+  const int lane = threadIdx.x & 31;
+  const int Ex = D.E[0], Ey = D.E[1];
+  const long long P = (long long)Ex * Ey * D.E[2];
+  const float *y = psi + D.psi_off + (long long)i * P + D.b[0] + (long long)Ex * (D.b[1] + (long long)Ey * D.b[2]);
+  const int cx2 = D.c[0] >> 1, cy = D.c[1];
+  const int nu = cx2 * cy * D.c[2];  // core point pairs
+  float hi = 0.f, lo = 0.f;
+  constexpr int U = 4;
+  for (int t0 = lane; t0 < nu; t0 += 32 * U) {
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + 32 * u;
+      v[u] = make_float2(0.f, 0.f);
+      if (t < nu) {
+        const int x2 = t % cx2, yz = t / cx2, yy = yz % cy, z = yz / cy;
+        v[u] = *reinterpret_cast<const float2 *>(y + 2 * x2 + Ex * (yy + (long long)Ey * z));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float p0 = __fmul_rn(v[u].x, v[u].x);  // not contracted into the TwoSum below
+      dw_add(hi, lo, p0);
+      lo += fmaf(v[u].x, v[u].x, -p0);
+      const float p1 = __fmul_rn(v[u].y, v[u].y);
+      dw_add(hi, lo, p1);
+      lo += fmaf(v[u].y, v[u].y, -p1);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    dw_add(hi, lo, h2);
+    lo += l2;
+  }
+  if (lane == 0) q[D.st_off + i] = dV * ((double)hi + (double)lo);
+}
+
+// rho(g) = sum_i 2 f_i psi_i(j)^2 over the core points of one fragment (CTA = fragment): each core
+// point is owned by exactly one fragment, so every global point is written once.  The occupations
+// are carried as FP32 pairs (2 f = oh + ol) and every term is formed with exact products, so the
+// density integrates to sum 2 f q = N_e to ~1e-12 (an FP32-rounded 2 f would break that at 1e-8).
+// A thread takes one core point pair and walks the orbitals eight loads at a time.
+__global__ void __launch_bounds__(256) k_density32(const FragDesc *desc, const float *psi, const double *occ, int Nx,
+                                                   int Ny, double *rho) {
+  __shared__ float occh[DC_MAX_NORB], occl[DC_MAX_NORB];
+  const FragDesc D = desc[blockIdx.x];
+  const int n = D.norb;
+  for (int i = threadIdx.x; i < n; i += 256) {
+    const double o2 = 2.0 * occ[D.st_off + i];
+    const float h = (float)o2;
+    occh[i] = h;
+    occl[i] = (float)(o2 - (double)h);
+  }
+  __syncthreads();
+  const int Ex = D.E[0], Ey = D.E[1];
+  const long long P = (long long)Ex * Ey * D.E[2];
+  const float *y0 = psi + D.psi_off + D.b[0] + (long long)Ex * (D.b[1] + (long long)Ey * D.b[2]);
+  const int cx2 = D.c[0] >> 1, cy = D.c[1];
+  const int nu = cx2 * cy * D.c[2];
+  const int gx0 = D.org[0] + D.b[0], gy0 = D.org[1] + D.b[1], gz0 = D.org[2] + D.b[2];
+  for (int t = threadIdx.x; t < nu; t += 256) {
+    const int x2 = t % cx2, yz = t / cx2, yy = yz % cy, z = yz / cy;
+    const float *y = y0 + 2 * x2 + Ex * (yy + (long long)Ey * z);
+    float hi0 = 0.f, lo0 = 0.f, hi1 = 0.f, lo1 = 0.f;
+    constexpr int U = 8;
+    for (int i0 = 0; i0 < n; i0 += U) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = i0 + u < n ? *reinterpret_cast<const float2 *>(y + (long long)(i0 + u) * P)
+                                                   : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (i0 + u >= n) break;
+        const float oh = occh[i0 + u], ol = occl[i0 + u];
+        {
+          const float p = __fmul_rn(v[u].x, v[u].x), pe = fmaf(v[u].x, v[u].x, -p);  // v^2 = p + pe exactly
+          const float th = __fmul_rn(oh, p), te = fmaf(oh, p, -th);                  // oh p = th + te exactly
+          dw_add(hi0, lo0, th);
+          lo0 += te + fmaf(oh, pe, ol * p);
+        }
+        {
+          const float p = __fmul_rn(v[u].y, v[u].y), pe = fmaf(v[u].y, v[u].y, -p);
+          const float th = __fmul_rn(oh, p), te = fmaf(oh, p, -th);
+          dw_add(hi1, lo1, th);
+          lo1 += te + fmaf(oh, pe, ol * p);
+        }
+      }
+    }
+    double *r = rho + (gx0 + 2 * x2) + (long long)Nx * ((gy0 + yy) + (long long)Ny * (gz0 + z));
+    r[0] = (double)hi0 + (double)lo0;
+    r[1] = (double)hi1 + (double)lo1;
+  }
+}
+
 }  // namespace
 
 namespace dck {
@@ -319,7 +426,10 @@ int launch_core_weights(dc_ctx *c, const T *psi, double *q, cudaStream_t s) {
   if (nf <= 0) return DC_OK;
   if constexpr (std::is_same<T, float>::value) {
     const dim3 grid((unsigned)nf, (unsigned)((c->layout.max_norb + 7) / 8));
-    k_core_weights32<<<grid, 256, 0, s>>>(c->d_desc + c->f_lo, psi, c->dV, q);
+    if (c->core_pairs)
+      k_core_weights32<<<grid, 256, 0, s>>>(c->d_desc + c->f_lo, psi, c->dV, q);
+    else
+      k_core_weights32s<<<grid, 256, 0, s>>>(c->d_desc + c->f_lo, psi, c->dV, q);
   } else {
     k_core_weights<T><<<(unsigned)(c->st_hi - c->st_lo), QNT, 0, s>>>(c->d_desc, c->d_items + c->st_lo, psi, c->dV, q);
   }
@@ -367,7 +477,10 @@ int launch_density(dc_ctx *c, const T *psi, const double *occ, double *rho, cuda
     // one CTA per owned core writes exactly that core's points; on a shard the rest of rho is zero
     if (nf < c->nfrag) DC_CUDA(cudaMemsetAsync(rho, 0, sizeof(double) * (size_t)c->npts, s));
     if (nf > 0)
-      k_density32<<<(unsigned)nf, 256, 0, s>>>(c->d_desc + c->f_lo, psi, occ, c->grid.n[0], c->grid.n[1], rho);
+      if (c->core_pairs)
+        k_density32<<<(unsigned)nf, 256, 0, s>>>(c->d_desc + c->f_lo, psi, occ, c->grid.n[0], c->grid.n[1], rho);
+      else
+        k_density32s<<<(unsigned)nf, 256, 0, s>>>(c->d_desc + c->f_lo, psi, occ, c->grid.n[0], c->grid.n[1], rho);
   } else {
     const unsigned nb = (unsigned)((c->npts + 255) / 256);
     k_density<T><<<nb, 256, 0, s>>>(c->d_desc, c->d_owner, c->d_core_local, c->npts, psi, occ, rho, c->f_lo,

@@ -183,12 +183,14 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   c->max_zlist = 0;
   c->max_plane_ent = 0;
   c->max_frag_ent = 0;
+  c->core_pairs = true;
   for (int d = 0; d < 3; ++d) c->max_E[d] = 0;
   int max_norb = 0;
   for (int f = 0; f < c->nfrag; ++f) {
     FragDesc &D = c->h_desc[f];
     long long P = (long long)D.E[0] * D.E[1] * D.E[2];
     for (int d = 0; d < 3; ++d) c->max_E[d] = std::max(c->max_E[d], D.E[d]);
+    if ((D.b[0] & 1) || (D.c[0] & 1) || (D.E[0] & 1)) c->core_pairs = false;
     max_norb = std::max(max_norb, D.norb);
     D.psi_off = psi_off;
     D.pt_off = pt_off;
