@@ -11,16 +11,16 @@
 // raw FP32 tiles in shared memory (cp.async, 16 bytes per copy, up to three tiles ahead; each
 // thread later converts exactly the chunks it copied, so a per-thread wait is enough), split them
 // into BF16 rows in a ring of shared-memory stages (K-major, no-swizzle canonical layout) and arrive
-// on the stage's `full` barrier; one thread of warp 15 waits on it and issues three MMAs per
-// 16-point K-step:
-//   D_S[128 x 3nb] = [Yh;Ym;Yl..] x [Yh|Ym|Yl]^T,  D_A[128 x 3nb] = [Yh;Ym;..] x [Zh|Zm|Zl]^T,
-//   D_L[128 x nb]  = [Yl;0] x [Zh]^T                                   (nb = n rounded up to 16)
+// on the stage's `full` barrier; one thread of warp 15 waits on it and issues five MMAs per 16-point
+// K-step (rows [h; m] of a 128-row operand whose remaining rows are the first l rows):
+//   S_h = [h; m] h^T,  A_h = [h; m] zh^T                  (the large terms, N = nb)
+//   S_r = [h; m] [m | l]^T,  A_r = [h; m] [zm | zl]^T     (N = 2 nb),  L = [l; 0] zh^T   (N = nb)
 // and commits them to the stage's `empty` barrier, which frees it for the converters.  The FP32
-// accumulators in tensor memory are drained every 256 points (the rounding of a tensor-memory sum
-// grows with its length): the MMA thread commits to `dready`, warps 7-14 add the accumulators into
-// FP32 sums kept in their registers (two warps per tensor-memory lane group, half the columns each)
-// and arrive on `ddone`, and only then may the next group overwrite them.  The register sums go to
-// shared memory once per item.  Each role has its own warps.
+// accumulators in tensor memory are drained into FP32 sums kept in the registers of warps 7-14 (two
+// warps per tensor-memory lane group, half the columns each): the large set every 256 points (the
+// rounding of a tensor-memory sum grows with its length) from two alternating buffers, so that its
+// drain runs while the MMAs fill the other buffer; the small set, ~2^-8 of the large one, every 1024
+// points, when the MMA thread waits for it.  The register sums go to shared memory once per item.
 // Each item leaves as one FP64 partial of S and A that the FP64 subspace kernel adds in a fixed
 // order.  Every wait is bounded; after a timeout every later wait returns at once, the kernel sets
 // DC_FLAG_TIMEOUT, waits (bounded) for its committed MMAs, frees its tensor memory and returns.
@@ -38,6 +38,8 @@ constexpr int TNT = 512;  // threads per CTA
 // vs FP64 energy difference after 43 steps, Gram time): 256 points 4.5e-7 Ha/atom, 1.09 ms; 512 points
 // 9.2e-7, 0.92 ms; 1024 points 2.1e-6, 0.90 ms.  The 1e-6 Ha/atom budget keeps 256.
 constexpr int TDR = 4;
+// Large-set drain groups per small-set drain (1024 points).
+constexpr int TSR = 4;
 constexpr int TMEM_COLS = 512;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -93,14 +95,50 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
   return false;
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
-  uint32_t r[8];
+// Three 32-lane x 8-column tensor-memory loads and one wait for all of them.  The wait names the 24
+// destination registers as in/out operands, so nothing reads them before the loads have completed.
+__device__ __forceinline__ void tmem_ld8x3(uint32_t t0, uint32_t t1, uint32_t t2, float *v0, float *v1, float *v2) {
+  uint32_t r[24];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
+               : "r"(t0));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(t1));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                 "=r"(r[23])
+               : "r"(t2));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]));
 #pragma unroll
-  for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+  for (int k = 0; k < 8; ++k) {
+    v0[k] = __uint_as_float(r[k]);
+    v1[k] = __uint_as_float(r[8 + k]);
+    v2[k] = __uint_as_float(r[16 + k]);
+  }
+}
+
+__device__ __forceinline__ void tmem_ld8x2(uint32_t t0, uint32_t t1, float *v0, float *v1) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(t0));
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(t1));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    v0[k] = __uint_as_float(r[k]);
+    v1[k] = __uint_as_float(r[8 + k]);
+  }
 }
 
 // byte offset of element (r, k) in a K-tile with `rows` rows (K-major, no swizzle)
@@ -214,13 +252,21 @@ __device__ __forceinline__ void convert_tile(const float4 *raw, int nslots, unsi
 // 8-column groups 2 j + h (h = (w - 7) / 4, j < NG).  Rows r < n (h rows) keep P1S = hh + hm + hl,
 // HL = hl, P1A = h.zh + h.zm + h.zl + l.zh; rows nb <= r < nb + n (m rows) keep P2S = mh + mm and
 // P2A = m.zh + m.zm; columns past n and other rows add nothing.
+//
+// The accumulators come in two sets.  The large terms (the h-column blocks: hh and mh of S, h.zh and
+// m.zh of A) are summed in FP32 in tensor memory over 256 points, the length the accuracy budget
+// allows; they alternate between two buffers, so that the drain of one overlaps the MMAs into the
+// other.  The remaining blocks (hm, hl, mm; h.zm, h.zl, m.zm; l.zh) are ~2^-8 of the large terms, so
+// their FP32 rounding over 1024 points stays ~2^-6 below that of the large terms over 256: they are
+// drained every 1024 points, and only then does the MMA thread wait for a drain.
 template <int NG>
 struct DrainRegs {
   float a0[8 * NG], a1[8 * NG], a2[8 * NG];
 };
 
+// The large set: S_h = [h; m] h^T and A_h = [h; m] zh^T.
 template <int NG>
-__device__ __forceinline__ void drain_add(DrainRegs<NG> &R, uint32_t tS, uint32_t tA, uint32_t tL, int n, int nb) {
+__device__ __forceinline__ void drain_big(DrainRegs<NG> &R, uint32_t tSh, uint32_t tAh, int n, int nb) {
   const int warp = threadIdx.x >> 5;
   const int half = (warp - 7) >> 2;
   const int r = 32 * (warp & 3) + (threadIdx.x & 31);
@@ -230,28 +276,52 @@ __device__ __forceinline__ void drain_add(DrainRegs<NG> &R, uint32_t tS, uint32_
   for (int j = 0; j < NG; ++j) {
     const int cg = 8 * (2 * j + half);
     if (cg >= nb) continue;  // warp-uniform
-    float x0[8], x1[8], x2[8];
-    tmem_ld8(tS + lane_base + cg, x0);
-    tmem_ld8(tS + lane_base + nb + cg, x1);
-    tmem_ld8(tS + lane_base + 2 * nb + cg, x2);
+    float x0[8], y0[8];
+    tmem_ld8x2(tSh + lane_base + cg, tAh + lane_base + cg, x0, y0);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       if (own) {
-        R.a0[8 * j + e] += x0[e] + x1[e] + x2[e];
-        R.a1[8 * j + e] += x2[e];
+        R.a0[8 * j + e] += x0[e];
+        R.a2[8 * j + e] += y0[e];
       } else if (mrow) {
-        R.a0[8 * j + e] += x0[e] + x1[e];
+        R.a0[8 * j + e] += x0[e];
+        R.a1[8 * j + e] += y0[e];
       }
     }
-    float y0[8], y1[8], y2[8], y3[8];
-    tmem_ld8(tA + lane_base + cg, y0);
-    tmem_ld8(tA + lane_base + nb + cg, y1);
-    tmem_ld8(tA + lane_base + 2 * nb + cg, y2);
-    tmem_ld8(tL + lane_base + cg, y3);
+  }
+}
+
+// The small set: S_r = [h; m] [m | l]^T, A_r = [h; m] [zm | zl]^T and L = [l; 0] zh^T.
+template <int NG>
+__device__ __forceinline__ void drain_small(DrainRegs<NG> &R, uint32_t tSr, uint32_t tAr, uint32_t tL, int n,
+                                            int nb) {
+  const int warp = threadIdx.x >> 5;
+  const int half = (warp - 7) >> 2;
+  const int r = 32 * (warp & 3) + (threadIdx.x & 31);
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const bool own = r < n, mrow = (r >= nb && r < nb + n);
+#pragma unroll
+  for (int j = 0; j < NG; ++j) {
+    const int cg = 8 * (2 * j + half);
+    if (cg >= nb) continue;  // warp-uniform
+    float x1[8], x2[8], y3[8];
+    tmem_ld8x3(tSr + lane_base + cg, tSr + lane_base + nb + cg, tL + lane_base + cg, x1, x2, y3);
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      if (own) R.a2[8 * j + e] += y0[e] + y1[e] + y2[e] + y3[e];
-      else if (mrow) R.a1[8 * j + e] += y0[e] + y1[e];
+      if (own) {
+        R.a0[8 * j + e] += x1[e] + x2[e];
+        R.a1[8 * j + e] += x2[e];
+        R.a2[8 * j + e] += y3[e];
+      } else if (mrow) {
+        R.a0[8 * j + e] += x1[e];
+      }
+    }
+    float y1[8], y2[8];
+    tmem_ld8x2(tAr + lane_base + cg, tAr + lane_base + nb + cg, y1, y2);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      if (own) R.a2[8 * j + e] += y1[e] + y2[e];
+      else if (mrow) R.a1[8 * j + e] += y1[e];
     }
   }
 }
@@ -294,7 +364,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
                                                     unsigned *flags) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t full[3], empty[3], dready, ddone;
+  __shared__ __align__(8) uint64_t full[3], empty[3], dready_b[2], ddone_b[2], dready_s, ddone_s;
   __shared__ int timed_out;
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -319,8 +389,12 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&full[k])), "r"(TCV));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&empty[k])), "r"(1));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&dready)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ddone)), "r"(TDW));
+    for (int k = 0; k < 2; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&dready_b[k])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ddone_b[k])), "r"(TDW));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&dready_s)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ddone_s)), "r"(TDW));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -328,7 +402,11 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tslot;
   int gt = 0;     // K-tiles this CTA has passed through the ring (stage gt % nstages, use gt / nstages)
-  int gd = 0;     // drains done by this CTA (phase of dready / ddone)
+  int gb = 0;     // large-set drain groups of this CTA (buffer gb % nbuf, its use gb / nbuf)
+  int gs = 0;     // small-set drains of this CTA
+  // tensor-memory columns (blocks sized for the largest orbital count): nbuf large-set buffers of
+  // [S_h | A_h] (2 nbmax columns each), then S_r and A_r (2 nbmax each) and L (nbmax)
+  const int nbuf = 9 * nbmax <= TMEM_COLS ? 2 : 1;
   int prev_n = -1;
   int commits = 0;  // MMA groups committed by the MMA thread (tracked for the final wait)
 
@@ -348,8 +426,8 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
     const float *Yf = Y + D.psi_off;
     const float *Zf = HY + D.psi_off;
     const bool vec = ((P | D.psi_off) & 3) == 0;
-    const uint32_t tS = tbase, tA = tbase + 3 * nb, tL = tbase + 6 * nb;
-    const uint32_t iS = idesc_bf16(128, 3 * nb), iL = idesc_bf16(128, nb);
+    const uint32_t tSr = tbase + 2 * nbuf * nbmax, tAr = tSr + 2 * nbmax, tL = tAr + 2 * nbmax;
+    const uint32_t iN1 = idesc_bf16(128, nb), iN2 = idesc_bf16(128, 2 * nb);
     const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
 
     // item start (the whole CTA is here, no MMA in flight): stage padding rows zero for this orbital
@@ -393,12 +471,22 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
 #pragma unroll
       for (int k = 0; k < 8 * NG; ++k) R.a0[k] = R.a1[k] = R.a2[k] = 0.f;
       const int ngroups = (ntiles + TDR - 1) / TDR;
-      for (int g = 0; g < ngroups; ++g, ++gd) {
-        if (!mbar_wait_or(&dready, (uint32_t)(gd & 1), &timed_out)) break;
+      for (int g = 0; g < ngroups; ++g) {
+        const int bb = gb % nbuf, bu = gb / nbuf;
+        if (!mbar_wait_or(&dready_b[bb], (uint32_t)(bu & 1), &timed_out)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        drain_add<NG>(R, tS, tA, tL, n, nb);
+        drain_big<NG>(R, tbase + 2 * bb * nbmax, tbase + 2 * bb * nbmax + nbmax, n, nb);
         asm volatile("tcgen05.fence::before_thread_sync;");
-        mbar_arrive(&ddone);
+        mbar_arrive(&ddone_b[bb]);
+        ++gb;
+        if (g % TSR == TSR - 1 || g == ngroups - 1) {
+          if (!mbar_wait_or(&dready_s, (uint32_t)(gs & 1), &timed_out)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          drain_small<NG>(R, tSr, tAr, tL, n, nb);
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          mbar_arrive(&ddone_s);
+          ++gs;
+        }
       }
       drain_store<NG>(R, n, nb, acc);
     } else if ((tid & 31) == 0) {
@@ -406,36 +494,47 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
       for (int t = 0; t < ntiles; ++t, ++gt) {
         const int s = gt % nstages;
         const uint32_t use = (uint32_t)(gt / nstages);
-        if (t % TDR == 0 && t > 0) {
-          // the previous group's accumulators must be drained before they are overwritten
-          if (!mbar_wait_or(&ddone, (uint32_t)((gd - 1) & 1), &timed_out)) break;
-        }
+        const bool gstart = t % TDR == 0, wstart = t % (TDR * TSR) == 0;
+        const int bb = gb % nbuf, bu = gb / nbuf;
+        // a large-set buffer is overwritten only after its previous group has been drained (with two
+        // buffers, the drain of the other one may still be running); the small set after its last drain
+        if (gstart && bu > 0 && !mbar_wait_or(&ddone_b[bb], (uint32_t)((bu - 1) & 1), &timed_out)) break;
+        if (wstart && gs > 0 && !mbar_wait_or(&ddone_s, (uint32_t)((gs - 1) & 1), &timed_out)) break;
         if (!mbar_wait_or(&full[s], use & 1u, &timed_out)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
         unsigned char *ys = sm + s * stage_bytes;
         unsigned char *zs = ys + ybytes;
         const uint32_t ya = su32(ys), za = su32(zs);
+        const uint32_t tSh = tbase + 2 * bb * nbmax, tAh = tSh + nbmax;
 #pragma unroll
         for (int kk = 0; kk < TKT / 16; ++kk) {
-          const uint32_t accum = (t % TDR != 0 || kk > 0) ? 1u : 0u;
-          const uint64_t aY = sdesc(ya + kk * 2 * ksY, ksY, 128);
-          const uint64_t aL = sdesc(ya + kk * 2 * ksY + (2 * nb / 8) * 128, ksY, 128);
-          const uint64_t bZ = sdesc(za + kk * 2 * ksZ, ksZ, 128);
-          mma_bf16(tS, aY, aY, iS, accum);
-          mma_bf16(tA, aY, bZ, iS, accum);
-          mma_bf16(tL, aL, bZ, iL, accum);
+          const uint32_t accB = (!gstart || kk > 0) ? 1u : 0u;
+          const uint32_t accS = (!wstart || kk > 0) ? 1u : 0u;
+          const uint64_t aY = sdesc(ya + kk * 2 * ksY, ksY, 128);                       // rows h, m, l
+          const uint64_t bYr = sdesc(ya + kk * 2 * ksY + (nb / 8) * 128, ksY, 128);     // rows m, l
+          const uint64_t aL = sdesc(ya + kk * 2 * ksY + (2 * nb / 8) * 128, ksY, 128);  // rows l, 0
+          const uint64_t bZ = sdesc(za + kk * 2 * ksZ, ksZ, 128);                       // rows zh, ...
+          const uint64_t bZr = sdesc(za + kk * 2 * ksZ + (nb / 8) * 128, ksZ, 128);     // rows zm, zl
+          mma_bf16(tSh, aY, aY, iN1, accB);   // [h; m] h^T
+          mma_bf16(tAh, aY, bZ, iN1, accB);   // [h; m] zh^T
+          mma_bf16(tSr, aY, bYr, iN2, accS);  // [h; m] [m | l]^T
+          mma_bf16(tAr, aY, bZr, iN2, accS);  // [h; m] [zm | zl]^T
+          mma_bf16(tL, aL, bZ, iN1, accS);    // [l; 0] zh^T
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             su32(&empty[s])));
         ++commits;
         if (t % TDR == TDR - 1 || t == ntiles - 1) {
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              su32(&dready)));
-          ++gd;
+              su32(&dready_b[bb])));
+          ++gb;
+        }
+        if (t % (TDR * TSR) == TDR * TSR - 1 || t == ntiles - 1) {
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              su32(&dready_s)));
+          ++gs;
         }
       }
-      // the item's last drain must be complete before the partial is read
-      if (!timed_out) mbar_wait_or(&ddone, (uint32_t)((gd - 1) & 1), &timed_out);
     } else {
       // lanes 1-31 of the MMA warp: no role
     }
