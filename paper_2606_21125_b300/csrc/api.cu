@@ -75,7 +75,7 @@ void free_ctx(dc_ctx *c) {
                   c->blk64[1], c->blk64[2], c->d_hy64, c->d_c64[0], c->d_c64[1], c->d_c32[0], c->d_c32[1],
                   c->d_eps, c->d_q, c->d_occ, c->d_bounds, c->d_gram, c->d_gram_off, c->d_gram_nchunk, c->d_C64,
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
-                  c->d_items2, c->d_row_beg, c->d_row_ent, c->d_nl_bound, c->d_rot2_items,
+                  c->d_items2, c->d_row_beg, c->d_row_ent, c->d_row_split, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
                   c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux, c->d_frag_order, c->d_rhof, c->d_vcore};
   for (void *p : ptrs)
@@ -595,6 +595,7 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(upload(&c->d_zl_items, ht.zl_items));
   DC_TRY(upload(&c->d_row_beg, ht.row_beg));
   DC_TRY(upload(&c->d_row_ent, ht.row_ent));
+  DC_TRY(upload(&c->d_row_split, ht.row_split));
   std::vector<double> Datom(c->natom), posv(c->h_pos);
   for (int a = 0; a < c->natom; ++a) Datom[a] = c->h_Ds[c->h_species[a]];
   DC_TRY(upload(&c->d_atom_D, Datom));
@@ -745,6 +746,10 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(dmalloc(&c->d_dots, (size_t)Lo.nstates));
   DC_TRY(dmalloc(&c->d_q_x, (size_t)Lo.nstates));
   DC_TRY(dmalloc(&c->d_occ_x, (size_t)Lo.nstates));
+  // the per-state arrays start at zero (they are readable through dc_get_state / dc_query before the
+  // first solve fills them)
+  for (double *d : {c->d_eps, c->d_q, c->d_occ, c->d_dots, c->d_q_x, c->d_occ_x})
+    DC_CUDA(cudaMemset(d, 0, sizeof(double) * (size_t)std::max<long long>(1, Lo.nstates)));
   DC_TRY(dmalloc(&c->d_aux, 4));
   if (P.xc_fragment) {
     DC_TRY(dmalloc(&c->d_rhof, (size_t)Lo.frag_points));

@@ -106,6 +106,7 @@ struct dc_ctx {
   int *d_zl_items = nullptr;   // per-plane atom slots
   int *d_row_beg = nullptr;    // per-row (z, y) list starts into d_row_ent
   int2 *d_row_ent = nullptr;   // (slot | y << 16, FP32 bits of gz(z) gy(y))
+  int *d_row_split = nullptr;  // per row: entries reaching only the left half | (those plus both halves) << 16
   double *d_atom_D = nullptr;  // D per atom (global index)
   double *d_nl_bound = nullptr;  // per fragment: upper bound of the nonlocal operator (filter bounds)
   double *d_atom_pos = nullptr;
@@ -222,6 +223,7 @@ struct HostTables {
   std::vector<int> zl_beg, zl_items;
   std::vector<int> row_beg;
   std::vector<int2> row_ent;
+  std::vector<int> row_split;
 };
 int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out);
 // Fragment range [*lo, *hi) of rank `rank` of `nranks` (1 <= nranks <= nfrag): contiguous ids, each

@@ -50,6 +50,7 @@ struct ChebArgs {
   const float *tab;       // FP32 projector factors
   const int *row_beg;     // per (fragment, z, y) start into row_ent
   const int2 *row_ent;    // (slot | y << 16, FP32 bits of gz gy)
+  const int *row_split;   // per row: left-only entries | (left-only + both) << 16
   const double *Datom;
   const float *vf;        // V per fragment point (FP32)
   unsigned *flags;        // device error flags (DC_FLAG_TIMEOUT)
@@ -150,7 +151,7 @@ struct ItemInfo {
 // Shared-memory carve (byte offsets; the same function sizes the launch on the host).
 template <int E, bool PREV>
 struct ChebLayout {
-  size_t ring, full, itab, pin, pout, gxp, pacc, sk2, dsk, cdv, sent, box, rb, end;
+  size_t ring, full, itab, pin, pout, gxp, pacc, sk2, dsk, cdv, sent, box, rb, rsp, end;
   static __host__ __device__ size_t up(size_t o, size_t a) { return (o + a - 1) / a * a; }
   __host__ __device__ ChebLayout(int A, int nent, int ipc) {
     using G = Geo<E>;
@@ -181,6 +182,8 @@ struct ChebLayout {
     o += (size_t)A * sizeof(int2);
     rb = o;
     o += (size_t)(G::PLANE + 1) * sizeof(int);
+    rsp = o;
+    o += (size_t)G::PLANE * sizeof(int);
     end = up(o, 16);
   }
 };
@@ -202,6 +205,7 @@ struct ChebSmem {
   int2 *sent;           // [nent]        the fragment's row-list entries
   int2 *box;            // [A]           even-aligned x support
   int *rb;              // [E*E + 1]     row starts (relative to the fragment's first entry)
+  int *rsp;             // [E*E]         row splits: left-only entries | (left-only + both) << 16
 };
 
 // Planes per ring slot: y_in of the pair, y_prev of the pair (with PREV), V.
@@ -229,6 +233,7 @@ __device__ __forceinline__ ChebSmem<E> cheb_carve(unsigned char *raw, int A, int
   m.sent = reinterpret_cast<int2 *>(raw + L.sent);
   m.box = reinterpret_cast<int2 *>(raw + L.box);
   m.rb = reinterpret_cast<int *>(raw + L.rb);
+  m.rsp = reinterpret_cast<int *>(raw + L.rsp);
   return m;
 }
 
@@ -416,7 +421,11 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
   // nonlocal term over the row's records
   {
     const int rz = z * E + T.py;
-    const int eb = m.rb[rz], ee = m.rb[rz + 1];
+    // entries that can reach this point's half of the row: [left-only | both] or [both | right-only]
+    const int r0 = m.rb[rz], sp = m.rsp[rz];
+    const bool left = (T.px >> 1) < (G::NPX + 1) / 2;
+    const int eb = left ? r0 : r0 + (sp & 0xffff);
+    const int ee = left ? r0 + (sp >> 16) : m.rb[rz + 1];
     const float2 *gp = m.gxp + (T.px >> 1);
     int e = eb;
     for (; e + 1 < ee; e += 2) {
@@ -589,6 +598,7 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
         sk2[k] = f2(ds * ci[0], nvalid > 1 ? ds * ci[A] : 0.f);
       }
       for (int t = tid; t <= G::PLANE; t += G::NT) m.rb[t] = a.row_beg[D.row_off + t] - r0;
+      for (int t = tid; t < G::PLANE; t += G::NT) m.rsp[t] = a.row_split[D.row_off + t];
       copy_int2<G::NT>(m.sent, a.row_ent + r0, nent);
       cur_vf = I.vf;
       __syncthreads();
@@ -723,6 +733,7 @@ int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yp
   a.tab = c->d_tab32;
   a.row_beg = c->d_row_beg;
   a.row_ent = c->d_row_ent;
+  a.row_split = c->d_row_split;
   a.Datom = c->d_atom_D;
   a.vf = c->d_vf32;
   a.flags = c->d_flags;

@@ -179,6 +179,7 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   std::vector<int> zl_beg, zl_items;
   std::vector<int> row_beg;
   std::vector<int2> row_ent;
+  std::vector<int> row_split;
   c->max_atoms = 0;
   c->max_zlist = 0;
   c->max_plane_ent = 0;
@@ -256,16 +257,23 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
     }
     zl_beg.push_back((int)zl_items.size());
     c->max_zlist = std::max(c->max_zlist, total);
-    // Row lists of the orbital-pair stencil kernel: for every row (z, y), in z-list order, the slots
-    // whose FP32 product gz(z) gy(y) is non-zero, as (k | y << 16, bits of that product).
+    // Row lists of the orbital-pair stencil kernel: for every row (z, y), the slots whose FP32 product
+    // gz(z) gy(y) is non-zero, as (k | y << 16, bits of that product).  Each row lists first the slots
+    // whose x-support lies in the left half of the row's point pairs, then those reaching both halves,
+    // then those only in the right half (z-list order within each group), and row_split records the two
+    // boundaries, so that a point walks only the entries that can reach its half.
     {
       const int Ex = D.E[0], Ey = D.E[1], Ez = D.E[2], tw = tab_width(D);
       const int zl0 = (int)zl_beg.size() - (Ez + 1);
+      const int xb = 2 * ((((Ex + 1) / 2) + 1) / 2);  // first point of the right half (point pairs)
+      const ProjSlot *fs = slots.data() + (slots.size() - A);
       D.row_off = (int)row_beg.size();
+      std::vector<int2> grp[3];
       for (int z = 0; z < Ez; ++z) {
         const size_t plane_start = row_ent.size();
         for (int y = 0; y < Ey; ++y) {
           row_beg.push_back((int)row_ent.size());
+          for (auto &v : grp) v.clear();
           for (int e = zl_beg[zl0 + z]; e < zl_beg[zl0 + z + 1]; ++e) {
             const int k = zl_items[e];
             const double *g = &tab[tab_off + (long long)k * tw];
@@ -273,13 +281,18 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
             if (w != 0.f) {
               int wb;
               std::memcpy(&wb, &w, sizeof(int));
-              row_ent.push_back(make_int2(k | (y << 16), wb));
+              const int side = fs[k].hi[0] <= xb ? 0 : (fs[k].lo[0] >= xb ? 2 : 1);
+              grp[side].push_back(make_int2(k | (y << 16), wb));
             }
           }
+          for (const auto &v : grp) row_ent.insert(row_ent.end(), v.begin(), v.end());
+          const int nl = (int)grp[0].size(), nlb = nl + (int)grp[1].size();
+          row_split.push_back(nl | (nlb << 16));
         }
         c->max_plane_ent = std::max(c->max_plane_ent, (int)(row_ent.size() - plane_start));
       }
       row_beg.push_back((int)row_ent.size());
+      row_split.push_back(0);  // parallel to row_beg (one sentinel per fragment)
       c->max_frag_ent = std::max(c->max_frag_ent, (int)(row_ent.size() - (size_t)row_beg[D.row_off]));
       if (row_ent.size() > (size_t)INT32_MAX / 2) {
         dc_set_error("dc_init: projector row lists too long");
@@ -341,6 +354,7 @@ int dc_build_host(dc_ctx *c, const dc_atoms_t *atoms, HostTables &out) {
   out.zl_items.swap(zl_items);
   out.row_beg.swap(row_beg);
   out.row_ent.swap(row_ent);
+  out.row_split.swap(row_split);
   return DC_OK;
 }
 
