@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdcdft.so")
 SOURCES = ["api.cu", "setup.cpp", "k_hamiltonian.cu", "k_subspace.cu", "k_density.cu", "k_global.cu",
-           "k_adjoint.cu", "k_gram_tc.cu", "k_probe.cu", "k_cheb.cu"]
+           "k_adjoint.cu", "k_gram_tc.cu", "k_probe.cu", "k_cheb.cu",
+           "k_rotate_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -295,6 +295,7 @@ int launch_bounds(dc_ctx *c, int first, cudaStream_t s);
 template <typename T>
 int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s);
 int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s);
+int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s);
 int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s);
 template <typename T>
 int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, double lambda_cut, double *basis,

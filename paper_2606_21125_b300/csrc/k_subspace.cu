@@ -1037,6 +1037,8 @@ int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s) 
 template <typename T>
 int launch_rotate(dc_ctx *c, const T *Y, T *out, cudaStream_t s) {
   if constexpr (std::is_same<T, float>::value) {
+    // tensor cores where the context qualifies (at most 64 orbitals, 16-byte aligned point rows)
+    if (launch_rotate_tc(c, Y, out, s) == DC_OK) return DC_OK;
     const int opt = (c->layout.max_norb + 7) / 8;
     const int nmax = c->layout.max_norb;
     const size_t sm = (size_t)nmax * R2PAD * sizeof(float) + (size_t)nmax * 8 * opt * sizeof(float2);
