@@ -1,6 +1,7 @@
 // Internal declarations of the DC-DFT fragment solver (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
@@ -296,6 +297,11 @@ template <typename T>
 int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s);
 int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s);
 int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s);
+// 2-D tensor map over an FP32 block viewed as `rows` rows of `inner` elements (inner a multiple of 4,
+// base 16-byte aligned), box (box_inner, box_rows), zero fill out of range, optional 128-byte swizzle;
+// false when the driver's encoder is unavailable or the shape does not qualify.
+bool tensor_map_rows(CUtensorMap *map, const float *base, long long inner, long long rows, int box_inner,
+                     int box_rows, bool swizzle128);
 int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s);
 template <typename T>
 int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, double lambda_cut, double *basis,

@@ -24,6 +24,7 @@
 // Each item leaves as one FP64 partial of S and A that the FP64 subspace kernel adds in a fixed
 // order.  Every wait is bounded; after a timeout every later wait returns at once, the kernel sets
 // DC_FLAG_TIMEOUT, waits (bounded) for its committed MMAs, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -233,6 +234,36 @@ __device__ __forceinline__ void store_split(unsigned char *st, int i, int k, int
   *reinterpret_cast<uint2 *>(st + toff(2 * nb + i, k, ks)) = make_uint2(l0, l1);
 }
 
+// TMA form of the raw ring: each array's K-tile arrives as two 32-point boxes of nbmax rows with the
+// 128-byte swizzle (16-byte chunk c of row i stored at chunk c ^ (i % 8)), so that the converters' reads
+// (one warp: 8 rows x 4 quads) hit eight different chunks of a 128-byte line.
+__device__ __forceinline__ float4 raw_tma(const unsigned char *slot, int nbmax, int a, int i, int kq) {
+  return *reinterpret_cast<const float4 *>(slot + ((a * 2 + (kq >> 3)) * nbmax + i) * 128 + (((kq & 7) ^ (i & 7)) << 4));
+}
+
+__device__ __forceinline__ void convert_tile_tma(const unsigned char *slot, int nbmax, unsigned char *ys,
+                                                 unsigned char *zs, int n, int nb, int ksY, int ksZ) {
+#pragma unroll
+  for (int j = 0; j < TSL; ++j) {
+    const int idx = threadIdx.x + j * TCV;
+    int i, kq;
+    tile_slot(idx, i, kq);
+    if (idx < 1024 && i < n) {
+      const int k = 4 * kq;
+      store_split(ys, i, k, ksY, nb, raw_tma(slot, nbmax, 0, i, kq));
+      store_split(zs, i, k, ksZ, nb, raw_tma(slot, nbmax, 1, i, kq));
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(su32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(su32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void convert_tile(const float4 *raw, int nslots, unsigned char *ys, unsigned char *zs,
                                              int n, int nb, int ksY, int ksZ) {
 #pragma unroll
@@ -357,14 +388,16 @@ __device__ __forceinline__ void drain_store(const DrainRegs<NG> &R, int n, int n
 
 constexpr int TDW = 256;  // drain threads (warps 7-14)
 
-template <int NG>
+template <int NG, bool TMA>
 __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const int2 *gitems, int n_items,
                                                     const long long *goff, int chunk, int nmax, int nstages,
                                                     int nraw, const float *Y, const float *HY, double *out,
-                                                    unsigned *flags) {
+                                                    unsigned *flags, const __grid_constant__ CUtensorMap tmY,
+                                                    const __grid_constant__ CUtensorMap tmZ) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tslot;
-  __shared__ __align__(8) uint64_t full[3], empty[3], dready_b[2], ddone_b[2], dready_s, ddone_s;
+  __shared__ __align__(8) uint64_t full[3], empty[3], dready_b[2], ddone_b[2], dready_s, ddone_s, rfull[3],
+      rempty[3];
   __shared__ int timed_out;
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -394,6 +427,10 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ddone_b[k])), "r"(TDW));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&dready_s)), "r"(1));
+    for (int k = 0; k < 3; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&rfull[k])), "r"(4));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&rempty[k])), "r"(TCV));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&ddone_s)), "r"(TDW));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -402,6 +439,8 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tslot;
   int gt = 0;     // K-tiles this CTA has passed through the ring (stage gt % nstages, use gt / nstages)
+  int gr = 0;     // K-tiles loaded through the TMA raw ring (slot gr % nraw, its use gr / nraw)
+  const int rslot = 4 * nbmax * 128;  // TMA raw slot: two arrays x two 32-point boxes of nbmax rows
   int gb = 0;     // large-set drain groups of this CTA (buffer gb % nbuf, its use gb / nbuf)
   int gs = 0;     // small-set drains of this CTA
   // tensor-memory columns (blocks sized for the largest orbital count): nbuf large-set buffers of
@@ -437,10 +476,51 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         reinterpret_cast<uint4 *>(sm)[t] = make_uint4(0, 0, 0, 0);
       prev_n = n;
     }
+    // ordinary stores into memory that the async proxy touches next (zeroed stages, which the MMAs
+    // read; the item sums, whose space the next TMA tiles overwrite) are ordered before it here
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (timed_out) break;
 
-    if (tid < TCV) {
+    if (TMA && tid < TCV) {
+      // ---- converters.  Each raw slot holds four 32-point boxes (Y and HY, two halves); box k of every
+      // tile is issued by converter thread 64 k (warps 0, 2, 4, 6), once every converter has arrived on
+      // the slot's `rempty` barrier after converting the tile that used it ----
+      const int row0 = (int)(D.psi_off / P);
+      unsigned char *rbase = reinterpret_cast<unsigned char *>(rawring);
+      const int box = (tid & 63) == 0 ? tid >> 6 : -1;  // 0..3 on the issuing threads
+      auto issue = [&](int t) {
+        const int r = (gr + t) % nraw;
+        unsigned char *dst = rbase + (size_t)r * rslot + box * nbmax * 128;
+        // the slot was last accessed through ordinary loads and stores (tiles, item sums)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&rfull[r])),
+                     "r"(nbmax * 128)
+                     : "memory");
+        tma_load_2d(dst, box < 2 ? &tmY : &tmZ, (int)(p0 + (long long)t * TKT) + 32 * (box & 1), row0, &rfull[r]);
+      };
+      if (box >= 0)
+        for (int t = 0; t < nraw && t < ntiles; ++t) issue(t);
+      for (int t = 0; t < ntiles; ++t, ++gt) {
+        const int s = gt % nstages;
+        const uint32_t use = (uint32_t)(gt / nstages);
+        const int r = (gr + t) % nraw;
+        const uint32_t ruse = (uint32_t)((gr + t) / nraw);
+        if (!mbar_wait_or(&rfull[r], ruse & 1u, &timed_out)) break;
+        if (!mbar_wait_or(&empty[s], (use & 1u) ^ 1u, &timed_out)) break;
+        unsigned char *ys = sm + s * stage_bytes;
+        unsigned char *zs = ys + ybytes;
+        convert_tile_tma(rbase + (size_t)r * rslot, nbmax, ys, zs, n, nb, ksY, ksZ);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&full[s]);
+        mbar_arrive(&rempty[r]);
+        if (box >= 0 && t + nraw < ntiles) {
+          if (!mbar_wait_or(&rempty[r], ruse & 1u, &timed_out)) break;
+          issue(t + nraw);
+        }
+      }
+      gr += ntiles;
+    } else if (tid < TCV) {
       // ---- converters: tile t's raw copy was issued nraw tiles earlier into ring slot t % nraw ----
       for (int r = 0; r < nraw; ++r) {
         if (r < ntiles) fetch_tile(rawring + (size_t)r * 2 * nslots, nslots, Yf, Zf, P, n, p0 + (long long)r * TKT,
@@ -506,15 +586,20 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         unsigned char *zs = ys + ybytes;
         const uint32_t ya = su32(ys), za = su32(zs);
         const uint32_t tSh = tbase + 2 * bb * nbmax, tAh = tSh + nbmax;
+        // the five operand descriptors of K-step 0; a K-step of 16 points advances each start address by
+        // two core-matrix columns (the start field counts 16-byte units)
+        const uint64_t dY = sdesc(ya, ksY, 128);                          // rows h, m, l
+        const uint64_t dYr = sdesc(ya + (nb / 8) * 128, ksY, 128);        // rows m, l
+        const uint64_t dL = sdesc(ya + (2 * nb / 8) * 128, ksY, 128);     // rows l, 0
+        const uint64_t dZ = sdesc(za, ksZ, 128);                          // rows zh, ...
+        const uint64_t dZr = sdesc(za + (nb / 8) * 128, ksZ, 128);        // rows zm, zl
+        const uint64_t stY = (uint64_t)((2 * ksY) >> 4), stZ = (uint64_t)((2 * ksZ) >> 4);
 #pragma unroll
         for (int kk = 0; kk < TKT / 16; ++kk) {
           const uint32_t accB = (!gstart || kk > 0) ? 1u : 0u;
           const uint32_t accS = (!wstart || kk > 0) ? 1u : 0u;
-          const uint64_t aY = sdesc(ya + kk * 2 * ksY, ksY, 128);                       // rows h, m, l
-          const uint64_t bYr = sdesc(ya + kk * 2 * ksY + (nb / 8) * 128, ksY, 128);     // rows m, l
-          const uint64_t aL = sdesc(ya + kk * 2 * ksY + (2 * nb / 8) * 128, ksY, 128);  // rows l, 0
-          const uint64_t bZ = sdesc(za + kk * 2 * ksZ, ksZ, 128);                       // rows zh, ...
-          const uint64_t bZr = sdesc(za + kk * 2 * ksZ + (nb / 8) * 128, ksZ, 128);     // rows zm, zl
+          const uint64_t aY = dY + kk * stY, bYr = dYr + kk * stY, aL = dL + kk * stY;
+          const uint64_t bZ = dZ + kk * stZ, bZr = dZr + kk * stZ;
           mma_bf16(tSh, aY, aY, iN1, accB);   // [h; m] h^T
           mma_bf16(tAh, aY, bZ, iN1, accB);   // [h; m] zh^T
           mma_bf16(tSr, aY, bYr, iN2, accS);  // [h; m] [m | l]^T
@@ -577,8 +662,20 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     dc_set_error("mixed-precision Gram needs n <= 64 orbitals per fragment");
     return DC_ERR_ARG;
   }
+  // raw tiles by TMA when every fragment has the same point count P (a multiple of 4): the blocks are
+  // then rows of P points, and a tile is two 32-point boxes of nb rows per array
+  CUtensorMap mY{}, mZ{};
+  bool tma = c->h_desc.size() > 0;
+  const long long P0 = tma ? (long long)c->h_desc[0].E[0] * c->h_desc[0].E[1] * c->h_desc[0].E[2] : 0;
+  for (const auto &D : c->h_desc)
+    if ((long long)D.E[0] * D.E[1] * D.E[2] != P0) tma = false;
+  tma = tma && (P0 & 3) == 0 && c->gram_chunk % TKT == 0;
+  if (tma) {
+    const long long rows = c->layout.psi_elems / P0;
+    tma = tensor_map_rows(&mY, Y, P0, rows, 32, nb, true) && tensor_map_rows(&mZ, HY, P0, rows, 32, nb, true);
+  }
   const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
-  const size_t rawslot = 2 * (size_t)((nmax + 7) / 8) * 128 * sizeof(float4);
+  const size_t rawslot = tma ? 4 * (size_t)nb * 128 : 2 * (size_t)((nmax + 7) / 8) * 128 * sizeof(float4);
   const size_t accb = 5 * (size_t)nmax * (nmax + 1) * sizeof(float);
   // deepest (BF16 stages, raw tiles) pair that fits: three stages let the conversion run two tiles
   // ahead of the MMA (which pauses for each drain), the raw ring keeps up to three tiles of loads in
@@ -604,15 +701,23 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
   auto run = [&](auto kern) -> int {
     DC_CUDA(dc_set_smem((const void *)kern, sm));
     kern<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,
-                               nstages, nraw, Y, HY, c->d_gram, c->d_flags);
+                               nstages, nraw, Y, HY, c->d_gram, c->d_flags, mY, mZ);
     DC_CUDA(cudaGetLastError());
     return DC_OK;
   };
+  if (tma) {
+    switch (ng) {
+      case 1: return run(k_gram_tc<1, true>);
+      case 2: return run(k_gram_tc<2, true>);
+      case 3: return run(k_gram_tc<3, true>);
+      default: return run(k_gram_tc<4, true>);
+    }
+  }
   switch (ng) {
-    case 1: return run(k_gram_tc<1>);
-    case 2: return run(k_gram_tc<2>);
-    case 3: return run(k_gram_tc<3>);
-    default: return run(k_gram_tc<4>);
+    case 1: return run(k_gram_tc<1, false>);
+    case 2: return run(k_gram_tc<2, false>);
+    case 3: return run(k_gram_tc<3, false>);
+    default: return run(k_gram_tc<4, false>);
   }
 }
 

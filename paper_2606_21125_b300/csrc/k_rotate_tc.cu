@@ -335,10 +335,14 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(RT_TMEM_COLS));
 }
 
+}  // namespace
+
+namespace dck {
+
+namespace {
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 EncodeTiled encode_fn() {
   static EncodeTiled fn = nullptr;
   if (!fn) {
@@ -350,10 +354,20 @@ EncodeTiled encode_fn() {
   }
   return fn;
 }
-
 }  // namespace
 
-namespace dck {
+bool tensor_map_rows(CUtensorMap *map, const float *base, long long inner, long long rows, int box_inner,
+                     int box_rows, bool swizzle128) {
+  const EncodeTiled enc = encode_fn();
+  if (!enc || (inner & 3) || ((uintptr_t)base & 15)) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)inner * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Psi = Y C on the tensor cores when the context qualifies (every fragment has the same point count P,
 // a multiple of 4; at most 64 orbitals; 16-byte aligned blocks); DC_ERR_ARG otherwise, so that the
@@ -368,19 +382,9 @@ int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s) {
   for (const auto &D : c->h_desc)
     if ((long long)D.E[0] * D.E[1] * D.E[2] != P) return DC_ERR_ARG;
   if ((((uintptr_t)Y) | ((uintptr_t)out)) & 15) return DC_ERR_ARG;
-  const EncodeTiled enc = encode_fn();
-  if (!enc) return DC_ERR_ARG;
-  // the block as rows of P points: dims (P, rows), row stride 4 P bytes, box (128 points, nbm rows)
+  // the block as rows of P points, box (128 points, nbm rows)
   CUtensorMap map;
-  const long long rows = c->layout.psi_elems / P;
-  const cuuint64_t dims[2] = {(cuuint64_t)P, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)P * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)RTM, (cuuint32_t)nbm};
-  const cuuint32_t estr[2] = {1, 1};
-  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(Y), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return DC_ERR_ARG;
+  if (!tensor_map_rows(&map, Y, P, c->layout.psi_elems / P, RTM, nbm, false)) return DC_ERR_ARG;
   RotArgs a;
   a.desc = c->d_desc;
   a.items = c->d_rot_items;
