@@ -662,13 +662,15 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     dc_set_error("mixed-precision Gram needs n <= 64 orbitals per fragment");
     return DC_ERR_ARG;
   }
-  // raw tiles by TMA when every fragment has the same point count P (a multiple of 4): the blocks are
-  // then rows of P points, and a tile is two 32-point boxes of nb rows per array
+  // raw tiles by TMA when every fragment has the same point count P (a multiple of 4) and the same
+  // orbital count: the blocks are then rows of P points, and a tile is two 32-point boxes of nb rows per
+  // array.  (With uneven orbital counts a box of the largest count would also carry the next fragment's
+  // rows: on the water cell that cost 19% more Gram time than the per-row copies.)
   CUtensorMap mY{}, mZ{};
   bool tma = c->h_desc.size() > 0;
   const long long P0 = tma ? (long long)c->h_desc[0].E[0] * c->h_desc[0].E[1] * c->h_desc[0].E[2] : 0;
   for (const auto &D : c->h_desc)
-    if ((long long)D.E[0] * D.E[1] * D.E[2] != P0) tma = false;
+    if ((long long)D.E[0] * D.E[1] * D.E[2] != P0 || D.norb != nmax) tma = false;
   tma = tma && (P0 & 3) == 0 && c->gram_chunk % TKT == 0;
   if (tma) {
     const long long rows = c->layout.psi_elems / P0;

@@ -215,6 +215,30 @@ def test_subspace_and_one_chefsi_pass_fp32(case, kind):
     assert np.max(np.abs(e1 - eps_1)) < 2e-5 * max(1.0, np.max(np.abs(eps_1))), shape
 
 
+@pytest.mark.parametrize("case", ["si8", "water_auto", "water32"])
+def test_one_chefsi_pass_mixed(case):
+    """One filtered pass in mixed precision against the FP64 oracle: the tensor-core Gram (its raw tiles by
+    TMA, since every fragment has the same point count) and the tensor-core rotation, with uneven orbital
+    counts per fragment in the water_auto case (orbital blocks of different widths in one launch) and 32^3
+    fragments in water32."""
+    cfg = (CASES[case] if case in CASES else CASES_EXTRA[case])(precision="mixed")
+    st = oracle_state(cfg)
+    V = st.veff(st.rho_in)
+    st.initial_rr(V)
+    st.solve(V, 1)
+    eps_1 = pack(st, st.eps)
+    with _solver(cfg) as s:
+        _, rho0 = s.initial()
+        s.potential(rho0)
+        s.subspace()
+        s.chefsi(1)
+        _, e1 = s.get_state()
+        e1 = _np(e1)
+    if case == "water_auto":
+        assert len(set(int(v) for v in st.norb)) > 1  # the case does have uneven orbital counts
+    assert np.max(np.abs(e1 - eps_1)) < 2e-5 * max(1.0, np.max(np.abs(eps_1)))
+
+
 @pytest.fixture(scope="module")
 def si8_oracle_run():
     cfg = workloads.make_config("si8")
