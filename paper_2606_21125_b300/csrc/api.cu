@@ -77,7 +77,7 @@ void free_ctx(dc_ctx *c) {
                   c->d_C32, c->d_flags, c->d_scalar, c->d_partials, c->d_gram_items, c->d_rot_items, c->d_Fn,
                   c->d_items2, c->d_row_beg, c->d_row_ent, c->d_row_split, c->d_nl_bound, c->d_rot2_items,
                   c->d_atom_slot_beg, c->d_atom_slots, c->d_slot_w, c->d_adj_vf64, c->d_adj_vf32, c->d_adj_fd,
-                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_q_x, c->d_occ_x, c->d_aux, c->d_frag_order, c->d_rhof, c->d_vcore};
+                  c->d_dots, c->d_ig2, c->d_kerkw, c->d_rhoinG, c->d_cplxh, c->d_fftr, c->d_q_x, c->d_occ_x, c->d_aux, c->d_frag_order, c->d_rhof, c->d_vcore};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->h_scalar_pinned) cudaFreeHost(c->h_scalar_pinned);
@@ -93,7 +93,11 @@ void free_ctx(dc_ctx *c) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->prof_free) cudaEventDestroy(e);
-  if (c->have_plan) cufftDestroy(c->plan_z2z);
+  if (c->have_plan) {
+    cufftDestroy(c->plan_z2z);
+    cufftDestroy(c->plan_d2z);
+    cufftDestroy(c->plan_z2d);
+  }
   cudaGetLastError();
   delete c;
 }
@@ -197,30 +201,32 @@ struct StageModel {
   int launches;
 };
 StageModel potential_model(const dc_ctx *c, bool save_spectrum) {
-  const double N = (double)c->npts;
+  const double N = (double)c->npts, NH = (double)c->nh;
+  (void)save_spectrum;
   if (c->params.hxc != DC_HXC_HARTREE_X) return {16.0 * N, 1};  // k_veff: V_loc in, V_eff out
-  // k_real_to_cplx 24N, forward FFT 32N, [spectrum copy 32N], k_poisson_scale 40N, inverse FFT 32N,
-  // k_veff (V_loc, spectrum, rho in; V_eff out) 40N
-  return {(168.0 + (save_spectrum ? 32.0 : 0.0)) * N, 3};
+  // real-to-complex FFT 8N + 16NH, k_poisson_scale 40NH, complex-to-real FFT 16NH + 8N, k_veff (V_loc,
+  // V_H, rho in; V_eff out) 32N
+  return {48.0 * N + 72.0 * NH, 2};
 }
 StageModel energy_model(const dc_ctx *c, bool spectrum_difference) {
-  const double N = (double)c->npts, ns = (double)c->layout.nstates;
+  const double N = (double)c->npts, NH = (double)c->nh, ns = (double)c->layout.nstates;
   // band sum (occ, eps, q) and entropy (occ, q) over the states; <V, rho_out>, E_x, |rho_out - rho_in|
   // and int rho_out over the grid; every reduction is two launches (block partials, final sum)
   double b = 40.0 * ns + 48.0 * N;
   int nk = 12 + 1;  // + k_energy_combine
   if (c->params.hxc == DC_HXC_HARTREE_X) {
-    b += (24.0 + 32.0 + 40.0) * N;  // k_real_to_cplx, forward FFT, E_es reduction (spectra, 1/G^2)
-    nk += 1 + 2;
+    // real-to-complex FFT; E_es reduction (half spectrum, 1/G^2, the ion spectrum at G and at -G)
+    b += 8.0 * N + 16.0 * NH + 56.0 * NH;
+    nk += 2;
   }
   // mixing
   if (!(c->params.kerker_q0 > 0.0)) {
     b += 24.0 * N;  // k_mix
     nk += 1;
   } else {
-    // residual spectrum: k_sub_cplx 48N, or k_residual_cplx 32N + forward FFT 32N; then k_kerker 40N,
-    // inverse FFT 32N, k_add_real 32N
-    b += (spectrum_difference ? 48.0 : 64.0) * N + 104.0 * N;
+    // residual spectrum: k_sub_cplx 48NH, or k_residual 24N + real-to-complex FFT 8N + 16NH; then
+    // k_kerker 40NH, complex-to-real FFT 16NH + 8N, k_add_real 24N
+    b += (spectrum_difference ? 48.0 * NH : 32.0 * N + 16.0 * NH) + 56.0 * NH + 32.0 * N;
     nk += 3;
   }
   return {b, nk};
@@ -717,12 +723,23 @@ static int dc_init_impl(const dc_grid_t *grid, const dc_fragments_t *fragments, 
   DC_TRY(dmalloc(&c->d_veff, N));
   DC_TRY(dmalloc(&c->d_rho_out, N));
   DC_TRY(dmalloc(&c->d_work, N));
+  c->nh = (long long)c->grid.n[2] * c->grid.n[1] * (c->grid.n[0] / 2 + 1);
+  const size_t NH = (size_t)c->nh;
   DC_TRY(dmalloc(&c->d_rhoiG, N));
-  DC_TRY(dmalloc(&c->d_ig2, N));
-  DC_TRY(dmalloc(&c->d_kerkw, N));
-  DC_TRY(dmalloc(&c->d_rhoinG, N));
+  DC_TRY(dmalloc(&c->d_ig2, NH));
+  DC_TRY(dmalloc(&c->d_kerkw, NH));
+  DC_TRY(dmalloc(&c->d_rhoinG, NH));
   DC_TRY(dmalloc(&c->d_cplx, N));
-  if (cufftPlan3d(&c->plan_z2z, c->grid.n[2], c->grid.n[1], c->grid.n[0], CUFFT_Z2Z) != CUFFT_SUCCESS) {
+  DC_TRY(dmalloc(&c->d_cplxh, NH));
+  DC_TRY(dmalloc(&c->d_fftr, N));
+  const int *gn = c->grid.n;
+  if (cufftPlan3d(&c->plan_z2z, gn[2], gn[1], gn[0], CUFFT_Z2Z) != CUFFT_SUCCESS) {
+    dc_set_error("cufftPlan3d failed");
+    return DC_ERR_CUDA;
+  }
+  if (cufftPlan3d(&c->plan_d2z, gn[2], gn[1], gn[0], CUFFT_D2Z) != CUFFT_SUCCESS ||
+      cufftPlan3d(&c->plan_z2d, gn[2], gn[1], gn[0], CUFFT_Z2D) != CUFFT_SUCCESS) {
+    cufftDestroy(c->plan_z2z);
     dc_set_error("cufftPlan3d failed");
     return DC_ERR_CUDA;
   }

@@ -120,12 +120,17 @@ struct dc_ctx {
 
   // global grid arrays (FP64)
   double *d_vion = nullptr, *d_rho0 = nullptr, *d_veff = nullptr, *d_rho_out = nullptr, *d_work = nullptr;
+  // Spectra: the per-step transforms are real-to-complex, on the half grid [nz][ny][nx/2 + 1] ("h");
+  // the starting potential and density (once per context) use the full complex grid.
+  long long nh = 0;            // half-grid points
   double2 *d_rhoiG = nullptr;  // rho_ion(G), full complex grid
-  double *d_ig2 = nullptr;     // 1/G^2 per grid index (0 at G = 0), set once
-  double *d_kerkw = nullptr;   // Kerker weight alpha G^2/(G^2 + q0^2)/N per grid index, set once
-  double2 *d_rhoinG = nullptr; // the step's input density in G space (unnormalised forward FFT)
+  double *d_ig2 = nullptr;     // 1/G^2 per half-grid index (0 at G = 0), set once
+  double *d_kerkw = nullptr;   // Kerker weight alpha G^2/(G^2 + q0^2)/N per half-grid index, set once
+  double2 *d_rhoinG = nullptr; // the step's input density on the half grid (unnormalised forward FFT)
   double2 *d_cplx = nullptr;   // FFT work (full complex grid)
-  cufftHandle plan_z2z = 0;
+  double2 *d_cplxh = nullptr;  // FFT work (half grid)
+  double *d_fftr = nullptr;    // real FFT output (N)
+  cufftHandle plan_z2z = 0, plan_d2z = 0, plan_z2d = 0;
   bool have_plan = false;
 
   // per-fragment-point potential

@@ -8,11 +8,13 @@ namespace {
 
 __device__ __forceinline__ int fft_freq(int g, int N) { return g < (N + 1) / 2 ? g : g - N; }
 
-__device__ __forceinline__ double gsq(long long idx, int nx, int ny, int nz, double Lx, double Ly, double Lz,
+// G of grid index idx in a layout whose rows hold nxl x-entries: nxl = nx (full grid) or nx/2 + 1 (the
+// half grid of a real-to-complex transform, x = 0 .. nx/2)
+__device__ __forceinline__ double gsq(long long idx, int nxl, int nx, int ny, int nz, double Lx, double Ly, double Lz,
                                       double *gx, double *gy, double *gz) {
-  const int x = (int)(idx % nx);
-  const int y = (int)((idx / nx) % ny);
-  const int z = (int)(idx / ((long long)nx * ny));
+  const int x = (int)(idx % nxl);
+  const int y = (int)((idx / nxl) % ny);
+  const int z = (int)(idx / ((long long)nxl * ny));
   *gx = 2.0 * M_PI * fft_freq(x, nx) / Lx;
   *gy = 2.0 * M_PI * fft_freq(y, ny) / Ly;
   *gz = 2.0 * M_PI * fft_freq(z, nz) / Lz;
@@ -20,13 +22,13 @@ __device__ __forceinline__ double gsq(long long idx, int nx, int ny, int nz, dou
 }
 
 // rho_ion(G) = (1/Omega) sum_a Z_a exp(-G^2 sigma_a^2/2) exp(-i G.R_a)  (Gaussian ion charges)
-__global__ void k_rho_ion_G(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz, int natom,
-                            const double *pos, const int *species, const double *spec, int nspecies, double volume,
-                            double2 *out) {
+__global__ void k_rho_ion_G(long long npts, int nxl, int nx, int ny, int nz, double Lx, double Ly, double Lz,
+                            int natom, const double *pos, const int *species, const double *spec, int nspecies,
+                            double volume, double2 *out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= npts) return;
   double gx, gy, gz;
-  const double g2 = gsq(idx, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
+  const double g2 = gsq(idx, nxl, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
   double re = 0.0, im = 0.0;
   for (int a = 0; a < natom; ++a) {
     const int s = species[a];
@@ -41,17 +43,29 @@ __global__ void k_rho_ion_G(long long npts, int nx, int ny, int nz, double Lx, d
   out[idx] = make_double2(re / volume, im / volume);
 }
 
-// out(G) = scale(G) * in(G) with scale = f/G^2 (0 at G=0)
-// The G-dependent factors of the reciprocal-space stages, fixed for a context: 1/G^2 (0 at G = 0)
-// and the Kerker weight alpha G^2/(G^2 + q0^2), divided by N for the unnormalised inverse transform.
-__global__ void k_gtables(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
-                          double q0sq, double *ig2, double *kw) {
+// The G-dependent factors of the per-step reciprocal-space stages on the half grid, fixed for a context:
+// 1/G^2 (0 at G = 0) and the Kerker weight alpha G^2/(G^2 + q0^2), divided by N (the full grid's point
+// count) for the unnormalised inverse transform.
+__global__ void k_gtables(long long nh, int nx, int ny, int nz, double Lx, double Ly, double Lz, double alpha,
+                          double q0sq, long long npts, double *ig2, double *kw) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nh) return;
+  double gx, gy, gz;
+  const double g2 = gsq(idx, nx / 2 + 1, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
+  ig2[idx] = g2 > 0.0 ? 1.0 / g2 : 0.0;
+  kw[idx] = alpha * g2 / (g2 + q0sq) / (double)npts;
+}
+
+// V_loc(G) = -4 pi rho_ion(G) / G^2 (0 at G = 0) on the full grid
+__global__ void k_vloc_G(long long npts, int nx, int ny, int nz, double Lx, double Ly, double Lz, const double2 *in,
+                         double2 *out) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= npts) return;
   double gx, gy, gz;
-  const double g2 = gsq(idx, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
-  ig2[idx] = g2 > 0.0 ? 1.0 / g2 : 0.0;
-  kw[idx] = alpha * g2 / (g2 + q0sq) / (double)npts;
+  const double g2 = gsq(idx, nx, nx, ny, nz, Lx, Ly, Lz, &gx, &gy, &gz);
+  const double sc = g2 > 0.0 ? -4.0 * M_PI / g2 : 0.0;
+  const double2 v = in[idx];
+  out[idx] = make_double2(sc * v.x, sc * v.y);
 }
 
 __global__ void k_poisson_scale(long long npts, const double *ig2, const double2 *in, double factor, double2 *out) {
@@ -60,11 +74,6 @@ __global__ void k_poisson_scale(long long npts, const double *ig2, const double2
   const double2 v = in[idx];
   const double s = factor * ig2[idx];
   out[idx] = make_double2(s * v.x, s * v.y);
-}
-
-__global__ void k_real_to_cplx(long long n, const double *in, double2 *out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_double2(in[i], 0.0);
 }
 
 __global__ void k_cplx_real(long long n, const double2 *in, double scale, double *out) {
@@ -85,13 +94,13 @@ __global__ void k_scale(long long n, double *x, const double *num, double den_sc
 
 // V_eff = V_loc + V_H + v_x[rho]  (vh holds the unnormalised inverse transform, scaled by 1/N); with
 // with_x = 0 the exchange is left to the per-fragment gather (Eq. 5, V_xc[rho_alpha])
-__global__ void k_veff(long long n, const double *vion, const double2 *vh, double inv_n, const double *rho, int hxc,
+__global__ void k_veff(long long n, const double *vion, const double *vh, double inv_n, const double *rho, int hxc,
                        int with_x, double *veff) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double v = vion[i];
   if (hxc == DC_HXC_HARTREE_X) {
-    v += vh[i].x * inv_n;
+    v += vh[i] * inv_n;
     if (with_x) v -= cbrt(3.0 * fmax(rho[i], 0.0) / M_PI);
   }
   veff[i] = v;
@@ -248,13 +257,31 @@ struct FnEntropy {
     return -2.0 * q[i] * t;
   }
 };
-struct FnEs {  // 4 pi |rho(G)/N - rho_ion(G)|^2 / G^2 for G != 0 (ig2 = 1/G^2, 0 at G = 0)
+// 4 pi |rho(G)/N - rho_ion(G)|^2 / G^2 for G != 0 (ig2 = 1/G^2, 0 at G = 0), summed over the full grid from
+// the half spectrum rG of the real field rho: an entry with 0 < x < nx/2 also stands for its partner
+// -G = (nx - x, -y, -z), where rho(-G) = conj rho(G).  The analytic ion spectrum iG (full grid) is not
+// conjugate-paired on the y and z Nyquist planes, so the partner's rho_ion is read, not inferred.
+struct FnEs {
   const double2 *rG, *iG;
   const double *ig2;
   double inv_n;
+  int nx, ny, nz;
   __device__ double operator()(long long i) const {
-    const double re = rG[i].x * inv_n - iG[i].x, im = rG[i].y * inv_n - iG[i].y;
-    return 4.0 * M_PI * (re * re + im * im) * ig2[i];
+    const int nxh = nx / 2 + 1;
+    const int x = (int)(i % nxh);
+    const long long yz = i / nxh;
+    const int y = (int)(yz % ny), z = (int)(yz / ny);
+    const double2 r = rG[i];
+    const double2 a = iG[((long long)z * ny + y) * nx + x];
+    const double ar = r.x * inv_n - a.x, ai = r.y * inv_n - a.y;
+    double t = ar * ar + ai * ai;
+    if (x != 0 && 2 * x != nx) {
+      const int yp = y == 0 ? 0 : ny - y, zp = z == 0 ? 0 : nz - z;
+      const double2 b = iG[((long long)zp * ny + yp) * nx + (nx - x)];
+      const double br = r.x * inv_n - b.x, bi = -r.y * inv_n - b.y;
+      t += br * br + bi * bi;
+    }
+    return 4.0 * M_PI * t * ig2[i];
   }
 };
 
@@ -271,9 +298,9 @@ __global__ void k_mix(long long n, double *rho_in, const double *rho_out, double
   if (i < n) rho_in[i] = rho_in[i] + alpha * (rho_out[i] - rho_in[i]);
 }
 
-__global__ void k_residual_cplx(long long n, const double *rho_out, const double *rho_in, double2 *out) {
+__global__ void k_residual(long long n, const double *rho_out, const double *rho_in, double *out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = make_double2(rho_out[i] - rho_in[i], 0.0);
+  if (i < n) out[i] = rho_out[i] - rho_in[i];
 }
 
 // Kerker weight (tabulated: alpha G^2/(G^2+q0^2)/N for the unnormalised inverse transform)
@@ -290,9 +317,9 @@ __global__ void k_sub_cplx(long long n, const double2 *b, double2 *a) {
   if (i < n) a[i] = make_double2(a[i].x - b[i].x, a[i].y - b[i].y);
 }
 
-__global__ void k_add_real(long long n, double *rho_in, const double2 *d) {
+__global__ void k_add_real(long long n, double *rho_in, const double *d) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) rho_in[i] += d[i].x;
+  if (i < n) rho_in[i] += d[i];
 }
 
 inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -307,6 +334,35 @@ int fft(dc_ctx *c, double2 *data, int dir) {
   return DC_OK;
 }
 
+// Real field (N) -> its half spectrum (out of place; the input is left as it is)
+int fft_r2c(dc_ctx *c, const double *in, double2 *out) {
+  if (cufftExecD2Z(c->plan_d2z, const_cast<double *>(in), reinterpret_cast<cufftDoubleComplex *>(out)) !=
+      CUFFT_SUCCESS) {
+    dc_set_error("cufftExecD2Z failed");
+    return DC_ERR_CUDA;
+  }
+  return DC_OK;
+}
+
+// Half spectrum -> real field (unnormalised; out of place, the spectrum is overwritten)
+int fft_c2r(dc_ctx *c, double2 *in, double *out) {
+  if (cufftExecZ2D(c->plan_z2d, reinterpret_cast<cufftDoubleComplex *>(in), out) != CUFFT_SUCCESS) {
+    dc_set_error("cufftExecZ2D failed");
+    return DC_ERR_CUDA;
+  }
+  return DC_OK;
+}
+
+int fft_streams(dc_ctx *c, cudaStream_t s) {
+  const bool ok = cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS && cufftSetStream(c->plan_d2z, s) == CUFFT_SUCCESS &&
+                  cufftSetStream(c->plan_z2d, s) == CUFFT_SUCCESS;
+  if (!ok) {
+    dc_set_error("cufftSetStream failed");
+    return DC_ERR_CUDA;
+  }
+  return DC_OK;
+}
+
 }  // namespace
 
 namespace dck {
@@ -315,14 +371,16 @@ int launch_vion(dc_ctx *c, cudaStream_t s) {
   const long long N = c->npts;
   const int *n = c->grid.n;
   const double *L = c->grid.L;
-  DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
-  k_gtables<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->params.mix_alpha,
-                                    c->params.kerker_q0 * c->params.kerker_q0, c->d_ig2, c->d_kerkw);
-  k_rho_ion_G<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->natom, c->d_atom_pos,
+  const long long NH = c->nh;
+  DC_TRY(fft_streams(c, s));
+  k_gtables<<<nblk(NH), 256, 0, s>>>(NH, n[0], n[1], n[2], L[0], L[1], L[2], c->params.mix_alpha,
+                                     c->params.kerker_q0 * c->params.kerker_q0, N, c->d_ig2, c->d_kerkw);
+  k_rho_ion_G<<<nblk(N), 256, 0, s>>>(N, n[0], n[0], n[1], n[2], L[0], L[1], L[2], c->natom, c->d_atom_pos,
                                       c->d_atom_species, c->d_species, c->nspecies, c->volume, c->d_rhoiG);
   DC_CUDA(cudaGetLastError());
-  // V_loc(G) = -4 pi rho_ion(G)/G^2 ; V_loc(r) = Re sum_G V(G) e^{iG.r}
-  k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, c->d_ig2, c->d_rhoiG, -4.0 * M_PI, c->d_cplx);
+  // V_loc(G) = -4 pi rho_ion(G)/G^2 ; V_loc(r) = Re sum_G V(G) e^{iG.r}.  The analytic spectrum's
+  // Nyquist planes are not conjugate-paired, so this once-per-context stage keeps the full transform.
+  k_vloc_G<<<nblk(N), 256, 0, s>>>(N, n[0], n[1], n[2], L[0], L[1], L[2], c->d_rhoiG, c->d_cplx);
   DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
   k_cplx_real<<<nblk(N), 256, 0, s>>>(N, c->d_cplx, 1.0, c->d_vion);
   // starting density: max(Re sum_G rho_ion(G) e^{iG.r}, 0) scaled to N_e
@@ -338,18 +396,17 @@ int launch_vion(dc_ctx *c, cudaStream_t s) {
 
 int launch_potential(dc_ctx *c, const double *rho, cudaStream_t s, double2 *save_rhoG, bool with_fragment_xc) {
   const long long N = c->npts;
-  const int *n = c->grid.n;
-  const double *L = c->grid.L;
-  DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
   if (c->params.hxc == DC_HXC_HARTREE_X) {
-    k_real_to_cplx<<<nblk(N), 256, 0, s>>>(N, rho, c->d_cplx);
-    DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
-    if (save_rhoG) DC_CUDA(cudaMemcpyAsync(save_rhoG, c->d_cplx, sizeof(double2) * N, cudaMemcpyDeviceToDevice, s));
-    k_poisson_scale<<<nblk(N), 256, 0, s>>>(N, c->d_ig2, c->d_cplx, 4.0 * M_PI, c->d_cplx);
-    DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
+    const long long NH = c->nh;
+    DC_TRY(fft_streams(c, s));
+    // rho(G) on the half grid, kept in save_rhoG when the mixing stage wants it
+    double2 *spec = save_rhoG ? save_rhoG : c->d_cplxh;
+    DC_TRY(fft_r2c(c, rho, spec));
+    k_poisson_scale<<<nblk(NH), 256, 0, s>>>(NH, c->d_ig2, spec, 4.0 * M_PI, c->d_cplxh);
+    DC_TRY(fft_c2r(c, c->d_cplxh, c->d_fftr));
   }
   const int with_x = c->params.xc_fragment && with_fragment_xc ? 0 : 1;
-  k_veff<<<nblk(N), 256, 0, s>>>(N, c->d_vion, c->d_cplx, 1.0 / (double)N, rho, c->params.hxc, with_x, c->d_veff);
+  k_veff<<<nblk(N), 256, 0, s>>>(N, c->d_vion, c->d_fftr, 1.0 / (double)N, rho, c->params.hxc, with_x, c->d_veff);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
@@ -384,7 +441,6 @@ int launch_gather_plain(dc_ctx *c, const double *V, double *vf64, float *vf32, c
 int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s) {
   const long long N = c->npts;
   const int *n = c->grid.n;
-  const double *L = c->grid.L;
   double *sc = c->d_scalar;
   const long long ns = c->layout.nstates;
   DC_TRY(reduce(FnBand{c->d_occ, c->d_eps, c->d_q}, ns, 1.0, sc + 1, c->d_partials, s));
@@ -395,18 +451,17 @@ int launch_energy(dc_ctx *c, const double *rho_in, cudaStream_t s) {
   DC_TRY(reduce(FnAbsDiff{c->d_rho_out, rho_in}, N, c->dV / c->ne, sc + 5, c->d_partials, s));
   DC_TRY(reduce(FnSum{c->d_rho_out}, N, c->dV, sc + 6, c->d_partials, s));
   if (c->params.hxc == DC_HXC_HARTREE_X) {
-    DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
-    k_real_to_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, c->d_cplx);
-    DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
-    FnEs fe{c->d_cplx, c->d_rhoiG, c->d_ig2, 1.0 / (double)N};
-    DC_TRY(reduce(fe, N, 0.5 * c->volume, sc + 3, c->d_partials, s));
+    DC_TRY(fft_streams(c, s));
+    DC_TRY(fft_r2c(c, c->d_rho_out, c->d_cplxh));
+    FnEs fe{c->d_cplxh, c->d_rhoiG, c->d_ig2, 1.0 / (double)N, n[0], n[1], n[2]};
+    DC_TRY(reduce(fe, c->nh, 0.5 * c->volume, sc + 3, c->d_partials, s));
   }
   k_energy_combine<<<1, 1, 0, s>>>(sc, c->params.hxc, c->params.kT);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
 
-// rho_in_G: the spectrum of rho_in from this step's potential stage, with c->d_cplx still holding the
+// rho_in_G: the half spectrum of rho_in from this step's potential stage, with c->d_cplxh still holding the
 // energy stage's spectrum of rho_out; the residual's spectrum is then their difference (linearity of
 // the transform) and its forward transform is skipped.  nullptr: transform the residual.
 int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s, const double2 *rho_in_G) {
@@ -417,18 +472,17 @@ int launch_mix(dc_ctx *c, double *rho_in, cudaStream_t s, const double2 *rho_in_
     DC_CUDA(cudaGetLastError());
     return DC_OK;
   }
-  const int *n = c->grid.n;
-  const double *L = c->grid.L;
-  DC_CUDA(cufftSetStream(c->plan_z2z, s) == CUFFT_SUCCESS ? cudaSuccess : cudaErrorUnknown);
+  const long long NH = c->nh;
+  DC_TRY(fft_streams(c, s));
   if (rho_in_G) {
-    k_sub_cplx<<<nblk(N), 256, 0, s>>>(N, rho_in_G, c->d_cplx);
+    k_sub_cplx<<<nblk(NH), 256, 0, s>>>(NH, rho_in_G, c->d_cplxh);
   } else {
-    k_residual_cplx<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, rho_in, c->d_cplx);
-    DC_TRY(fft(c, c->d_cplx, CUFFT_FORWARD));
+    k_residual<<<nblk(N), 256, 0, s>>>(N, c->d_rho_out, rho_in, c->d_fftr);
+    DC_TRY(fft_r2c(c, c->d_fftr, c->d_cplxh));
   }
-  k_kerker<<<nblk(N), 256, 0, s>>>(N, c->d_kerkw, c->d_cplx);
-  DC_TRY(fft(c, c->d_cplx, CUFFT_INVERSE));
-  k_add_real<<<nblk(N), 256, 0, s>>>(N, rho_in, c->d_cplx);
+  k_kerker<<<nblk(NH), 256, 0, s>>>(NH, c->d_kerkw, c->d_cplxh);
+  DC_TRY(fft_c2r(c, c->d_cplxh, c->d_fftr));
+  k_add_real<<<nblk(N), 256, 0, s>>>(N, rho_in, c->d_fftr);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
