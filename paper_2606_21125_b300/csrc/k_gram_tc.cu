@@ -7,15 +7,18 @@
 //   S = hh + hm + mh + hl + lh + mm            (lh = (hl)^T by symmetry)
 //   A = h.zh + h.zm + m.zh + h.zl + l.zh + m.zm (z = HY split the same way)
 // Persistent CTAs (one per SM, 16 warps) walk the (fragment, 4096-point item) list as a warp-
-// specialised pipeline.  Seven converter warps copy 64-point K-tiles of Y and HY into a ring of
-// raw FP32 tiles in shared memory (cp.async, 16 bytes per copy, up to three tiles ahead; each
-// thread later converts exactly the chunks it copied, so a per-thread wait is enough), split them
-// into BF16 rows in a ring of shared-memory stages (K-major, no-swizzle canonical layout) and arrive
-// on the stage's `full` barrier; one thread of warp 15 waits on it and issues five MMAs per 16-point
-// K-step (rows [h; m] of a 128-row operand whose remaining rows are the first l rows):
-//   S_h = [h; m] h^T,  A_h = [h; m] zh^T                  (the large terms, N = nb)
-//   S_r = [h; m] [m | l]^T,  A_r = [h; m] [zm | zl]^T     (N = 2 nb),  L = [l; 0] zh^T   (N = nb)
-// and commits them to the stage's `empty` barrier, which frees it for the converters.  The FP32
+// specialised pipeline.  Seven converter warps bring 64-point K-tiles of Y and HY into a ring of
+// raw FP32 tiles in shared memory (by TMA when the fragments share one shape, else by cp.async),
+// split them into BF16 rows of a ring of shared-memory stages (K-major, no-swizzle canonical layout,
+// rows [zh | h | m | l | zm | zl], nb each, then zero rows) and arrive on the stage's `full` barrier;
+// one thread of warp 15 waits on it and issues three MMAs per 16-point K-step, the A operand being the
+// 128 rows from h ([h; m] and the first l rows) or from l:
+//   [A_h | S_h] = [h; m] [zh | h]^T                        (the large terms, N = 2 nb)
+//   [S_r | A_r] = [h; m] [m | l | zm | zl]^T               (N = 4 nb)
+//   L           = [l; ...] zh^T                            (N = nb, only the l rows are read)
+// and commits them to the stage's `empty` barrier, which frees it for the converters.  (Five MMAs per
+// K-step, one per block, re-read the 128-row A operand five times: on Si512 the MMA issue took ~1,360
+// of a ~2,800-cycle tile period.)  The FP32
 // accumulators in tensor memory are drained into FP32 sums kept in the registers of warps 7-14 (two
 // warps per tensor-memory lane group, half the columns each): the large set every 256 points (the
 // rounding of a tensor-memory sum grows with its length) from two alternating buffers, so that its
@@ -224,14 +227,24 @@ __device__ __forceinline__ void cp_async_wait(int pending) {
   else asm volatile("cp.async.wait_group 2;" ::: "memory");
 }
 
-// Split 4 consecutive-point values of row i into h/m/l rows (base row offsets 0, nb, 2 nb).
-__device__ __forceinline__ void store_split(unsigned char *st, int i, int k, int ks, int nb, float4 v) {
+// Stage rows: [zh | h | m | l | zm | zl] (nb each), then zero rows up to the 128 that an A operand
+// starting at l reads.
+__host__ __device__ constexpr int stage_rows(int nb) { return 6 * nb > 3 * nb + 128 ? 6 * nb : 3 * nb + 128; }
+
+// Split 4 consecutive-point values of one orbital into its three BF16 words, stored in rows rh, rm, rl.
+__device__ __forceinline__ void store_split(unsigned char *st, int rh, int rm, int rl, int k, int ks, float4 v) {
   uint32_t h0, m0, l0, h1, m1, l1;
   split3x2(v.x, v.y, h0, m0, l0);
   split3x2(v.z, v.w, h1, m1, l1);
-  *reinterpret_cast<uint2 *>(st + toff(i, k, ks)) = make_uint2(h0, h1);
-  *reinterpret_cast<uint2 *>(st + toff(nb + i, k, ks)) = make_uint2(m0, m1);
-  *reinterpret_cast<uint2 *>(st + toff(2 * nb + i, k, ks)) = make_uint2(l0, l1);
+  *reinterpret_cast<uint2 *>(st + toff(rh, k, ks)) = make_uint2(h0, h1);
+  *reinterpret_cast<uint2 *>(st + toff(rm, k, ks)) = make_uint2(m0, m1);
+  *reinterpret_cast<uint2 *>(st + toff(rl, k, ks)) = make_uint2(l0, l1);
+}
+
+// Orbital i's value of Y into rows h, m, l and of HY into rows zh, zm, zl.
+__device__ __forceinline__ void store_pair(unsigned char *st, int i, int k, int ks, int nb, float4 y, float4 z) {
+  store_split(st, nb + i, 2 * nb + i, 3 * nb + i, k, ks, y);
+  store_split(st, i, 4 * nb + i, 5 * nb + i, k, ks, z);
 }
 
 // TMA form of the raw ring: each array's K-tile arrives as two 32-point boxes of nbmax rows with the
@@ -241,18 +254,15 @@ __device__ __forceinline__ float4 raw_tma(const unsigned char *slot, int nbmax, 
   return *reinterpret_cast<const float4 *>(slot + ((a * 2 + (kq >> 3)) * nbmax + i) * 128 + (((kq & 7) ^ (i & 7)) << 4));
 }
 
-__device__ __forceinline__ void convert_tile_tma(const unsigned char *slot, int nbmax, unsigned char *ys,
-                                                 unsigned char *zs, int n, int nb, int ksY, int ksZ) {
+__device__ __forceinline__ void convert_tile_tma(const unsigned char *slot, int nbmax, unsigned char *st, int n,
+                                                 int nb, int ks) {
 #pragma unroll
   for (int j = 0; j < TSL; ++j) {
     const int idx = threadIdx.x + j * TCV;
     int i, kq;
     tile_slot(idx, i, kq);
-    if (idx < 1024 && i < n) {
-      const int k = 4 * kq;
-      store_split(ys, i, k, ksY, nb, raw_tma(slot, nbmax, 0, i, kq));
-      store_split(zs, i, k, ksZ, nb, raw_tma(slot, nbmax, 1, i, kq));
-    }
+    if (idx < 1024 && i < n)
+      store_pair(st, i, 4 * kq, ks, nb, raw_tma(slot, nbmax, 0, i, kq), raw_tma(slot, nbmax, 1, i, kq));
   }
 }
 
@@ -264,18 +274,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
       : "memory");
 }
 
-__device__ __forceinline__ void convert_tile(const float4 *raw, int nslots, unsigned char *ys, unsigned char *zs,
-                                             int n, int nb, int ksY, int ksZ) {
+__device__ __forceinline__ void convert_tile(const float4 *raw, int nslots, unsigned char *st, int n, int nb,
+                                             int ks) {
 #pragma unroll
   for (int j = 0; j < TSL; ++j) {
     const int idx = threadIdx.x + j * TCV;
     int i, kq;
     tile_slot(idx, i, kq);
-    if (idx < 1024 && i < n) {
-      const int k = 4 * kq;
-      store_split(ys, i, k, ksY, nb, raw[idx]);
-      store_split(zs, i, k, ksZ, nb, raw[nslots + idx]);
-    }
+    if (idx < 1024 && i < n) store_pair(st, i, 4 * kq, ks, nb, raw[idx], raw[nslots + idx]);
   }
 }
 
@@ -403,7 +409,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   const int warp = tid >> 5;
   const bool mma_warp = warp == TNT / 32 - 1;
   const int nbmax = (nmax + 15) & ~15;
-  const int stage_max = (2 * nbmax + 128) * TKT * 2 + 3 * nbmax * TKT * 2;
+  const int stage_max = stage_rows(nbmax) * TKT * 2;
   const int nslots = ((nmax + 7) / 8) * 128;                          // raw float4 slots per array
   float4 *rawring = reinterpret_cast<float4 *>(sm + nstages * stage_max);  // [nraw][2][nslots]
   // [5][n][n + 1] FP32 item sums.  They share the raw ring's space: the drains write them only after
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
   int gb = 0;     // large-set drain groups of this CTA (buffer gb % nbuf, its use gb / nbuf)
   int gs = 0;     // small-set drains of this CTA
   // tensor-memory columns (blocks sized for the largest orbital count): nbuf large-set buffers of
-  // [S_h | A_h] (2 nbmax columns each), then S_r and A_r (2 nbmax each) and L (nbmax)
+  // [A_h | S_h] (2 nbmax columns each), then [S_r | A_r] (4 nbmax) and L (nbmax)
   const int nbuf = 9 * nbmax <= TMEM_COLS ? 2 : 1;
   int prev_n = -1;
   int commits = 0;  // MMA groups committed by the MMA thread (tracked for the final wait)
@@ -458,15 +464,13 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
     const long long P = (long long)D.E[0] * D.E[1] * D.E[2];
     const long long p0 = (long long)ch * chunk;
     const long long p1 = min(P, p0 + chunk);
-    const int Ry = 2 * nb + 128, Rz = 3 * nb;
-    const int ksY = (Ry / 8) * 128, ksZ = (Rz / 8) * 128;
-    const int ybytes = Ry * TKT * 2, zbytes = Rz * TKT * 2;
-    const int stage_bytes = ybytes + zbytes;
+    const int ks = (stage_rows(nb) / 8) * 128;  // bytes per 8-point K column of a stage
+    const int stage_bytes = stage_rows(nb) * TKT * 2;
     const float *Yf = Y + D.psi_off;
     const float *Zf = HY + D.psi_off;
     const bool vec = ((P | D.psi_off) & 3) == 0;
-    const uint32_t tSr = tbase + 2 * nbuf * nbmax, tAr = tSr + 2 * nbmax, tL = tAr + 2 * nbmax;
-    const uint32_t iN1 = idesc_bf16(128, nb), iN2 = idesc_bf16(128, 2 * nb);
+    const uint32_t tSr = tbase + 2 * nbuf * nbmax, tAr = tSr + 2 * nb, tL = tSr + 4 * nbmax;
+    const uint32_t iN1 = idesc_bf16(128, nb), iN2 = idesc_bf16(128, 2 * nb), iN4 = idesc_bf16(128, 4 * nb);
     const int ntiles = (int)((p1 - p0 + TKT - 1) / TKT);
 
     // item start (the whole CTA is here, no MMA in flight): stage padding rows zero for this orbital
@@ -508,9 +512,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         const uint32_t ruse = (uint32_t)((gr + t) / nraw);
         if (!mbar_wait_or(&rfull[r], ruse & 1u, &timed_out)) break;
         if (!mbar_wait_or(&empty[s], (use & 1u) ^ 1u, &timed_out)) break;
-        unsigned char *ys = sm + s * stage_bytes;
-        unsigned char *zs = ys + ybytes;
-        convert_tile_tma(rbase + (size_t)r * rslot, nbmax, ys, zs, n, nb, ksY, ksZ);
+        convert_tile_tma(rbase + (size_t)r * rslot, nbmax, sm + s * stage_bytes, n, nb, ks);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&full[s]);
         mbar_arrive(&rempty[r]);
@@ -533,9 +535,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         float4 *raw = rawring + (size_t)(t % nraw) * 2 * nslots;
         cp_async_wait(nraw - 1);  // this thread's chunks of tile t have landed
         if (!mbar_wait_or(&empty[s], (use & 1u) ^ 1u, &timed_out)) break;
-        unsigned char *ys = sm + s * stage_bytes;
-        unsigned char *zs = ys + ybytes;
-        convert_tile(raw, nslots, ys, zs, n, nb, ksY, ksZ);
+        convert_tile(raw, nslots, sm + s * stage_bytes, n, nb, ks);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&full[s]);
         // the slot's values are in the stage now: refill it with tile t + nraw
@@ -555,7 +555,7 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         const int bb = gb % nbuf, bu = gb / nbuf;
         if (!mbar_wait_or(&dready_b[bb], (uint32_t)(bu & 1), &timed_out)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        drain_big<NG>(R, tbase + 2 * bb * nbmax, tbase + 2 * bb * nbmax + nbmax, n, nb);
+        drain_big<NG>(R, tbase + 2 * bb * nbmax + nb, tbase + 2 * bb * nbmax, n, nb);  // S_h, A_h
         asm volatile("tcgen05.fence::before_thread_sync;");
         mbar_arrive(&ddone_b[bb]);
         ++gb;
@@ -582,29 +582,23 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
         if (wstart && gs > 0 && !mbar_wait_or(&ddone_s, (uint32_t)((gs - 1) & 1), &timed_out)) break;
         if (!mbar_wait_or(&full[s], use & 1u, &timed_out)) break;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        unsigned char *ys = sm + s * stage_bytes;
-        unsigned char *zs = ys + ybytes;
-        const uint32_t ya = su32(ys), za = su32(zs);
-        const uint32_t tSh = tbase + 2 * bb * nbmax, tAh = tSh + nbmax;
-        // the five operand descriptors of K-step 0; a K-step of 16 points advances each start address by
+        const uint32_t sa = su32(sm + s * stage_bytes);
+        const uint32_t tAh = tbase + 2 * bb * nbmax;  // [A_h | S_h]
+        // the four operand descriptors of K-step 0; a K-step of 16 points advances each start address by
         // two core-matrix columns (the start field counts 16-byte units)
-        const uint64_t dY = sdesc(ya, ksY, 128);                          // rows h, m, l
-        const uint64_t dYr = sdesc(ya + (nb / 8) * 128, ksY, 128);        // rows m, l
-        const uint64_t dL = sdesc(ya + (2 * nb / 8) * 128, ksY, 128);     // rows l, 0
-        const uint64_t dZ = sdesc(za, ksZ, 128);                          // rows zh, ...
-        const uint64_t dZr = sdesc(za + (nb / 8) * 128, ksZ, 128);        // rows zm, zl
-        const uint64_t stY = (uint64_t)((2 * ksY) >> 4), stZ = (uint64_t)((2 * ksZ) >> 4);
+        const uint64_t dA = sdesc(sa + (nb / 8) * 128, ks, 128);      // A: 128 rows from h
+        const uint64_t dAL = sdesc(sa + (3 * nb / 8) * 128, ks, 128); // A: 128 rows from l
+        const uint64_t dB1 = sdesc(sa, ks, 128);                      // B: zh, h (N = nb or 2 nb)
+        const uint64_t dB2 = sdesc(sa + (2 * nb / 8) * 128, ks, 128); // B: m, l, zm, zl
+        const uint64_t stp = (uint64_t)((2 * ks) >> 4);
 #pragma unroll
         for (int kk = 0; kk < TKT / 16; ++kk) {
           const uint32_t accB = (!gstart || kk > 0) ? 1u : 0u;
           const uint32_t accS = (!wstart || kk > 0) ? 1u : 0u;
-          const uint64_t aY = dY + kk * stY, bYr = dYr + kk * stY, aL = dL + kk * stY;
-          const uint64_t bZ = dZ + kk * stZ, bZr = dZr + kk * stZ;
-          mma_bf16(tSh, aY, aY, iN1, accB);   // [h; m] h^T
-          mma_bf16(tAh, aY, bZ, iN1, accB);   // [h; m] zh^T
-          mma_bf16(tSr, aY, bYr, iN2, accS);  // [h; m] [m | l]^T
-          mma_bf16(tAr, aY, bZr, iN2, accS);  // [h; m] [zm | zl]^T
-          mma_bf16(tL, aL, bZ, iN1, accS);    // [l; 0] zh^T
+          const uint64_t a = dA + kk * stp, b1 = dB1 + kk * stp;
+          mma_bf16(tAh, a, b1, iN2, accB);                      // [h; m] [zh | h]^T
+          mma_bf16(tSr, a, dB2 + kk * stp, iN4, accS);          // [h; m] [m | l | zm | zl]^T
+          mma_bf16(tL, dAL + kk * stp, b1, iN1, accS);          // [l; ...] zh^T
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             su32(&empty[s])));
@@ -676,7 +670,7 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     const long long rows = c->layout.psi_elems / P0;
     tma = tensor_map_rows(&mY, Y, P0, rows, 32, nb, true) && tensor_map_rows(&mZ, HY, P0, rows, 32, nb, true);
   }
-  const size_t stage = (size_t)(2 * nb + 128) * TKT * 2 + (size_t)(3 * nb) * TKT * 2;
+  const size_t stage = (size_t)stage_rows(nb) * TKT * 2;
   const size_t rawslot = tma ? 4 * (size_t)nb * 128 : 2 * (size_t)((nmax + 7) / 8) * 128 * sizeof(float4);
   const size_t accb = 5 * (size_t)nmax * (nmax + 1) * sizeof(float);
   // deepest (BF16 stages, raw tiles) pair that fits: three stages let the conversion run two tiles
