@@ -247,8 +247,15 @@ __device__ __forceinline__ void store_pair(unsigned char *st, int i, int k, int 
   store_split(st, i, 4 * nb + i, 5 * nb + i, k, ks, z);
 }
 
-// TMA form of the raw ring: each array's K-tile arrives as two 32-point boxes of nbmax rows with the
-// 128-byte swizzle (16-byte chunk c of row i stored at chunk c ^ (i % 8)), so that the converters' reads
+// Tensor maps over Y and HY as rows of P points, boxes of 32 points x 8 (k + 1) rows: a tile's boxes are
+// the fragment's orbital count rounded up to 8 rows (a box of the largest count would also carry the next
+// fragment's rows).
+struct GramMaps {
+  CUtensorMap y[8], z[8];
+};
+
+// TMA form of the raw ring: each array's K-tile arrives as two 32-point boxes (of up to nbmax rows, at
+// nbmax-row spacing) with the 128-byte swizzle (16-byte chunk c of row i stored at chunk c ^ (i % 8)), so that the converters' reads
 // (one warp: 8 rows x 4 quads) hit eight different chunks of a 128-byte line.
 __device__ __forceinline__ float4 raw_tma(const unsigned char *slot, int nbmax, int a, int i, int kq) {
   return *reinterpret_cast<const float4 *>(slot + ((a * 2 + (kq >> 3)) * nbmax + i) * 128 + (((kq & 7) ^ (i & 7)) << 4));
@@ -398,8 +405,7 @@ template <int NG, bool TMA>
 __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const int2 *gitems, int n_items,
                                                     const long long *goff, int chunk, int nmax, int nstages,
                                                     int nraw, const float *Y, const float *HY, double *out,
-                                                    unsigned *flags, const __grid_constant__ CUtensorMap tmY,
-                                                    const __grid_constant__ CUtensorMap tmZ) {
+                                                    unsigned *flags, const __grid_constant__ GramMaps tm) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tslot;
   __shared__ __align__(8) uint64_t full[3], empty[3], dready_b[2], ddone_b[2], dready_s, ddone_s, rfull[3],
@@ -493,15 +499,17 @@ __global__ void __launch_bounds__(TNT, 1) k_gram_tc(const FragDesc *desc, const 
       const int row0 = (int)(D.psi_off / P);
       unsigned char *rbase = reinterpret_cast<unsigned char *>(rawring);
       const int box = (tid & 63) == 0 ? tid >> 6 : -1;  // 0..3 on the issuing threads
+      const int h8 = (n + 7) >> 3;                       // box height in units of 8 rows
       auto issue = [&](int t) {
         const int r = (gr + t) % nraw;
         unsigned char *dst = rbase + (size_t)r * rslot + box * nbmax * 128;
         // the slot was last accessed through ordinary loads and stores (tiles, item sums)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(&rfull[r])),
-                     "r"(nbmax * 128)
+                     "r"(8 * h8 * 128)
                      : "memory");
-        tma_load_2d(dst, box < 2 ? &tmY : &tmZ, (int)(p0 + (long long)t * TKT) + 32 * (box & 1), row0, &rfull[r]);
+        tma_load_2d(dst, box < 2 ? &tm.y[h8 - 1] : &tm.z[h8 - 1], (int)(p0 + (long long)t * TKT) + 32 * (box & 1),
+                    row0, &rfull[r]);
       };
       if (box >= 0)
         for (int t = 0; t < nraw && t < ntiles; ++t) issue(t);
@@ -656,19 +664,20 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
     dc_set_error("mixed-precision Gram needs n <= 64 orbitals per fragment");
     return DC_ERR_ARG;
   }
-  // raw tiles by TMA when every fragment has the same point count P (a multiple of 4) and the same
-  // orbital count: the blocks are then rows of P points, and a tile is two 32-point boxes of nb rows per
-  // array.  (With uneven orbital counts a box of the largest count would also carry the next fragment's
-  // rows: on the water cell that cost 19% more Gram time than the per-row copies.)
-  CUtensorMap mY{}, mZ{};
+  // raw tiles by TMA when every fragment has the same point count P (a multiple of 4): the blocks are then
+  // rows of P points, and a tile is two 32-point boxes per array of the fragment's orbital count rounded up
+  // to 8 rows
+  GramMaps maps{};
   bool tma = c->h_desc.size() > 0;
   const long long P0 = tma ? (long long)c->h_desc[0].E[0] * c->h_desc[0].E[1] * c->h_desc[0].E[2] : 0;
   for (const auto &D : c->h_desc)
-    if ((long long)D.E[0] * D.E[1] * D.E[2] != P0 || D.norb != nmax) tma = false;
+    if ((long long)D.E[0] * D.E[1] * D.E[2] != P0) tma = false;
   tma = tma && (P0 & 3) == 0 && c->gram_chunk % TKT == 0;
   if (tma) {
     const long long rows = c->layout.psi_elems / P0;
-    tma = tensor_map_rows(&mY, Y, P0, rows, 32, nb, true) && tensor_map_rows(&mZ, HY, P0, rows, 32, nb, true);
+    for (int k = 0; k < nb / 8 && tma; ++k)
+      tma = tensor_map_rows(&maps.y[k], Y, P0, rows, 32, 8 * (k + 1), true) &&
+            tensor_map_rows(&maps.z[k], HY, P0, rows, 32, 8 * (k + 1), true);
   }
   const size_t stage = (size_t)stage_rows(nb) * TKT * 2;
   const size_t rawslot = tma ? 4 * (size_t)nb * 128 : 2 * (size_t)((nmax + 7) / 8) * 128 * sizeof(float4);
@@ -697,7 +706,7 @@ int launch_gram_tc(dc_ctx *c, const float *Y, const float *HY, cudaStream_t s) {
   auto run = [&](auto kern) -> int {
     DC_CUDA(dc_set_smem((const void *)kern, sm));
     kern<<<grid, TNT, sm, s>>>(c->d_desc, c->d_gram_items, c->n_gram_items, c->d_gram_off, c->gram_chunk, nmax,
-                               nstages, nraw, Y, HY, c->d_gram, c->d_flags, mY, mZ);
+                               nstages, nraw, Y, HY, c->d_gram, c->d_flags, maps);
     DC_CUDA(cudaGetLastError());
     return DC_OK;
   };

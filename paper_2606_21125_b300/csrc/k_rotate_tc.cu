@@ -10,7 +10,8 @@
 // Persistent CTAs (one per SM) run contiguous blocks of (fragment, tile) items as a warp-specialised
 // pipeline:
 //  - one thread loads each tile's [orbital][point] FP32 rows with one 2-D TMA copy (a tensor map over
-//    the block as rows of P points; points past P arrive as zeros) into a ring of three raw tiles;
+//    the block as rows of P points, whose box is the fragment's orbital count rounded up to 8 rows, one
+//    map per height; points past P arrive as zeros) into a ring of three raw tiles;
 //  - eight converter warps transpose and split a raw tile into a BF16 stage (a thread takes one point
 //    and eight orbitals: eight conflict-free shared loads, three 16-byte stores), two stages;
 //  - one thread issues the tile's 6 x nb/16 MMAs into one of two tensor-memory accumulators;
@@ -123,6 +124,13 @@ __device__ __forceinline__ void split8(const float *v, uint4 &h, uint4 &m, uint4
   split3x2(v[6], v[7], h.w, m.w, l.w);
 }
 
+// Tensor maps over the block as rows of P points, box 128 points x 8 (k + 1) rows.  A box of the
+// largest orbital count would also load the next fragment's rows: on the water cell (orbital counts
+// 15-53) that doubled the rotation's reads of Y.
+struct RotMaps {
+  CUtensorMap m[8];
+};
+
 struct RotArgs {
   const FragDesc *desc;
   const int2 *items;  // (fragment, 128-point tile)
@@ -135,7 +143,7 @@ struct RotArgs {
 };
 
 __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ RotArgs a,
-                                                       const __grid_constant__ CUtensorMap tmY) {
+                                                       const __grid_constant__ RotMaps tmY) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ uint32_t tslot;
   __shared__ __align__(8) uint64_t rfull[RT_NRAW], afull[RT_NST], aempty[RT_NST], dfull[2], dempty[2];
@@ -145,7 +153,7 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
   const int nbm = (a.nmax + 15) & ~15;
   const int ksA = (RTM / 8) * 128, ksB = (nbm / 8) * 128;
   const int abytes = RTM * nbm * 2, bbytes = nbm * nbm * 2;
-  const int rawbytes = nbm * RTM * 4;  // one TMA box (nbm rows of 128 points)
+  const int rawbytes = nbm * RTM * 4;  // one raw slot (the largest box: nbm rows of 128 points)
   // raw tiles [NRAW] (1024-aligned), BF16 stages [NST][3 words], B words [3]
   const int rawpitch = (rawbytes + 1023) & ~1023;
   float *raw0 = reinterpret_cast<float *>(sm);
@@ -189,9 +197,10 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
       const int2 fi = a.items[it0 + t];
       const FragDesc &D = a.desc[fi.x];
       const int r = t % RT_NRAW;
-      mbar_expect_tx(&rfull[r], (uint32_t)rawbytes);
-      tma_load_2d(reinterpret_cast<unsigned char *>(raw0) + r * rawpitch, &tmY, fi.y * RTM, (int)(D.psi_off / P),
-                  &rfull[r]);
+      const int hb = (D.norb + 7) >> 3;  // box height in units of 8 rows
+      mbar_expect_tx(&rfull[r], (uint32_t)(8 * hb * RTM * 4));
+      tma_load_2d(reinterpret_cast<unsigned char *>(raw0) + r * rawpitch, &tmY.m[hb - 1], fi.y * RTM,
+                  (int)(D.psi_off / P), &rfull[r]);
     };
     if (tid == 0)
       for (int t = 0; t < RT_NRAW && t < nt; ++t) issue(t);
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
     for (int t = 0; t < nt; ++t) {
       const int2 fi = a.items[it0 + t];
       const FragDesc &D = a.desc[fi.x];
-      const int n = D.norb;
+      const int n = D.norb, nb = (n + 15) & ~15;
       const int s = t % RT_NST, r = t % RT_NRAW;
       mbar_wait(&rfull[r], (uint32_t)((t / RT_NRAW) & 1), abort);
       mbar_wait(&aempty[s], (uint32_t)(((t / RT_NST) & 1) ^ 1), abort);
@@ -207,9 +216,10 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
         // a new fragment's B(i, j) = C_ji: every MMA of the previous tiles has completed (their commit
         // to aempty of tile t - 1 has fired) before B is overwritten
         if (t > 0) mbar_wait(&aempty[(t - 1) % RT_NST], (uint32_t)(((t - 1) / RT_NST) & 1), abort);
+        // (the MMAs read rows i < nb and orbitals j < nb of it)
         const float *Cf = a.C + D.sub_off;
-        for (int u = tid; u < nbm * (nbm / 8); u += RT_CONV) {
-          const int i = u / (nbm / 8), q = u - i * (nbm / 8);
+        for (int u = tid; u < nb * (nb / 8); u += RT_CONV) {
+          const int i = u / (nb / 8), q = u - i * (nb / 8);
           float v[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
@@ -225,10 +235,11 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
         }
         cur_f = fi.x;
       }
-      // transpose-split: A(p, j) for eight orbitals j = 8q .. 8q + 7 of point p (orbitals >= n are zero)
+      // transpose-split: A(p, j) for eight orbitals j = 8q .. 8q + 7 of point p, j < nb (orbitals >= n are
+      // zero; the MMAs read no orbital past nb, so the work follows the fragment's own count)
       const float *raw = reinterpret_cast<const float *>(reinterpret_cast<const unsigned char *>(raw0) + r * rawpitch);
       unsigned char *As = Aw + s * 3 * abytes;
-      for (int u = tid; u < RTM * (nbm / 8); u += RT_CONV) {
+      for (int u = tid; u < RTM * (nb / 8); u += RT_CONV) {
         const int q = u / RTM, p = u - q * RTM;
         float v[8];
 #pragma unroll
@@ -382,9 +393,10 @@ int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s) {
   for (const auto &D : c->h_desc)
     if ((long long)D.E[0] * D.E[1] * D.E[2] != P) return DC_ERR_ARG;
   if ((((uintptr_t)Y) | ((uintptr_t)out)) & 15) return DC_ERR_ARG;
-  // the block as rows of P points, box (128 points, nbm rows)
-  CUtensorMap map;
-  if (!tensor_map_rows(&map, Y, P, c->layout.psi_elems / P, RTM, nbm, false)) return DC_ERR_ARG;
+  // the block as rows of P points, boxes of 128 points and 8, 16, .. nbm rows
+  RotMaps maps{};
+  for (int k = 0; k < nbm / 8; ++k)
+    if (!tensor_map_rows(&maps.m[k], Y, P, c->layout.psi_elems / P, RTM, 8 * (k + 1), false)) return DC_ERR_ARG;
   RotArgs a;
   a.desc = c->d_desc;
   a.items = c->d_rot_items;
@@ -398,7 +410,7 @@ int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s) {
   const size_t sm = RT_NRAW * rawpitch + (size_t)RT_NST * 3 * RTM * nbm * 2 + 3 * (size_t)nbm * nbm * 2;
   DC_CUDA(dc_set_smem((const void *)k_rotate_tc, sm));
   const int grid = std::min(c->n_rot_items, c->sm_count);
-  k_rotate_tc<<<(unsigned)grid, RTNT, sm, s>>>(a, map);
+  k_rotate_tc<<<(unsigned)grid, RTNT, sm, s>>>(a, maps);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }

@@ -149,6 +149,11 @@ CASES_EXTRA = {
     "water32": lambda **kw: workloads.small_config(n=(32, 32, 32), L=(10.93, 10.93, 10.93), num_fragment=(2, 2, 2),
                                                    buffer=(8, 8, 8), nstate=0, natom=9, seed=12, species=("O", "H"),
                                                    **kw),
+    # 48 O/H atoms in a 9 bohr box: orbital counts 22-56 from the fragments' electrons, so one launch holds
+    # orbital blocks rounded to 32, 48 and 64 (the widest tensor-core MMA, N = 4 x 64 = 256)
+    "water_dense": lambda **kw: workloads.small_config(n=(24, 24, 24), L=(9.0, 9.0, 9.0), num_fragment=(2, 2, 2),
+                                                       buffer=(3, 3, 3), nstate=0, natom=48, seed=9,
+                                                       species=("O", "H"), **kw),
 }
 
 
@@ -215,12 +220,12 @@ def test_subspace_and_one_chefsi_pass_fp32(case, kind):
     assert np.max(np.abs(e1 - eps_1)) < 2e-5 * max(1.0, np.max(np.abs(eps_1))), shape
 
 
-@pytest.mark.parametrize("case", ["si8", "water_auto", "water32"])
+@pytest.mark.parametrize("case", ["si8", "water_auto", "water32", "water_dense"])
 def test_one_chefsi_pass_mixed(case):
     """One filtered pass in mixed precision against the FP64 oracle: the tensor-core Gram (its raw tiles by
-    TMA, since every fragment has the same point count) and the tensor-core rotation, with uneven orbital
-    counts per fragment in the water_auto case (orbital blocks of different widths in one launch) and 32^3
-    fragments in water32."""
+    TMA when every fragment has the same point and orbital counts) and the tensor-core rotation, with uneven
+    orbital counts per fragment in the water_auto case (orbital blocks of different widths in one launch),
+    32^3 fragments in water32 and orbital blocks rounded to 32, 48 and 64 in one launch in water_dense."""
     cfg = (CASES[case] if case in CASES else CASES_EXTRA[case])(precision="mixed")
     st = oracle_state(cfg)
     V = st.veff(st.rho_in)
@@ -236,6 +241,8 @@ def test_one_chefsi_pass_mixed(case):
         e1 = _np(e1)
     if case == "water_auto":
         assert len(set(int(v) for v in st.norb)) > 1  # the case does have uneven orbital counts
+    if case == "water_dense":
+        assert {(int(v) + 15) // 16 for v in st.norb} == {2, 3, 4}
     assert np.max(np.abs(e1 - eps_1)) < 2e-5 * max(1.0, np.max(np.abs(eps_1)))
 
 
