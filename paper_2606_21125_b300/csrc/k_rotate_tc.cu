@@ -35,6 +35,8 @@ constexpr int RTNT = 32 * (RT_MMAW + 1);   // threads per CTA
 constexpr int RT_NRAW = 3;                 // raw tiles in flight
 constexpr int RT_NST = 2;                  // BF16 stages
 constexpr int RT_TMEM_COLS = 128;          // two accumulators of up to 64 columns
+constexpr int RT_TP = 36;                  // drain transpose buffer row pitch (floats; 16-byte rows)
+constexpr int RT_DRAIN_SM = 8 * 8 * RT_TP * 4;  // eight drain warps x [8 orbitals][32 points]
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
   float *raw0 = reinterpret_cast<float *>(sm);
   unsigned char *Aw = sm + RT_NRAW * rawpitch;
   unsigned char *Bw = Aw + RT_NST * 3 * abytes;
+  float *tbuf = reinterpret_cast<float *>(Bw + 3 * bbytes);  // drain transposes
   const long long P = a.P;
   const int it0 = (int)(((long long)blockIdx.x * a.n_items) / gridDim.x);
   const int it1 = (int)(((long long)(blockIdx.x + 1) * a.n_items) / gridDim.x);
@@ -279,20 +282,44 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
       const int2 fi = a.items[it0 + t];
       const FragDesc &D = a.desc[fi.x];
       const int n = D.norb, nb = (n + 15) & ~15;
-      const long long pp = (long long)fi.y * RTM + 32 * q4 + lane;
       float *of = a.out + D.psi_off;
       const uint32_t tl = tbase + (uint32_t)(b * 64) + ((uint32_t)(32 * q4) << 16);
-      for (int g = gh; g < nb / 8; g += 2) {
-        uint32_t v[8];
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                     : "r"(tl + 8 * g));
-        asm volatile("tcgen05.wait::ld.sync.aligned;"
-                     : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]));
-        if (pp < P) {
+      // all of this warp's column groups (up to four) with one wait, then each group through a per-warp
+      // [8 orbitals][32 points] shared buffer, so that a lane stores 4 consecutive points of one orbital
+      uint32_t v[4][8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (8 * g + e < n) of[(long long)(8 * g + e) * P + pp] = __uint_as_float(v[e]);
+      for (int j = 0; j < 4; ++j) {
+        const int g = gh + 2 * j;
+        if (g < nb / 8)  // warp-uniform
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[j][0]), "=r"(v[j][1]), "=r"(v[j][2]), "=r"(v[j][3]), "=r"(v[j][4]), "=r"(v[j][5]),
+                         "=r"(v[j][6]), "=r"(v[j][7])
+                       : "r"(tl + 8 * g));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;"
+                   : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[0][4]), "+r"(v[0][5]),
+                     "+r"(v[0][6]), "+r"(v[0][7]), "+r"(v[1][0]), "+r"(v[1][1]), "+r"(v[1][2]), "+r"(v[1][3]),
+                     "+r"(v[1][4]), "+r"(v[1][5]), "+r"(v[1][6]), "+r"(v[1][7]), "+r"(v[2][0]), "+r"(v[2][1]),
+                     "+r"(v[2][2]), "+r"(v[2][3]), "+r"(v[2][4]), "+r"(v[2][5]), "+r"(v[2][6]), "+r"(v[2][7]),
+                     "+r"(v[3][0]), "+r"(v[3][1]), "+r"(v[3][2]), "+r"(v[3][3]), "+r"(v[3][4]), "+r"(v[3][5]),
+                     "+r"(v[3][6]), "+r"(v[3][7]));
+      float *tb = tbuf + (warp - RT_CONV / 32) * 8 * RT_TP;
+      const long long p0 = (long long)fi.y * RTM + 32 * q4;  // the warp's first point
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int g = gh + 2 * j;
+        if (g >= nb / 8) break;  // warp-uniform
+        __syncwarp();  // the previous group's reads of the buffer are done
+#pragma unroll
+        for (int e = 0; e < 8; ++e) tb[e * RT_TP + lane] = __uint_as_float(v[j][e]);
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int i = lane + 32 * h, e = i >> 3, q = i & 7;
+          const long long pq = p0 + 4 * q;
+          if (8 * g + e < n && pq < P)  // P is a multiple of 4: a quad lies wholly inside or outside
+            *reinterpret_cast<float4 *>(of + (long long)(8 * g + e) * P + pq) =
+                *reinterpret_cast<const float4 *>(tb + e * RT_TP + 4 * q);
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -407,7 +434,7 @@ int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s) {
   a.nmax = nmax;
   a.P = P;
   const size_t rawpitch = ((size_t)nbm * RTM * 4 + 1023) & ~(size_t)1023;
-  const size_t sm = RT_NRAW * rawpitch + (size_t)RT_NST * 3 * RTM * nbm * 2 + 3 * (size_t)nbm * nbm * 2;
+  const size_t sm = RT_NRAW * rawpitch + (size_t)RT_NST * 3 * RTM * nbm * 2 + 3 * (size_t)nbm * nbm * 2 + RT_DRAIN_SM;
   DC_CUDA(dc_set_smem((const void *)k_rotate_tc, sm));
   const int grid = std::min(c->n_rot_items, c->sm_count);
   k_rotate_tc<<<(unsigned)grid, RTNT, sm, s>>>(a, maps);
