@@ -34,7 +34,8 @@ constexpr int RT_MMAW = 16;                // MMA warp (warps 8-15 drain: lane g
 constexpr int RTNT = 32 * (RT_MMAW + 1);   // threads per CTA
 constexpr int RT_NRAW = 3;                 // raw tiles in flight
 constexpr int RT_NST = 2;                  // BF16 stages
-constexpr int RT_TMEM_COLS = 128;          // two accumulators of up to 64 columns
+constexpr int RT_ACC = 192;                // tensor-memory columns per accumulator: three blocks of up to 64
+constexpr int RT_TMEM_COLS = 512;          // two accumulators
 constexpr int RT_TP = 36;                  // drain transpose buffer row pitch (floats; 16-byte rows)
 constexpr int RT_DRAIN_SM = 8 * 8 * RT_TP * 4;  // eight drain warps x [8 orbitals][32 points]
 
@@ -85,6 +86,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
   }
   *abort = 1;
   return false;
+}
+
+// One 32-lane x 8-column tensor-memory load (completed by a later wait).
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(addr));
+}
+
+// Wait for every earlier tensor-memory load of the thread; the 24 registers named as in/out operands are
+// not read before it.
+__device__ __forceinline__ void tmem_wait24(uint32_t (&a)[8], uint32_t (&b)[8], uint32_t (&c)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                 "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                 "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7]));
 }
 
 // 2-D TMA load of box (x = first point, y = first row) into shared memory, completion on `bar`.
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
   volatile int *abort = &abort_w;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int nbm = (a.nmax + 15) & ~15;
-  const int ksA = (RTM / 8) * 128, ksB = (nbm / 8) * 128;
+  const int ksA = (RTM / 8) * 128, ksB = (3 * nbm / 8) * 128;  // B: rows [B_h | B_m | B_l], nb each
   const int abytes = RTM * nbm * 2, bbytes = nbm * nbm * 2;
   const int rawbytes = nbm * RTM * 4;  // one raw slot (the largest box: nbm rows of 128 points)
   // raw tiles [NRAW] (1024-aligned), BF16 stages [NST][3 words], B words [3]
@@ -231,10 +248,9 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
           }
           uint4 h, m, l;
           split8(v, h, m, l);
-          const int o = toff(i, 8 * q, ksB);
-          *reinterpret_cast<uint4 *>(Bw + o) = h;
-          *reinterpret_cast<uint4 *>(Bw + bbytes + o) = m;
-          *reinterpret_cast<uint4 *>(Bw + 2 * bbytes + o) = l;
+          *reinterpret_cast<uint4 *>(Bw + toff(i, 8 * q, ksB)) = h;
+          *reinterpret_cast<uint4 *>(Bw + toff(nb + i, 8 * q, ksB)) = m;
+          *reinterpret_cast<uint4 *>(Bw + toff(2 * nb + i, 8 * q, ksB)) = l;
         }
         cur_f = fi.x;
       }
@@ -283,43 +299,45 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
       const FragDesc &D = a.desc[fi.x];
       const int n = D.norb, nb = (n + 15) & ~15;
       float *of = a.out + D.psi_off;
-      const uint32_t tl = tbase + (uint32_t)(b * 64) + ((uint32_t)(32 * q4) << 16);
-      // all of this warp's column groups (up to four) with one wait, then each group through a per-warp
-      // [8 orbitals][32 points] shared buffer, so that a lane stores 4 consecutive points of one orbital
-      uint32_t v[4][8];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int g = gh + 2 * j;
-        if (g < nb / 8)  // warp-uniform
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(v[j][0]), "=r"(v[j][1]), "=r"(v[j][2]), "=r"(v[j][3]), "=r"(v[j][4]), "=r"(v[j][5]),
-                         "=r"(v[j][6]), "=r"(v[j][7])
-                       : "r"(tl + 8 * g));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;"
-                   : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[0][4]), "+r"(v[0][5]),
-                     "+r"(v[0][6]), "+r"(v[0][7]), "+r"(v[1][0]), "+r"(v[1][1]), "+r"(v[1][2]), "+r"(v[1][3]),
-                     "+r"(v[1][4]), "+r"(v[1][5]), "+r"(v[1][6]), "+r"(v[1][7]), "+r"(v[2][0]), "+r"(v[2][1]),
-                     "+r"(v[2][2]), "+r"(v[2][3]), "+r"(v[2][4]), "+r"(v[2][5]), "+r"(v[2][6]), "+r"(v[2][7]),
-                     "+r"(v[3][0]), "+r"(v[3][1]), "+r"(v[3][2]), "+r"(v[3][3]), "+r"(v[3][4]), "+r"(v[3][5]),
-                     "+r"(v[3][6]), "+r"(v[3][7]));
+      const uint32_t tl = tbase + (uint32_t)(b * RT_ACC) + ((uint32_t)(32 * q4) << 16);
+      // this warp's column groups (up to four), two per wait: the three blocks of each group summed small to
+      // large, then stored through a per-warp [8 orbitals][32 points] shared buffer, so that a lane writes 4
+      // consecutive points of one orbital
       float *tb = tbuf + (warp - RT_CONV / 32) * 8 * RT_TP;
       const long long p0 = (long long)fi.y * RTM + 32 * q4;  // the warp's first point
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int g = gh + 2 * j;
-        if (g >= nb / 8) break;  // warp-uniform
-        __syncwarp();  // the previous group's reads of the buffer are done
+      for (int jb = 0; jb < 4; jb += 2) {
+        if (gh + 2 * jb >= nb / 8) break;  // warp-uniform
+        uint32_t w[2][3][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) tb[e * RT_TP + lane] = __uint_as_float(v[j][e]);
-        __syncwarp();
+        for (int u = 0; u < 2; ++u) {
+          const int g = gh + 2 * (jb + u);
+          if (g < nb / 8) {  // warp-uniform
+            tmem_ld8(tl + 8 * g, w[u][0]);
+            tmem_ld8(tl + nb + 8 * g, w[u][1]);
+            tmem_ld8(tl + 2 * nb + 8 * g, w[u][2]);
+          }
+        }
+        tmem_wait24(w[0][0], w[0][1], w[0][2]);
+        tmem_wait24(w[1][0], w[1][1], w[1][2]);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = lane + 32 * h, e = i >> 3, q = i & 7;
-          const long long pq = p0 + 4 * q;
-          if (8 * g + e < n && pq < P)  // P is a multiple of 4: a quad lies wholly inside or outside
-            *reinterpret_cast<float4 *>(of + (long long)(8 * g + e) * P + pq) =
-                *reinterpret_cast<const float4 *>(tb + e * RT_TP + 4 * q);
+        for (int u = 0; u < 2; ++u) {
+          const int g = gh + 2 * (jb + u);
+          if (g >= nb / 8) break;  // warp-uniform
+          __syncwarp();  // the previous group's reads of the buffer are done
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            tb[e * RT_TP + lane] =
+                __uint_as_float(w[u][0][e]) + (__uint_as_float(w[u][1][e]) + __uint_as_float(w[u][2][e]));
+          __syncwarp();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int i = lane + 32 * h, e = i >> 3, q = i & 7;
+            const long long pq = p0 + 4 * q;
+            if (8 * g + e < n && pq < P)  // P is a multiple of 4: a quad lies wholly inside or outside
+              *reinterpret_cast<float4 *>(of + (long long)(8 * g + e) * P + pq) =
+                  *reinterpret_cast<const float4 *>(tb + e * RT_TP + 4 * q);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
@@ -334,19 +352,15 @@ __global__ void __launch_bounds__(RTNT, 1) k_rotate_tc(const __grid_constant__ R
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int2 fi = a.items[it0 + t];
       const int nb = (a.desc[fi.x].norb + 15) & ~15;
-      const uint32_t id = idesc_bf16(RTM, nb);
+      const uint32_t id3 = idesc_bf16(RTM, 3 * nb), id2 = idesc_bf16(RTM, 2 * nb), id1 = idesc_bf16(RTM, nb);
       const uint32_t a0 = su32(Aw + s * 3 * abytes), b0 = su32(Bw);
-      const uint32_t td = tbase + (uint32_t)(b * 64);
-      // terms (A word, B word): hh hm hl mh mm lh
+      const uint32_t td = tbase + (uint32_t)(b * RT_ACC);
+      // blocks [hh + mh + lh | hm + mm | hl]: A_h [B_h | B_m | B_l]^T, A_m [B_h | B_m]^T, A_l B_h^T
       for (int kk = 0; kk < nb / 16; ++kk) {
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-          const int wa = u < 3 ? 0 : (u < 5 ? 1 : 2);
-          const int wb = u < 3 ? u : (u < 5 ? u - 3 : 0);
-          const uint64_t da = sdesc(a0 + wa * abytes + kk * 2 * ksA, ksA, 128);
-          const uint64_t db = sdesc(b0 + wb * bbytes + kk * 2 * ksB, ksB, 128);
-          mma_bf16(td, da, db, id, (kk > 0 || u > 0) ? 1u : 0u);
-        }
+        const uint64_t db = sdesc(b0 + kk * 2 * ksB, ksB, 128);
+        mma_bf16(td, sdesc(a0 + kk * 2 * ksA, ksA, 128), db, id3, kk > 0 ? 1u : 0u);
+        mma_bf16(td, sdesc(a0 + abytes + kk * 2 * ksA, ksA, 128), db, id2, 1u);
+        mma_bf16(td, sdesc(a0 + 2 * abytes + kk * 2 * ksA, ksA, 128), db, id1, 1u);
       }
       mma_commit(&aempty[s]);
       mma_commit(&dfull[b]);
