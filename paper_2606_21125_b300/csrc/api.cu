@@ -297,10 +297,14 @@ int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
     }
   }
   const int hy = (cur + 1) % 3;
+  // H Y feeds only the Gram.  Where the specialised kernel applies H, it applies the local part alone and
+  // the subspace stage adds the nonlocal part of A = Y^T H Y from the block's projections <p|Y> (Eq. 5:
+  // Y^T D P P^T Y = sum_a D_a <p_a|Y>^T <p_a|Y>), which the last filter step has already formed.
+  const bool hloc = sizeof(T) == 4 && dck::hstep_specialised(c);
   {
-    StageScope sc(c, DC_STAGE_HPSI, s, 2.0 * blk + vfb + pj, 1);
-    DC_TRY(dck::launch_hstep<T>(c, HSTEP_HPSI, 0, B[cur], nullptr, B[hy], cproj<T>(c, cbuf), nullptr, nullptr,
-                                nullptr, nullptr, nullptr, s));
+    StageScope sc(c, DC_STAGE_HPSI, s, 2.0 * blk + vfb + (hloc ? 0.0 : pj), 1);
+    DC_TRY(dck::launch_hstep<T>(c, hloc ? HSTEP_HLOC : HSTEP_HPSI, 0, B[cur], nullptr, B[hy], cproj<T>(c, cbuf),
+                                nullptr, nullptr, nullptr, nullptr, nullptr, s));
   }
   {
     StageScope sc(c, DC_STAGE_GRAM, s, 2.0 * blk + 8.0 * c->gram_elems, 1);
@@ -310,8 +314,9 @@ int chefsi_pass(dc_ctx *c, T *B[3], int &ib, bool filter, cudaStream_t s) {
       DC_TRY(dck::launch_gram<T>(c, B[cur], B[hy], s));
   }
   {
-    StageScope sc(c, DC_STAGE_SUBSPACE, s, 8.0 * c->gram_elems, 1);
-    DC_TRY(dck::launch_subspace(c, sizeof(T) == 4 ? 32 : 64, c->d_eps, s));
+    StageScope sc(c, DC_STAGE_SUBSPACE, s, 8.0 * c->gram_elems + (hloc ? pj : 0.0), 1);
+    DC_TRY(dck::launch_subspace(c, sizeof(T) == 4 ? 32 : 64, c->d_eps, s,
+                                hloc ? reinterpret_cast<const float *>(cproj<T>(c, cbuf)) : nullptr));
   }
   {
     StageScope sc(c, DC_STAGE_ROTATE, s, 2.0 * blk, 1);

@@ -290,8 +290,11 @@ int hstep_shape_find(const dc_ctx *c, size_t esz, int kind, int threads, int pai
 template <typename T>
 int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T *yout, const T *cin, T *cout,
                  const double *Datom, const double *occ, double *dots, const T *vf, cudaStream_t s);
+// true when FP32 H-applies of this context run the specialised kernel (the only one with HSTEP_HLOC)
+bool hstep_specialised(const dc_ctx *c);
 // specialised FP32 kernel (uniform cubic fragments, zero boundary, isotropic spacing): the compiled extent
-// it runs for this context, or 0; and its launch (HSTEP_CHEB / HSTEP_HPSI, input projections required)
+// it runs for this context, or 0; and its launch (HSTEP_CHEB / HSTEP_HPSI / HSTEP_HLOC, input projections
+// required)
 int cheb_extent(const dc_ctx *c);
 int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yprev, float *yout, const float *cin,
                 float *cout, cudaStream_t s);
@@ -307,7 +310,9 @@ int launch_rotate_tc(dc_ctx *c, const float *Y, float *out, cudaStream_t s);
 // false when the driver's encoder is unavailable or the shape does not qualify.
 bool tensor_map_rows(CUtensorMap *map, const float *base, long long inner, long long rows, int box_inner,
                      int box_rows, bool swizzle128);
-int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s);
+// cnl: when not null, the FP32 projections <p|Y> (per fragment at c_off, orbital-major) of a block whose
+// H Y holds only the local part of H; their nonlocal term sum_a D_a <p_a|y_i><p_a|y_j> is added to A
+int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s, const float *cnl = nullptr);
 template <typename T>
 int launch_lcfo(dc_ctx *c, const T *psi, const double *eps, double eps_cut, double lambda_cut, double *basis,
                 int *nbasis, double *s_out, cudaStream_t s);
@@ -340,3 +345,4 @@ int launch_sum(const double *x, long long n, double *out, double *partials, int 
 #define HSTEP_HPSI 0  // out = H y
 #define HSTEP_CHEB 1  // out = alpha (H y - shift y) + beta yprev
 #define HSTEP_ADJ 2   // out = 2 occ dV H y ; dots[item] = occ dV <y|H y>
+#define HSTEP_HLOC 3  // out = (-1/2 L8 + V) y, the local part of H (the specialised FP32 kernel only)

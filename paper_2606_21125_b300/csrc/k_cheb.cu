@@ -322,7 +322,7 @@ __device__ __forceinline__ void proj_plane(const ChebSmem<E> &m, int zp, int A) 
 // the end.  A loop over z with these moves runs faster than a body unrolled nine times that renames the
 // registers instead: the unrolled kernel's instruction footprint stalled the warps on instruction fetch.
 // Returns false when the CTA aborts.
-template <int E, bool PREV, bool PROJ>
+template <int E, bool PREV, bool PROJ, bool NL>
 __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> &m, const ChebT &T, float4 (&q)[9],
                                            int z, int gbase, int ntot, const ItemInfo &I, const float2 *sk2,
                                            float *yout) {
@@ -419,8 +419,8 @@ __device__ __forceinline__ bool cheb_plane(const ChebArgs &a, const ChebSmem<E> 
     h0 = fma2(ksh, c0, fma2(f2(vr.x, vr.x), c0, h0));
     h1 = fma2(ksh, c1, fma2(f2(vr.y, vr.y), c1, h1));
   }
-  // nonlocal term over the row's records
-  {
+  // nonlocal term over the row's records (NL = false: the local part of H only)
+  if (NL) {
     const int rz = z * E + T.py;
     // entries that can reach this point's half of the row: [left-only | both] or [both | right-only].
     // Measured per extent: 22^3 fragments 1.650 -> 1.639 ms per Si512 launch with the halves; on 32^3
@@ -525,7 +525,7 @@ __device__ __forceinline__ void copy_int2(int2 *dst, const int2 *src, int n) {
 // coef dV) stay in shared memory.  The ring runs on across items (the next item's first planes are in
 // flight while the current item ends), and the next item's first column planes and, for the same
 // fragment, its D C <p|y> are fetched during the current item's tail.
-template <int E, bool PREV, bool PROJ>
+template <int E, bool PREV, bool PROJ, bool NL>
 __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_constant__ ChebArgs a) {
   using G = Geo<E>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
     const ItemInfo &I = m.itab[lj];
     const int A = I.nva >> 2, nvalid = I.nva & 3;
     float2 *sk2 = m.sk2 + (lj & 1) * a.amax;
-    if (I.vf != cur_vf) {
+    if ((NL || PROJ) && I.vf != cur_vf) {
       // a new fragment: its tables, and the pair's D C <p|y> (the tables' previous readers finished
       // before the barrier that ended the last item)
       const int f = a.items[it0 + lj].x;
@@ -617,7 +617,7 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
     float *yout = a.yout + I.base;
     bool ok = true;
 #pragma unroll 1
-    for (int z = 0; z < E && ok; ++z) ok = cheb_plane<E, PREV, PROJ>(a, m, T, q, z, lj * E, ntot, I, sk2, yout);
+    for (int z = 0; z < E && ok; ++z) ok = cheb_plane<E, PREV, PROJ, NL>(a, m, T, q, z, lj * E, ntot, I, sk2, yout);
     __syncthreads();
     if (*m.abort) break;
     // the next item: its first column planes (the loads are in flight during this item's tail) and, for
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(Geo<E>::NT, Geo<E>::MINB) k_cheb(const __grid_
     if (lj + 1 < nit) {
       const ItemInfo &In = m.itab[lj + 1];
       column_start<E>(a, T, In, q);
-      if (In.vf == I.vf && tid >= G::NT - 32) {
+      if (NL && In.vf == I.vf && tid >= G::NT - 32) {
         float2 *skn = m.sk2 + ((lj + 1) & 1) * a.amax;
         const int nvn = In.nva & 3;
         for (int k = tid - (G::NT - 32); k < A; k += 32) {
@@ -671,7 +671,7 @@ bool cheb_fits(const dc_ctx *c) {
   return L.end <= 227 * 1024;
 }
 
-template <int E, bool PREV, bool PROJ>
+template <int E, bool PREV, bool PROJ, bool NL>
 int run_cheb(const dc_ctx *c, ChebArgs a, cudaStream_t s) {
   using G = Geo<E>;
   const int n = c->n_items2;
@@ -684,9 +684,9 @@ int run_cheb(const dc_ctx *c, ChebArgs a, cudaStream_t s) {
     const int g = std::min(n, per * c->sm_count);
     const int ipc = cheb_ipc(n, g);
     sm = ChebLayout<E, PREV>(a.amax, a.nentmax, ipc).end;
-    DC_CUDA(dc_set_smem((const void *)k_cheb<E, PREV, PROJ>, sm));
+    DC_CUDA(dc_set_smem((const void *)k_cheb<E, PREV, PROJ, NL>, sm));
     int occ = 0;
-    DC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cheb<E, PREV, PROJ>, G::NT, sm));
+    DC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cheb<E, PREV, PROJ, NL>, G::NT, sm));
     if (occ >= per) {
       grid = g;
       a.ipc = ipc;
@@ -696,17 +696,18 @@ int run_cheb(const dc_ctx *c, ChebArgs a, cudaStream_t s) {
     dc_set_error("hpsi: the specialised FP32 kernel's shared memory does not fit");
     return DC_ERR_ARG;
   }
-  k_cheb<E, PREV, PROJ><<<(unsigned)grid, G::NT, sm, s>>>(a);
+  k_cheb<E, PREV, PROJ, NL><<<(unsigned)grid, G::NT, sm, s>>>(a);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
 
 template <int E>
-int run_cheb_e(const dc_ctx *c, const ChebArgs &a, bool prev, bool proj, cudaStream_t s) {
-  if (prev && proj) return run_cheb<E, true, true>(c, a, s);
-  if (proj) return run_cheb<E, false, true>(c, a, s);
-  if (prev) return run_cheb<E, true, false>(c, a, s);
-  return run_cheb<E, false, false>(c, a, s);
+int run_cheb_e(const dc_ctx *c, const ChebArgs &a, bool prev, bool proj, bool nl, cudaStream_t s) {
+  if (!nl) return run_cheb<E, false, false, false>(c, a, s);  // the local part of H (no y_prev, no projections)
+  if (prev && proj) return run_cheb<E, true, true, true>(c, a, s);
+  if (proj) return run_cheb<E, false, true, true>(c, a, s);
+  if (prev) return run_cheb<E, true, false, true>(c, a, s);
+  return run_cheb<E, false, false, true>(c, a, s);
 }
 
 }  // namespace
@@ -733,7 +734,7 @@ int cheb_extent(const dc_ctx *c) {
 int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yprev, float *yout, const float *cin,
                 float *cout, cudaStream_t s) {
   const int E = cheb_extent(c);
-  if (!E || (mode != HSTEP_CHEB && mode != HSTEP_HPSI) || !cin || !yout) {
+  if (!E || (mode != HSTEP_CHEB && mode != HSTEP_HPSI && mode != HSTEP_HLOC) || !cin || !yout) {
     dc_set_error("hpsi: the specialised FP32 kernel does not apply here");
     return DC_ERR_ARG;
   }
@@ -772,11 +773,16 @@ int launch_cheb(dc_ctx *c, int mode, int step, const float *yin, const float *yp
   a.kc = -2.f * 3.f * (kn[3] + kn[4]);
   const bool prev = mode == HSTEP_CHEB && step > 0 && yprev != nullptr;
   const bool proj = cout != nullptr;
+  const bool nl = mode != HSTEP_HLOC;
+  if (!nl && (prev || proj)) {
+    dc_set_error("hpsi: the local part of H is applied without y_prev or output projections");
+    return DC_ERR_ARG;
+  }
   switch (E) {
-    case 18: return run_cheb_e<18>(c, a, prev, proj, s);
-    case 20: return run_cheb_e<20>(c, a, prev, proj, s);
-    case 22: return run_cheb_e<22>(c, a, prev, proj, s);
-    default: return run_cheb_e<32>(c, a, prev, proj, s);
+    case 18: return run_cheb_e<18>(c, a, prev, proj, nl, s);
+    case 20: return run_cheb_e<20>(c, a, prev, proj, nl, s);
+    case 22: return run_cheb_e<22>(c, a, prev, proj, nl, s);
+    default: return run_cheb_e<32>(c, a, prev, proj, nl, s);
   }
 }
 

@@ -1353,9 +1353,19 @@ int launch_hstep(dc_ctx *c, int mode, int step, const T *yin, const T *yprev, T 
   if (!shape_ok(c, shape, sizeof(T))) shape = default_shape(c, sizeof(T));
   // the specialised kernel takes Chebyshev steps and plain H-applies with input projections; the
   // adjoint (and any call without projections) runs the general kernel's default shape
-  if (kShapes[shape].kind == 4 && ((mode != HSTEP_CHEB && mode != HSTEP_HPSI) || !cin || !yout))
+  if (kShapes[shape].kind == 4 && ((mode != HSTEP_CHEB && mode != HSTEP_HPSI && mode != HSTEP_HLOC) || !cin || !yout))
     shape = default_shape(c, sizeof(T));
+  if (mode == HSTEP_HLOC && kShapes[shape].kind != 4) {
+    dc_set_error("hpsi: the local part of H alone runs only in the specialised kernel");
+    return DC_ERR_ARG;
+  }
   return run_shape<T>(c, shape, a, s);
+}
+
+bool hstep_specialised(const dc_ctx *c) {
+  int shape = c->hstep_shape[0];
+  if (!shape_ok(c, shape, sizeof(float))) shape = default_shape(c, sizeof(float));
+  return kShapes[shape].kind == 4;
 }
 
 // Time every useful launch shape on the context's fragments (H applied to `y`, written to `out`,

@@ -346,7 +346,8 @@ __device__ __forceinline__ void tri_ij(int t, int np, int &i, int &j) {
 __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const long long *goff, const int *gnchunk,
                                                   const double *gram, double dV, double *eps, double *C64,
                                                   float *C32, unsigned *flags, int fp64_sweeps,
-                                                  const int *order) {
+                                                  const int *order, const float *cnl, const ProjSlot *slots,
+                                                  const double *Datom) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = order[blockIdx.x];
   const FragDesc D = desc[f];
@@ -385,6 +386,35 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
     M2[i * ld + j] = a;
   }
   __syncthreads();
+
+  // 1b. H Y held only the local part of H: A += sum_a D_a <p_a|y_i> <p_a|y_j> from the block's projections
+  // (orbital-major n x A per fragment), staged with an odd row pitch in the space of M3 and M4, which step 4
+  // fills; FP32 products and sums, like the contraction of the rest of A
+  if (cnl) {
+    const int A = D.natom, ap = A | 1;
+    const float *cf = cnl + D.c_off;
+    float *cs = reinterpret_cast<float *>(M3);
+    const bool staged = (size_t)(n + 1) * ap <= (size_t)4 * np * ld;
+    if (staged) {
+      for (int t = tid; t < n * A; t += SNT) {
+        const int i = t / A, k = t - i * A;
+        cs[i * ap + k] = cf[t];
+      }
+      for (int k = tid; k < A; k += SNT) cs[n * ap + k] = float(Datom[slots[D.at_off + k].atom]);
+      __syncthreads();
+    }
+    for (int t = tid; t < n * n; t += SNT) {
+      const int i = t / n, j = t - i * n;
+      float acc = 0.f;
+      for (int k = 0; k < A; ++k) {
+        const float dk = staged ? cs[n * ap + k] : float(Datom[slots[D.at_off + k].atom]);
+        const float ci = staged ? cs[i * ap + k] : cf[i * A + k], cj = staged ? cs[j * ap + k] : cf[j * A + k];
+        acc = fmaf(dk * ci, cj, acc);
+      }
+      M2[i * ld + j] += (double)acc;
+    }
+    __syncthreads();
+  }
 
   // 2. Cholesky S = L L^T (lower, in M0)
   for (int k = 0; k < n; ++k) {
@@ -1021,7 +1051,7 @@ int launch_gram(dc_ctx *c, const T *Y, const T *HY, cudaStream_t s) {
   return DC_OK;
 }
 
-int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s) {
+int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s, const float *cnl) {
   const int np = c->layout.max_norb + (c->layout.max_norb & 1);
   const size_t sm = 5 * (size_t)np * (np + 1) * sizeof(double);
   DC_CUDA(dc_set_smem((const void *)k_subspace, sm));
@@ -1029,7 +1059,8 @@ int launch_subspace(dc_ctx *c, int precision_bits, double *eps, cudaStream_t s) 
   const int nf = c->f_hi - c->f_lo;
   if (nf <= 0) return DC_OK;
   k_subspace<<<nf, SNT, sm, s>>>(c->d_desc, c->d_gram_off, c->d_gram_nchunk, c->d_gram, c->dV, eps, c->d_C64,
-                                 precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags, fp64_sweeps, c->d_frag_order);
+                                 precision_bits == 32 ? c->d_C32 : nullptr, c->d_flags, fp64_sweeps, c->d_frag_order,
+                                 cnl, c->d_slots, c->d_atom_D);
   DC_CUDA(cudaGetLastError());
   return DC_OK;
 }
