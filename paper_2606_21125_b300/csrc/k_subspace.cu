@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(SNT) k_subspace(const FragDesc *desc, const lo
 
   // 1b. H Y held only the local part of H: A += sum_a D_a <p_a|y_i> <p_a|y_j> from the block's projections
   // (orbital-major n x A per fragment), staged with an odd row pitch in the space of M3 and M4, which step 4
-  // fills; FP32 products and sums, like the contraction of the rest of A
+  // fills (read from global memory instead when n + 1 rows of A do not fit there); FP32 products and sums,
+  // like the contraction of the rest of A
   if (cnl) {
     const int A = D.natom, ap = A | 1;
     const float *cf = cnl + D.c_off;
